@@ -1,0 +1,136 @@
+/*
+ * ctd_oracle.h -- CPU oracle for the gCTD photon transport (TEST INFRASTRUCTURE).
+ *
+ * This header and ctd_oracle.c are a plain, slow, single-threaded restatement of
+ * the method of Jia, Yan, Gu and Jiang, "Fast Monte Carlo Simulation for
+ * Patient-specific CT/CBCT Imaging Dose Calculation" (arXiv:1109.3266):
+ * Woodcock tracking (Sec. 2.1), interaction choice (Sec. 2.1), R/C-surface
+ * angular sampling (Sec. 2.2.2, Eq. 1; Sec. 2.2.3, Eq. 2), local deposition
+ * (Sec. 2.1), stratified spectrum (Sec. 2.2.5), source trajectory (Sec. 2.2.6)
+ * and batches (Sec. 2.2.1).
+ *
+ * Only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load this code.  The product library never links or calls it,
+ * and it shares no source with the product library.
+ *
+ * Every function exists in two precisions built from one source:
+ *   *_f64 : the method in IEEE binary64 with the C library's log/sin/cos/sqrt;
+ *   *_f32 : the method in the paper's single precision (Sec. 2.2.7 item 1), with
+ *           a fixed operation order and the single-precision log and sincos
+ *           defined in ctd_oracle.c, so that integer decisions (interaction
+ *           type, voxel index, escape) are taken in binary32.
+ * Integer-only helpers (Philox, allocation) have one version.
+ */
+#ifndef CTD_ORACLE_H
+#define CTD_ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Material record: the closed-form cross sections need these four numbers. */
+typedef struct {
+    double z_over_a;  /* electrons per gram / N_A (Compton, Eq. 2 with S = 1)      */
+    double a_mol;     /* molar mass of one formula unit, g/mol (PE and Rayleigh)   */
+    double z_eff;     /* effective atomic number (PE ~ Z^4, Rayleigh ~ Z^2)         */
+    double q0;        /* analytic form-factor width, 1/Angstrom; <= 0 means F^2 = 1 */
+} or_material;
+
+enum { OR_SRC_STATIC = 0, OR_SRC_ARC = 1 };
+enum { OR_MODE_FULL = 0, OR_MODE_MAX_REAL = 1 };
+enum { OR_SAMPLE_SURFACE = 0, OR_SAMPLE_EXACT = 1 };
+
+typedef struct {
+    /* phantom: x fastest, then y, then z; centred at the origin */
+    int nx, ny, nz;
+    double dx, dy, dz;            /* cm */
+    const uint8_t *mat;           /* material index per voxel */
+    const float *rho;             /* density per voxel, g/cm^3 */
+    int n_mat;
+    const or_material *mats;
+    /* source */
+    int src_kind;                 /* OR_SRC_STATIC: from (0,0,-sad) along +z; OR_SRC_ARC: about z */
+    double sad;                   /* source-to-centre distance, cm */
+    double u_lo, u_hi, v_lo, v_hi;/* field at the centre plane, cm */
+    int n_proj;                   /* discrete projections on the arc */
+    double arc0, arc1;            /* arc start/end, radians */
+    int continuous;               /* 1: angle uniform on [arc0, arc1) (Sec. 2.2.6) */
+    /* spectrum: bins [e_lo, e_hi] keV with relative weight w (Sec. 2.2.5) */
+    int nbins;
+    const double *e_lo, *e_hi, *w;
+    /* physics */
+    int e_min, e_max;             /* node grid e_min..e_max keV step 1; e_min is the cutoff */
+    int n_zeta;                   /* surface columns in zeta */
+    double majorant_scale;        /* >= 1 */
+    int mode;                     /* OR_MODE_* */
+    int max_real;                 /* real interactions before termination (OR_MODE_MAX_REAL) */
+    int sampling;                 /* OR_SAMPLE_* (EXACT only in f64) */
+    /* run */
+    uint64_t n_hist;
+    int n_batches;
+    uint64_t seed;
+} or_problem;
+
+/* Integer counts: one slot per outcome. */
+typedef struct {
+    uint64_t pe, compton, rayleigh, fictitious;
+    uint64_t escaped, missed, cutoff, terminated, aborted;
+    uint64_t steps;
+    double e_emitted, e_escaped, e_deposited;  /* keV */
+} or_counts;
+
+/* Philox4x32-10, Salmon et al. (SC'11). */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_uniform(uint32_t x);
+
+/* closed forms, cm^2/g, E in keV */
+double or_sigma_kn(double e_kev);                  /* cm^2 per electron */
+double or_mu_pe(const or_material *m, double e_kev);
+double or_mu_compton(const or_material *m, double e_kev);
+double or_mu_rayleigh(const or_material *m, double e_kev);
+
+/* integer allocation of n histories to bins by largest remainder */
+int or_allocate(uint64_t n, int nbins, const double *w, uint64_t *out);
+
+/* single-precision elementary functions of the f32 method */
+float or_log_f32(float u);
+void or_sincos_turns_f32(float t, float *c, float *s);
+void or_eval_log_f32(const float *u, float *out, size_t n);
+void or_eval_sincos_f32(const float *t, float *c, float *s, size_t n);
+
+/* problem set-up (tables and surfaces) and transport of a history range */
+typedef struct or_setup or_setup;
+or_setup *or_setup_create_f64(const or_problem *p);
+or_setup *or_setup_create_f32(const or_problem *p);
+void or_setup_destroy(or_setup *s);
+int or_transport_f64(const or_setup *s, uint64_t h0, uint64_t h1, double *edep, or_counts *c);
+int or_transport_f32(const or_setup *s, uint64_t h0, uint64_t h1, double *edep, or_counts *c);
+
+/* inspection of the set-up (node values as stored; f32 values widened) */
+int or_setup_sizes(const or_setup *s, int *n_e, int *n_zeta, int *n_mat);
+void or_setup_tables(const or_setup *s, double *mu_cum /* n_mat*n_e*3 */, double *mu_max /* n_e */);
+void or_setup_surfaces(const or_setup *s, double *c_surf /* n_e*n_zeta */,
+                       double *r_surf /* n_mat*n_e*n_zeta */);
+
+/* the surfaces on their own (Sec. 2.2.2 and 2.2.3), binary64 */
+void or_build_kn_surface(int e_min, int n_e, int n_zeta, double *out);
+void or_build_rayleigh_surface(double q0, int e_min, int n_e, int n_zeta, double *out);
+
+/* angular samplers for the sampler validation of Figs. 3-4:
+ * kind 0 = Compton (free-electron Klein-Nishina), 1 = Rayleigh;
+ * surface samplers read the set-up's surfaces at E; exact samplers use rejection. */
+int or_sample_mu_f64(const or_setup *s, int kind, int material, double e_kev, int exact,
+                     uint64_t seed, uint64_t n, double *out);
+int or_sample_mu_f32(const or_setup *s, int kind, int material, double e_kev,
+                     uint64_t seed, uint64_t n, double *out);
+
+/* the direction rotation on its own, for invariant checks */
+void or_rotate_f64(double *u, double mu, double t_phi);
+void or_rotate_f32(float *u, float mu, float t_phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

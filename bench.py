@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the dose engine: photon histories per second on one GB300.
+
+A step is one complete dose calculation of the workload through the C ABI:
+source sampling, Woodcock transport, interactions and tallies for every
+history in N_b batches, the batch folds and the avg-RSD reduction.  Its inputs
+(phantom, tables) are resident in HBM; between timed steps L2 is flushed by
+writing a 256 MB buffer, outside the timed events.
+
+Default workload: the CBCT water phantom, 256x256x128 voxels of 0.2 cm,
+120 kVp, 360 projections, 1e9 histories in 10 batches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica (own seed); value = all histories / max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon histories/sec (sec-to-1% avg RSD beside it)"
+UNIT = "histories/s"
+SM_COUNT = 152
+LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes issue per SM clock
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name):
+    from paper_1109_3266_gb300 import inputs as I
+    if name == "cbct_water":
+        return I.cbct_water()
+    if name == "head":
+        return I.head()
+    if name == "tiny_water":
+        return I.tiny_water()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("CTD_BENCH_BACKEND", "nccl")
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def oracle_rate(p, seconds, threads):
+    """Histories/s of the binary64 oracle as it stands on a bounded prefix of the workload."""
+    from oracle import oracle as O
+    s = O.Setup(p, 64)
+    n = 4000
+    while True:
+        t0 = time.perf_counter()
+        s.transport(0, n, threads)
+        dt = time.perf_counter() - t0
+        if dt > 0.5 or n >= p.n_hist:
+            break
+        n *= 4
+    n = int(max(2000, min(p.n_hist, n / max(dt, 1e-6) * seconds)))
+    t0 = time.perf_counter()
+    _, c = s.transport(0, n, threads)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, c
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world = dist_init(args.gpus)
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    threads = cpu_cores()
+    for _ in range(args.warmup):
+        oracle_rate(p, 0.5, threads)
+    rates, ns = [], []
+    for _ in range(args.steps):
+        r, n, dt, _ = oracle_rate(p, args.ref_seconds, threads)
+        rates.append(r)
+        ns.append(n)
+    value = float(np.mean(rates))
+    sample = (f"binary64 oracle, first {ns[0]} histories of batch 0 of {p.name} per step, "
+              f"{threads} threads over history ranges")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ns[0] / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": p.name, "histories_per_step": ns[0]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+
+    from paper_1109_3266_gb300 import ctd
+
+    rank, world = dist_init(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = workload(args.workload)
+    seed = p.seed + 7919 * rank
+    nvox = p.phantom.nvox
+    ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
+                         threads_per_block=args.threads, chunk=args.chunk)
+    h = ctd.load_problem(ctx, p)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        ctd.ctd_run(ctx, h, p.n_hist, seed, p.n_batches)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_transport, launches, stats = 0.0, 0, None
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            _, _, stats = ctd.ctd_get_dose_and_stddev(ctx, h, nvox, want_arrays=False)
+            t_transport += stats["t_transport_s"]
+            launches += stats["transport_launches"]
+            flush.zero_()
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    t_max = max_over_ranks(t_dev, world, dev)
+    hist_total = sum_over_ranks(float(p.n_hist * args.steps), world, dev)
+    value = hist_total / t_max
+
+    # sec-to-1% avg RSD: N scales as RSD^-2 at fixed variance per history
+    rsd = stats["avg_rsd"]
+    sec_run = t_dev / args.steps
+    sec_to_1 = sec_run * (rsd / 0.01) ** 2
+
+    # end to end through the public API with host buffers: phantom upload, set-up,
+    # run and the read-back of dose and stddev, every step
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    mat_h = torch.from_numpy(np.ascontiguousarray(p.phantom.mat).ravel()).pin_memory().numpy()
+    rho_h = torch.from_numpy(np.ascontiguousarray(p.phantom.rho).ravel()).pin_memory().numpy()
+    dose_h = torch.empty(nvox, dtype=torch.float64).pin_memory().numpy()
+    sd_h = torch.empty(nvox, dtype=torch.float64).pin_memory().numpy()
+    st = ctd.ctd_run_stats()
+    L = ctd.lib()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ph = p.phantom
+        h2 = ctd.ctd_create_phantom(ctx, ph.nx, ph.ny, ph.nz, ph.dx, ph.dy, ph.dz, mat_h, rho_h, ph.materials)
+        s = p.source
+        ctd.ctd_set_source(ctx, h2, s.kind, s.sad, s.u_lo, s.u_hi, s.v_lo, s.v_hi, s.n_proj, s.arc0, s.arc1,
+                           s.continuous)
+        ctd.ctd_set_spectrum(ctx, h2, p.spectrum.e_lo, p.spectrum.e_hi, p.spectrum.w)
+        ctd.ctd_run(ctx, h2, p.n_hist, seed, p.n_batches)
+        ctd._check(L.ctd_get_dose_and_stddev(ctx, h2, ctd._dp(dose_h), ctd._dp(sd_h), nvox, ctd.C.byref(st)))
+        ctd.ctd_destroy_phantom(ctx, h2)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = sum_over_ranks(float(p.n_hist * e2e_steps), world, dev) / t_e2e
+    h2d = nvox * (1 + 4) + 3 * 8 * len(p.spectrum.w)
+    d2h = nvox * 16
+
+    # roofline of the transport kernel: lane-instructions per history over the
+    # SM issue ceiling 152 SM x 128 lanes x clock
+    peaks, peak_kind = load_peaks()
+    ck = clk.summary()
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = SM_COUNT * LANES_PER_SM_CLK * mhz * 1e6 / 1e12        # tera lane-instructions / s
+    inst_per_hist = args.inst_per_history
+    achieved = p.n_hist * args.steps * inst_per_hist / t_transport / 1e12 if inst_per_hist else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-inst/s",
+            "frac": achieved / peak if achieved else None, "traffic": args.traffic_per_launch,
+            "kernel": "transport_kernel", "launches": launches,
+            "avg_launch_ms": 1e3 * t_transport / max(launches, 1),
+            "peak_source": f"{SM_COUNT} SM x {LANES_PER_SM_CLK} lanes x {mhz:.0f} MHz ({peak_kind} max clock)"}
+    # memory-side view: algorithmic bytes per history, counted live from this run's steps and deposits
+    steps_per_hist = stats["steps"] / p.n_hist
+    deposits_per_hist = (stats["pe"] + stats["compton"]) / p.n_hist
+    bytes_per_hist = steps_per_hist * 5.0 + deposits_per_hist * 16.0
+    roof["memory_side"] = {"bytes_per_history": bytes_per_hist,
+                           "achieved_gbs": p.n_hist * args.steps * bytes_per_hist / t_transport / 1e9,
+                           "peak_gbs": peaks.get("hbm_gbs"),
+                           "atomics_per_s": p.n_hist * args.steps * deposits_per_hist / t_transport,
+                           "steps_per_history": steps_per_hist, "deposits_per_history": deposits_per_hist}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = cpu_cores()
+        r, n, dt, _ = oracle_rate(p, args.ref_seconds, threads)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"binary64 oracle, first {n} histories of {p.name} ({dt:.1f} s), {threads} threads"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": p.name, "voxels": [p.phantom.nx, p.phantom.ny, p.phantom.nz],
+                       "voxel_cm": p.phantom.dx, "histories_per_step": p.n_hist, "batches": p.n_batches,
+                       "kvp": 120 if p.name == "cbct_water" else None, "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (256 MB write outside timed events)",
+                       "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk},
+            "sec_to_1pct_avg_rsd": sec_to_1, "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
+            "clocks": ck,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches + 17 * args.steps,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+        }), flush=True)
+    ctd.ctd_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cbct_water")
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inst-per-history", type=float, default=0.0)
+    ap.add_argument("--traffic-per-launch", type=float, default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * ctd.h -- C ABI of the GB300 photon Monte Carlo dose engine (method of Jia,
+ * Yan, Gu, Jiang, "Fast Monte Carlo Simulation for Patient-specific CT/CBCT
+ * Imaging Dose Calculation", arXiv:1109.3266).
+ *
+ * Conventions for every call:
+ *   - the return value is a ctd_status; on failure ctd_last_error() returns a
+ *     message for the calling thread; no call aborts the process;
+ *   - pointers are host pointers unless the name ends in _dev; the caller owns
+ *     every buffer it passes and the library copies what it keeps;
+ *   - voxel arrays are x fastest, then y, then z (index x + nx*(y + ny*z));
+ *   - units: cm, g/cm^3, keV, radians; dose in Gy per source history;
+ *   - a context is used by one host thread at a time;
+ *   - all work runs on the context's CUDA stream; calls that return results to
+ *     the host synchronise that stream.
+ */
+#ifndef CTD_H
+#define CTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CTD_ABI_VERSION 1
+
+typedef enum {
+    CTD_OK = 0,
+    CTD_EINVAL = 1,       /* an argument is out of range or inconsistent   */
+    CTD_ENOMEM = 2,       /* device or host allocation failed              */
+    CTD_ECUDA = 3,        /* a CUDA runtime call failed                    */
+    CTD_EBUSY = 4,        /* the object is in use by a running request     */
+    CTD_ETIMEOUT = 5,     /* a bounded wait ran out                        */
+    CTD_ECANCELLED = 6,   /* the request was cancelled                     */
+    CTD_ENOTFOUND = 7     /* unknown handle                                */
+} ctd_status;
+
+typedef struct ctd_ctx ctd_ctx;
+typedef int32_t ctd_phantom;
+
+/* Context options.  Zero fields take defaults. */
+typedef struct {
+    int device;               /* CUDA device ordinal                                  */
+    void *stream;             /* cudaStream_t to launch on; NULL: the context makes one */
+    int blocks_per_sm;        /* transport grid = SMs x blocks_per_sm (default 4)     */
+    int threads_per_block;    /* multiple of 32, <= 1024 (default 256)               */
+    int chunk;                /* histories a warp claims per refill (default 64)      */
+} ctd_options;
+
+/* Material: the numbers the closed-form cross sections use (Sec. 2.1).
+ *   z_over_a : electrons per gram / Avogadro (Compton: N_A (Z/A) sigma_KN)
+ *   a_mol    : g/mol of one formula unit (photoelectric 1e-2 Z^4/E_MeV^3 microbarn,
+ *              Rayleigh 1.565e-5 Z^2/E_MeV^2 barn, both per formula unit)
+ *   z_eff    : effective atomic number
+ *   q0       : Rayleigh form-factor width F^2 ~ exp(-q^2/q0^2), 1/Angstrom; <= 0: F^2 = 1 */
+typedef struct {
+    double z_over_a;
+    double a_mol;
+    double z_eff;
+    double q0;
+} ctd_material;
+
+typedef enum { CTD_SRC_STATIC = 0, CTD_SRC_ARC = 1 } ctd_source_kind;
+
+/* Source (Sec. 2.2.6).  STATIC: point at (0, 0, -sad) aimed along +z, field u
+ * along x and v along y.  ARC: point at sad (sin b, cos b, 0) aimed at the
+ * origin, u lateral in the xy-plane, v along z; b = arc0 + (arc1-arc0) k/n_proj
+ * for a uniform integer k < n_proj, or b uniform on [arc0, arc1) if continuous.
+ * The field [u_lo,u_hi] x [v_lo,v_hi] is given in cm at the plane through the
+ * origin; directions are uniform in solid angle over it. */
+typedef struct {
+    int kind;
+    double sad_cm;
+    double u_lo_cm, u_hi_cm, v_lo_cm, v_hi_cm;
+    int n_proj;
+    double arc0_rad, arc1_rad;
+    int continuous;
+} ctd_source;
+
+typedef enum { CTD_MODE_FULL = 0, CTD_MODE_MAX_REAL = 1 } ctd_mode;
+
+/* Physics options.  Attenuation data are linear interpolation between the
+ * closed forms at integer-keV nodes e_min..e_max (Sec. 2.2.7 item 3); e_min is
+ * also the absorption energy (Sec. 3.1).  n_zeta columns per R/C surface row
+ * (Sec. 2.2.2-2.2.3).  majorant_scale >= 1 multiplies mu_max(E) (Sec. 2.1).
+ * CTD_MODE_MAX_REAL stops a photon after max_real real interactions (1 =
+ * primary only), counting its remaining energy as escaped. */
+typedef struct {
+    int e_min_kev;
+    int e_max_kev;
+    int n_zeta;
+    double majorant_scale;
+    int mode;
+    int max_real;
+} ctd_physics;
+
+/* Results of the last run of a phantom. */
+typedef struct {
+    uint64_t histories;
+    int n_batches;
+    uint64_t pe, compton, rayleigh, fictitious;   /* interactions and fictitious events */
+    uint64_t escaped, missed, cutoff, terminated, aborted;  /* how histories ended       */
+    uint64_t steps;                               /* Woodcock steps                        */
+    double e_emitted_kev, e_escaped_kev, e_deposited_kev;
+    double avg_rsd;          /* mean s/D over D > 0.1 D_max, rho >= 0.1 g/cm^3            */
+    double paper_sigma_bar;  /* mean s/D_max over D > 0.2 D_max (Sec. 3.1)               */
+    double d_max;            /* Gy per history                                            */
+    double t_total_s;        /* wall time of the run call                                 */
+    double t_transport_s;    /* device time of the transport kernels (CUDA events)        */
+    int transport_launches;
+} ctd_run_stats;
+
+/* Thread-local message of the last failed call on this thread. */
+const char *ctd_last_error(void);
+int ctd_abi_version(void);
+
+/* Context on one GPU.  opt may be NULL.  The context owns the stream it makes;
+ * a stream passed in opt->stream stays the caller's. */
+int ctd_create(ctd_ctx **out, const ctd_options *opt);
+int ctd_destroy(ctd_ctx *ctx);
+
+/* Voxel phantom (Sec. 2.2.1): nx*ny*nz voxels of dx*dy*dz cm centred at the
+ * origin; mat[v] < n_mat indexes mats; density[v] >= 0 (g/cm^3).  Host arrays;
+ * the library copies them to the device and keeps them resident until
+ * ctd_destroy_phantom.  Default physics: nodes 1..150 keV, n_zeta 1024, scale 1,
+ * full transport. */
+int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                       const uint8_t *mat, const float *density, int n_mat, const ctd_material *mats,
+                       ctd_phantom *out);
+int ctd_destroy_phantom(ctd_ctx *ctx, ctd_phantom ph);
+int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys);
+int ctd_set_source(ctd_ctx *ctx, ctd_phantom ph, const ctd_source *src);
+
+/* Spectrum (Sec. 2.2.5): nbins intervals [e_lo[j], e_hi[j]] keV (e_lo == e_hi
+ * is a line) with weights w[j] >= 0, sum > 0, inside [e_min, e_max] of the
+ * physics.  Each batch's histories are split over the bins by largest
+ * remainder and run bin by bin with E uniform inside the bin. */
+int ctd_set_spectrum(ctd_ctx *ctx, ctd_phantom ph, const double *e_lo, const double *e_hi,
+                     const double *w, int nbins);
+
+/* Transport n_histories in n_batches (>= 2) batches (Sec. 2.2.1) with random
+ * numbers keyed by seed; afterwards mean dose and batch uncertainty are ready
+ * for ctd_get_dose_and_stddev.  Blocks until the device is done. */
+int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches);
+
+/* Transport only histories [h_begin, h_end) of the n_histories/n_batches
+ * problem (a shard: history h gives the same track in any shard) and add their
+ * energy to the phantom's deposit tally, which ctd_get_edep returns; counts
+ * and energies go to the stats.  The tally and stats are cleared when
+ * clear != 0. */
+int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches,
+                  uint64_t h_begin, uint64_t h_end, int clear);
+
+/* Mean dose and its standard error (Gy per history, nvox doubles each; either
+ * may be NULL) and the stats of the last ctd_run (stats may be NULL). */
+int ctd_get_dose_and_stddev(ctd_ctx *ctx, ctd_phantom ph, double *dose, double *stddev, size_t nvox,
+                            ctd_run_stats *stats);
+
+/* Energy deposited per voxel (keV) summed over the last run or range runs. */
+int ctd_get_edep(ctd_ctx *ctx, ctd_phantom ph, double *edep_kev, size_t nvox);
+
+/* The binary32 tables the device uses, widened to double: mu_cum[n_mat][n_e][3]
+ * (photoelectric, +Compton, +Rayleigh, cm^2/g), mu_max[n_e] (1/cm),
+ * c_surf[n_e][n_zeta], r_surf[n_mat][n_e][n_zeta].  Sizes via the out-params
+ * (any pointer may be NULL).  Builds the tables if needed. */
+int ctd_get_tables(ctd_ctx *ctx, ctd_phantom ph, int *n_e, int *n_zeta, int *n_mat, double *mu_cum,
+                   double *mu_max, double *c_surf, double *r_surf);
+
+/* Sampler validation (Figs. 3-4): n polar cosines at energy e_kev drawn on the
+ * device from the C surface (kind 0) or the R surface of material (kind 1),
+ * the i-th from Philox counter (i, 0, 0, 3) under seed.  out: host doubles. */
+int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e_kev, uint64_t seed,
+                  uint64_t n, double *out);
+
+/* Device evaluation of the transport's binary32 logarithm (fn 0: out = ln x)
+ * and sincos of 2 pi x (fn 1: out[2i] = cos, out[2i+1] = sin) for n host
+ * floats; out holds n (fn 0) or 2n (fn 1) host floats. */
+int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTD_H */

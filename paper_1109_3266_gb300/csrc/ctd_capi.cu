@@ -1,0 +1,715 @@
+// ctd_capi.cu -- the C ABI of include/ctd.h: contexts, resident phantoms,
+// source/spectrum/physics set-up, the batch loop of Sec. 2.2.1 and results.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ctd_internal.h"
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return fail(CTD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+#define CKS(call)                                                                                         \
+    do {                                                                                                  \
+        int s_ = (call);                                                                                  \
+        if (s_ != CTD_OK) {                                                                               \
+            if (g_error.empty()) fail(s_, "%s failed: %s", #call, cudaGetErrorString(cudaGetLastError())); \
+            return s_;                                                                                    \
+        }                                                                                                 \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    int ensure(size_t count)
+    {
+        if (count <= n && p) return CTD_OK;
+        release();
+        if (count == 0) count = 1;
+        if (cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(CTD_ENOMEM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+        }
+        n = count;
+        return CTD_OK;
+    }
+};
+
+struct Phantom {
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0, dy = 0, dz = 0;
+    size_t nvox = 0;
+    std::vector<ctd_material> mats;
+    std::vector<double> rho_max;
+    std::vector<int> present;
+    ctd_physics phys{};
+    ctd_source src{};
+    bool has_src = false;
+    std::vector<double> e_lo, e_hi, w;
+    bool has_spec = false;
+
+    DevBuf<uint8_t> mat;
+    DevBuf<float> rho;
+    // tables
+    bool tables_ok = false;
+    int n_e = 0;
+    std::vector<float> h_tab, h_mm, h_cs, h_rs;
+    DevBuf<float> tab, mm, cs, rs;
+    // per-run state
+    DevBuf<double> tally, sum_d, sum_d2, edep, dose, sd, partials, result;
+    DevBuf<ctd::DeviceCounts> counts;
+    DevBuf<unsigned long long> work;
+    DevBuf<uint64_t> pref;     // [2][nbins+1]: batch of n_lo+1, batch of n_lo
+    DevBuf<float> bins;        // [2][nbins]: lo, hi
+    DevBuf<float> proj;        // [2][n_proj]: cos, sin
+    uint64_t alloc_n = ~0ull;
+    int alloc_nb = -1;
+    ctd_run_stats stats{};
+    bool have_result = false;
+};
+
+}  // namespace
+
+struct ctd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int blocks_per_sm = 4;
+    int threads = 256;
+    int chunk = 64;
+    std::map<int, std::unique_ptr<Phantom>> phantoms;
+    int next_id = 1;
+    std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+constexpr int kRsdParts = 1024;
+
+int use_device(ctd_ctx *ctx)
+{
+    if (!ctx) return fail(CTD_EINVAL, "null context");
+    g_error.clear();
+    CK(cudaSetDevice(ctx->device));
+    return CTD_OK;
+}
+
+Phantom *find(ctd_ctx *ctx, ctd_phantom id)
+{
+    auto it = ctx->phantoms.find(id);
+    return it == ctx->phantoms.end() ? nullptr : it->second.get();
+}
+
+int build_tables(ctd_ctx *ctx, Phantom &P)
+{
+    if (P.tables_ok) return CTD_OK;
+    const ctd_physics &ph = P.phys;
+    const int n_e = ph.e_max_kev - ph.e_min_kev + 1;
+    const int nm = static_cast<int>(P.mats.size());
+    std::vector<double> cum, mmax;
+    ctd::build_tables(P.mats, P.rho_max, P.present, ph.e_min_kev, n_e, ph.majorant_scale, cum, mmax);
+    P.h_tab.assign(static_cast<size_t>(nm) * n_e * 4, 0.0f);
+    for (size_t i = 0; i < static_cast<size_t>(nm) * n_e; ++i)
+        for (int c = 0; c < 3; ++c) P.h_tab[i * 4 + c] = static_cast<float>(cum[i * 3 + c]);
+    P.h_mm.resize(n_e);
+    for (int j = 0; j < n_e; ++j) P.h_mm[j] = static_cast<float>(mmax[j]);
+    const size_t row = static_cast<size_t>(n_e) * ph.n_zeta;
+    std::vector<double> tmp(row);
+    ctd::build_surface(0, 0.0, ph.e_min_kev, n_e, ph.n_zeta, tmp.data());
+    P.h_cs.resize(row);
+    for (size_t i = 0; i < row; ++i) P.h_cs[i] = static_cast<float>(tmp[i]);
+    P.h_rs.resize(row * nm);
+    for (int m = 0; m < nm; ++m) {
+        ctd::build_surface(1, P.mats[m].q0, ph.e_min_kev, n_e, ph.n_zeta, tmp.data());
+        for (size_t i = 0; i < row; ++i) P.h_rs[m * row + i] = static_cast<float>(tmp[i]);
+    }
+    int rc;
+    if ((rc = P.tab.ensure(P.h_tab.size())) || (rc = P.mm.ensure(n_e)) || (rc = P.cs.ensure(row)) ||
+        (rc = P.rs.ensure(row * nm)))
+        return rc;
+    CK(cudaMemcpyAsync(P.tab.p, P.h_tab.data(), P.h_tab.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P.mm.p, P.h_mm.data(), n_e * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P.cs.p, P.h_cs.data(), row * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P.rs.p, P.h_rs.data(), row * nm * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    P.n_e = n_e;
+    P.tables_ok = true;
+    return CTD_OK;
+}
+
+// stratified allocation for batches of n_lo + 1 and n_lo histories (Sec. 2.2.5)
+int upload_allocation(ctd_ctx *ctx, Phantom &P, uint64_t n, int nb)
+{
+    if (P.alloc_n == n && P.alloc_nb == nb) return CTD_OK;
+    const int nbins = static_cast<int>(P.w.size());
+    const uint64_t n_lo = n / static_cast<uint64_t>(nb);
+    std::vector<uint64_t> pref(2 * (nbins + 1), 0), a;
+    for (int which = 0; which < 2; ++which) {
+        const uint64_t size = which == 0 ? n_lo + 1 : n_lo;
+        if (!ctd::allocate(size, P.w, a)) return fail(CTD_EINVAL, "spectrum weights cannot be allocated");
+        uint64_t *pr = &pref[which * (nbins + 1)];
+        for (int j = 0; j < nbins; ++j) pr[j + 1] = pr[j] + a[j];
+    }
+    int rc;
+    if ((rc = P.pref.ensure(pref.size()))) return rc;
+    CK(cudaMemcpyAsync(P.pref.p, pref.data(), pref.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    P.alloc_n = n;
+    P.alloc_nb = nb;
+    return CTD_OK;
+}
+
+int ensure_run_buffers(Phantom &P)
+{
+    int rc;
+    if ((rc = P.tally.ensure(P.nvox)) || (rc = P.sum_d.ensure(P.nvox)) || (rc = P.sum_d2.ensure(P.nvox)) ||
+        (rc = P.edep.ensure(P.nvox)) || (rc = P.dose.ensure(P.nvox)) || (rc = P.sd.ensure(P.nvox)) ||
+        (rc = P.partials.ensure(6 * kRsdParts)) || (rc = P.result.ensure(8)) || (rc = P.counts.ensure(1)) ||
+        (rc = P.work.ensure(1)))
+        return rc;
+    return CTD_OK;
+}
+
+int check_ready(Phantom &P)
+{
+    if (!P.has_src) return fail(CTD_EINVAL, "no source set");
+    if (!P.has_spec) return fail(CTD_EINVAL, "no spectrum set");
+    for (size_t j = 0; j < P.w.size(); ++j)
+        if (!(P.e_lo[j] >= P.phys.e_min_kev && P.e_hi[j] <= P.phys.e_max_kev))
+            return fail(CTD_EINVAL, "spectrum bin %zu outside the node grid [%d, %d] keV", j, P.phys.e_min_kev,
+                        P.phys.e_max_kev);
+    return CTD_OK;
+}
+
+void fill_params(ctd_ctx *ctx, Phantom &P, uint64_t seed, ctd::TransportParams &T)
+{
+    std::memset(&T, 0, sizeof(T));
+    T.mat = P.mat.p;
+    T.rho = P.rho.p;
+    T.tab = P.tab.p;
+    T.mmax = P.mm.p;
+    T.csurf = P.cs.p;
+    T.rsurf = P.rs.p;
+    T.nbins = static_cast<int>(P.w.size());
+    T.bin_lo = P.bins.p;
+    T.bin_hi = P.bins.p + T.nbins;
+    T.cb = P.proj.p;
+    T.sb = P.proj.p + (P.src.n_proj > 0 ? P.src.n_proj : 1);
+    T.work = P.work.p;
+    T.counts = P.counts.p;
+    T.seed = seed;
+    T.nx = P.nx;
+    T.ny = P.ny;
+    T.nz = P.nz;
+    const double hx = static_cast<double>(P.nx) * P.dx / 2.0, hy = static_cast<double>(P.ny) * P.dy / 2.0,
+                 hz = static_cast<double>(P.nz) * P.dz / 2.0;
+    T.bx0 = static_cast<float>(-hx);
+    T.by0 = static_cast<float>(-hy);
+    T.bz0 = static_cast<float>(-hz);
+    T.bx1 = static_cast<float>(hx);
+    T.by1 = static_cast<float>(hy);
+    T.bz1 = static_cast<float>(hz);
+    T.ix = static_cast<float>(1.0 / P.dx);
+    T.iy = static_cast<float>(1.0 / P.dy);
+    T.iz = static_cast<float>(1.0 / P.dz);
+    T.n_mat = static_cast<int>(P.mats.size());
+    T.n_e = P.n_e;
+    T.n_zeta = P.phys.n_zeta;
+    T.e_min = P.phys.e_min_kev;
+    T.src_kind = P.src.kind;
+    T.n_proj = P.src.n_proj;
+    T.continuous = P.src.continuous;
+    T.D = static_cast<float>(P.src.sad_cm);
+    T.D2 = T.D * T.D;
+    T.ulo = static_cast<float>(P.src.u_lo_cm);
+    T.uw = static_cast<float>(P.src.u_hi_cm) - T.ulo;
+    T.vlo = static_cast<float>(P.src.v_lo_cm);
+    T.vw = static_cast<float>(P.src.v_hi_cm) - T.vlo;
+    T.a0t = static_cast<float>(P.src.arc0_rad / (2.0 * ctd::kPi));
+    T.awt = static_cast<float>((P.src.arc1_rad - P.src.arc0_rad) / (2.0 * ctd::kPi));
+    T.mode = P.phys.mode;
+    T.max_real = P.phys.max_real;
+    T.chunk = ctx->chunk;
+}
+
+cudaEvent_t event_at(ctd_ctx *ctx, size_t i)
+{
+    while (ctx->events.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->events.push_back(e);
+    }
+    return ctx->events[i];
+}
+
+// One transport launch over local histories [lb, le) of a batch starting at global h_base.
+int transport(ctd_ctx *ctx, Phantom &P, ctd::TransportParams &T, int which_size, uint64_t h_base, uint64_t lb,
+              uint64_t le, double *tally, size_t ev_index)
+{
+    T.pref = P.pref.p + which_size * (T.nbins + 1);
+    T.h_base = h_base;
+    T.local_begin = lb;
+    T.local_end = le;
+    T.tally = tally;
+    CK(cudaMemsetAsync(P.work.p, 0, sizeof(unsigned long long), ctx->stream));
+    cudaEvent_t e0 = event_at(ctx, 2 * ev_index), e1 = event_at(ctx, 2 * ev_index + 1);
+    if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
+    CK(cudaEventRecord(e0, ctx->stream));
+    const int grid = ctx->num_sms * ctx->blocks_per_sm;
+    CKS(ctd::launch_transport(T, grid, ctx->threads, ctd::transport_smem_bytes(T.n_mat, T.n_e), ctx->stream));
+    CK(cudaEventRecord(e1, ctx->stream));
+    return CTD_OK;
+}
+
+int prepare_run(ctd_ctx *ctx, Phantom &P, uint64_t n, int nb)
+{
+    int rc;
+    if ((rc = check_ready(P))) return rc;
+    if ((rc = build_tables(ctx, P))) return rc;
+    if ((rc = upload_allocation(ctx, P, n, nb))) return rc;
+    if ((rc = ensure_run_buffers(P))) return rc;
+    return CTD_OK;
+}
+
+int collect(ctd_ctx *ctx, Phantom &P, size_t n_launch, double t0_wall)
+{
+    ctd::DeviceCounts c;
+    CK(cudaMemcpyAsync(&c, P.counts.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+    double res[4];
+    CK(cudaMemcpyAsync(res, P.result.p, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctd_run_stats &s = P.stats;
+    s.pe = c.n[ctd::kCntPe];
+    s.compton = c.n[ctd::kCntCompton];
+    s.rayleigh = c.n[ctd::kCntRayleigh];
+    s.fictitious = c.n[ctd::kCntFict];
+    s.escaped = c.n[ctd::kCntEscaped];
+    s.missed = c.n[ctd::kCntMissed];
+    s.cutoff = c.n[ctd::kCntCutoff];
+    s.terminated = c.n[ctd::kCntTerminated];
+    s.aborted = c.n[ctd::kCntAborted];
+    s.steps = c.n[ctd::kCntSteps];
+    s.e_emitted_kev = c.e_emitted;
+    s.e_escaped_kev = c.e_escaped;
+    s.avg_rsd = res[0];
+    s.paper_sigma_bar = res[1];
+    s.d_max = res[2];
+    s.e_deposited_kev = res[3];
+    double tt = 0.0;
+    for (size_t i = 0; i < n_launch; ++i) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]));
+        tt += ms * 1e-3;
+    }
+    s.t_transport_s = tt;
+    s.transport_launches = static_cast<int>(n_launch);
+    s.t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0_wall;
+    return CTD_OK;
+}
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ctd_last_error(void) { return g_error.c_str(); }
+
+int ctd_abi_version(void) { return CTD_ABI_VERSION; }
+
+int ctd_create(ctd_ctx **out, const ctd_options *opt)
+{
+    g_error.clear();
+    if (!out) return fail(CTD_EINVAL, "null output pointer");
+    *out = nullptr;
+    std::unique_ptr<ctd_ctx> ctx(new ctd_ctx());
+    if (opt) {
+        ctx->device = opt->device;
+        if (opt->blocks_per_sm > 0) ctx->blocks_per_sm = opt->blocks_per_sm;
+        if (opt->threads_per_block > 0) ctx->threads = opt->threads_per_block;
+        if (opt->chunk > 0) ctx->chunk = opt->chunk;
+    }
+    if (ctx->threads % 32 != 0 || ctx->threads > 256) return fail(CTD_EINVAL, "threads_per_block must be a multiple of 32 and at most 256");
+    if (ctx->blocks_per_sm > 64) return fail(CTD_EINVAL, "blocks_per_sm at most 64");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (ctx->device < 0 || ctx->device >= ndev) return fail(CTD_EINVAL, "device %d out of range (%d devices)", ctx->device, ndev);
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (opt && opt->stream) {
+        ctx->stream = static_cast<cudaStream_t>(opt->stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    *out = ctx.release();
+    return CTD_OK;
+}
+
+int ctd_destroy(ctd_ctx *ctx)
+{
+    if (!ctx) return CTD_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->phantoms.clear();
+    for (auto e : ctx->events) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return CTD_OK;
+}
+
+int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz, const uint8_t *mat,
+                       const float *density, int n_mat, const ctd_material *mats, ctd_phantom *out)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    if (!out || !mat || !density || !mats) return fail(CTD_EINVAL, "null pointer argument");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(CTD_EINVAL, "voxel counts must be positive");
+    if (!(dx > 0 && dy > 0 && dz > 0)) return fail(CTD_EINVAL, "voxel sizes must be positive");
+    if (n_mat <= 0 || n_mat > 255) return fail(CTD_EINVAL, "n_mat must be 1..255");
+    for (int m = 0; m < n_mat; ++m)
+        if (!(mats[m].z_over_a > 0 && mats[m].a_mol > 0 && mats[m].z_eff > 0))
+            return fail(CTD_EINVAL, "material %d has non-positive parameters", m);
+    const size_t nvox = static_cast<size_t>(nx) * ny * nz;
+    if (nvox > (static_cast<size_t>(1) << 40)) return fail(CTD_EINVAL, "phantom too large");
+    std::unique_ptr<Phantom> P(new Phantom());
+    P->nx = nx; P->ny = ny; P->nz = nz;
+    P->dx = dx; P->dy = dy; P->dz = dz;
+    P->nvox = nvox;
+    P->mats.assign(mats, mats + n_mat);
+    P->rho_max.assign(n_mat, 0.0);
+    P->present.assign(n_mat, 0);
+    for (size_t v = 0; v < nvox; ++v) {
+        const int m = mat[v];
+        const double r = density[v];
+        if (m >= n_mat) return fail(CTD_EINVAL, "voxel %zu has material %d >= n_mat", v, m);
+        if (!(r >= 0.0) || !std::isfinite(r)) return fail(CTD_EINVAL, "voxel %zu has an invalid density", v);
+        if (!P->present[m] || r > P->rho_max[m]) P->rho_max[m] = r;
+        P->present[m] = 1;
+    }
+    P->phys.e_min_kev = 1;
+    P->phys.e_max_kev = 150;
+    P->phys.n_zeta = 1024;
+    P->phys.majorant_scale = 1.0;
+    P->phys.mode = CTD_MODE_FULL;
+    P->phys.max_real = 0;
+    if ((rc = P->mat.ensure(nvox)) || (rc = P->rho.ensure(nvox))) return rc;
+    CK(cudaMemcpyAsync(P->mat.p, mat, nvox, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P->rho.p, density, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int id = ctx->next_id++;
+    ctx->phantoms[id] = std::move(P);
+    *out = id;
+    return CTD_OK;
+}
+
+int ctd_destroy_phantom(ctd_ctx *ctx, ctd_phantom ph)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    auto it = ctx->phantoms.find(ph);
+    if (it == ctx->phantoms.end()) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->phantoms.erase(it);
+    return CTD_OK;
+}
+
+int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!phys) return fail(CTD_EINVAL, "null physics");
+    if (phys->e_min_kev < 1 || phys->e_max_kev <= phys->e_min_kev || phys->e_max_kev > 100000)
+        return fail(CTD_EINVAL, "node grid must satisfy 1 <= e_min < e_max");
+    if (phys->n_zeta < 2 || phys->n_zeta > (1 << 20)) return fail(CTD_EINVAL, "n_zeta must be 2..2^20");
+    if (!(phys->majorant_scale >= 1.0) || !std::isfinite(phys->majorant_scale))
+        return fail(CTD_EINVAL, "majorant_scale must be >= 1");
+    if (phys->mode != CTD_MODE_FULL && phys->mode != CTD_MODE_MAX_REAL) return fail(CTD_EINVAL, "unknown mode");
+    if (phys->mode == CTD_MODE_MAX_REAL && phys->max_real < 1) return fail(CTD_EINVAL, "max_real must be >= 1");
+    P->phys = *phys;
+    P->tables_ok = false;
+    return CTD_OK;
+}
+
+int ctd_set_source(ctd_ctx *ctx, ctd_phantom ph, const ctd_source *src)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!src) return fail(CTD_EINVAL, "null source");
+    if (src->kind != CTD_SRC_STATIC && src->kind != CTD_SRC_ARC) return fail(CTD_EINVAL, "unknown source kind");
+    if (!(src->sad_cm > 0) || !(src->u_hi_cm >= src->u_lo_cm) || !(src->v_hi_cm >= src->v_lo_cm))
+        return fail(CTD_EINVAL, "source distance must be positive and field bounds ordered");
+    const double hx = P->nx * P->dx / 2.0, hy = P->ny * P->dy / 2.0, hz = P->nz * P->dz / 2.0;
+    if (src->kind == CTD_SRC_STATIC && !(src->sad_cm > hz))
+        return fail(CTD_EINVAL, "static source must lie outside the phantom");
+    if (src->kind == CTD_SRC_ARC && !(src->sad_cm > std::sqrt(hx * hx + hy * hy)))
+        return fail(CTD_EINVAL, "arc radius must clear the phantom");
+    const int np = src->kind == CTD_SRC_ARC && !src->continuous ? src->n_proj : 1;
+    if (src->kind == CTD_SRC_ARC && !src->continuous && (src->n_proj < 1 || src->n_proj > (1 << 24)))
+        return fail(CTD_EINVAL, "n_proj must be 1..2^24");
+    std::vector<float> tab(2 * np);
+    for (int k = 0; k < np; ++k) {
+        // projection angles b_k = arc0 + (arc1 - arc0) k / n_proj
+        const double b = src->arc0_rad + (src->arc1_rad - src->arc0_rad) * static_cast<double>(k) / static_cast<double>(np);
+        tab[k] = static_cast<float>(std::cos(b));
+        tab[np + k] = static_cast<float>(std::sin(b));
+    }
+    if ((rc = P->proj.ensure(tab.size()))) return rc;
+    CK(cudaMemcpyAsync(P->proj.p, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    P->src = *src;
+    P->src.n_proj = np;
+    P->has_src = true;
+    return CTD_OK;
+}
+
+int ctd_set_spectrum(ctd_ctx *ctx, ctd_phantom ph, const double *e_lo, const double *e_hi, const double *w, int nbins)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!e_lo || !e_hi || !w || nbins <= 0 || nbins > 100000) return fail(CTD_EINVAL, "bad spectrum arrays");
+    double total = 0.0;
+    for (int j = 0; j < nbins; ++j) {
+        if (!(e_hi[j] >= e_lo[j]) || !(e_lo[j] > 0) || !(w[j] >= 0) || !std::isfinite(w[j]) || !std::isfinite(e_hi[j]))
+            return fail(CTD_EINVAL, "spectrum bin %d is invalid", j);
+        total += w[j];
+    }
+    if (!(total > 0)) return fail(CTD_EINVAL, "spectrum weights sum to zero");
+    P->e_lo.assign(e_lo, e_lo + nbins);
+    P->e_hi.assign(e_hi, e_hi + nbins);
+    P->w.assign(w, w + nbins);
+    std::vector<float> b(2 * nbins);
+    for (int j = 0; j < nbins; ++j) {
+        b[j] = static_cast<float>(e_lo[j]);
+        b[nbins + j] = static_cast<float>(e_hi[j]);
+    }
+    if ((rc = P->bins.ensure(b.size()))) return rc;
+    CK(cudaMemcpyAsync(P->bins.p, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    P->alloc_n = ~0ull;
+    P->alloc_nb = -1;
+    P->has_spec = true;
+    return CTD_OK;
+}
+
+int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (n_batches < 2 || static_cast<uint64_t>(n_batches) > n_histories)
+        return fail(CTD_EINVAL, "need 2 <= n_batches <= n_histories");
+    const double t0 = now_s();
+    if ((rc = prepare_run(ctx, *P, n_histories, n_batches))) return rc;
+    P->have_result = false;
+    const size_t nv = P->nvox;
+    CK(cudaMemsetAsync(P->tally.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->sum_d.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+    ctd::TransportParams T;
+    fill_params(ctx, *P, seed, T);
+    const uint64_t n_lo = n_histories / n_batches, rem = n_histories % n_batches;
+    const double vol = P->dx * P->dy * P->dz;
+    uint64_t h = 0;
+    for (int b = 0; b < n_batches; ++b) {
+        const uint64_t nb = static_cast<uint64_t>(b) < rem ? n_lo + 1 : n_lo;
+        const int which = static_cast<uint64_t>(b) < rem ? 0 : 1;
+        if ((rc = transport(ctx, *P, T, which, h, 0, nb, P->tally.p, b))) return rc;
+        // d = E / (m n_b) with m = rho V / 1000 kg
+        const double scale = ctd::kKevToJ * 1000.0 / (vol * static_cast<double>(nb));
+        CKS(ctd::launch_fold(P->tally.p, P->rho.p, P->sum_d.p, P->sum_d2.p, P->edep.p, nv, scale, ctx->stream));
+        h += nb;
+    }
+    CKS(ctd::launch_finalize(P->sum_d.p, P->sum_d2.p, n_batches, P->dose.p, P->sd.p, nv, ctx->stream));
+    CKS(ctd::launch_rsd(P->dose.p, P->sd.p, P->rho.p, nv, P->partials.p, kRsdParts, P->result.p, ctx->stream));
+    CKS(ctd::launch_sum(P->edep.p, nv, P->partials.p + 5 * kRsdParts, kRsdParts, P->result.p + 3, ctx->stream));
+    if ((rc = collect(ctx, *P, n_batches, t0))) return rc;
+    P->stats.histories = n_histories;
+    P->stats.n_batches = n_batches;
+    P->have_result = true;
+    return CTD_OK;
+}
+
+int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches, uint64_t h_begin,
+                  uint64_t h_end, int clear)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (n_batches < 1 || static_cast<uint64_t>(n_batches) > n_histories)
+        return fail(CTD_EINVAL, "need 1 <= n_batches <= n_histories");
+    if (h_begin > h_end || h_end > n_histories) return fail(CTD_EINVAL, "history range outside [0, n_histories]");
+    const double t0 = now_s();
+    if ((rc = prepare_run(ctx, *P, n_histories, n_batches))) return rc;
+    const size_t nv = P->nvox;
+    if (clear) {
+        CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+    }
+    P->have_result = false;
+    ctd::TransportParams T;
+    fill_params(ctx, *P, seed, T);
+    const uint64_t n_lo = n_histories / n_batches, rem = n_histories % n_batches;
+    uint64_t h = 0;
+    size_t launches = 0;
+    for (int b = 0; b < n_batches; ++b) {
+        const uint64_t nb = static_cast<uint64_t>(b) < rem ? n_lo + 1 : n_lo;
+        const uint64_t lo = h_begin > h ? h_begin : h, hi = h_end < h + nb ? h_end : h + nb;
+        if (lo < hi) {
+            if ((rc = transport(ctx, *P, T, static_cast<uint64_t>(b) < rem ? 0 : 1, h, lo - h, hi - h, P->edep.p, launches)))
+                return rc;
+            ++launches;
+        }
+        h += nb;
+    }
+    CK(cudaMemsetAsync(P->result.p, 0, 3 * sizeof(double), ctx->stream));
+    CKS(ctd::launch_sum(P->edep.p, nv, P->partials.p + 5 * kRsdParts, kRsdParts, P->result.p + 3, ctx->stream));
+    if ((rc = collect(ctx, *P, launches, t0))) return rc;
+    P->stats.histories = h_end - h_begin;
+    P->stats.n_batches = n_batches;
+    return CTD_OK;
+}
+
+int ctd_get_dose_and_stddev(ctd_ctx *ctx, ctd_phantom ph, double *dose, double *stddev, size_t nvox,
+                            ctd_run_stats *stats)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if ((dose || stddev) && !P->have_result) return fail(CTD_EINVAL, "no completed ctd_run on this phantom");
+    if ((dose || stddev) && nvox != P->nvox) return fail(CTD_EINVAL, "nvox %zu != phantom's %zu", nvox, P->nvox);
+    if (dose) CK(cudaMemcpyAsync(dose, P->dose.p, nvox * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (stddev) CK(cudaMemcpyAsync(stddev, P->sd.p, nvox * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (stats) *stats = P->stats;
+    return CTD_OK;
+}
+
+int ctd_get_edep(ctd_ctx *ctx, ctd_phantom ph, double *edep_kev, size_t nvox)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!edep_kev || nvox != P->nvox) return fail(CTD_EINVAL, "edep buffer must hold the phantom's voxels");
+    if (!P->edep.p) return fail(CTD_EINVAL, "nothing has run on this phantom");
+    CK(cudaMemcpyAsync(edep_kev, P->edep.p, nvox * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return CTD_OK;
+}
+
+int ctd_get_tables(ctd_ctx *ctx, ctd_phantom ph, int *n_e, int *n_zeta, int *n_mat, double *mu_cum, double *mu_max,
+                   double *c_surf, double *r_surf)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if ((rc = build_tables(ctx, *P))) return rc;
+    const int nm = static_cast<int>(P->mats.size());
+    if (n_e) *n_e = P->n_e;
+    if (n_zeta) *n_zeta = P->phys.n_zeta;
+    if (n_mat) *n_mat = nm;
+    if (mu_cum)
+        for (size_t i = 0; i < static_cast<size_t>(nm) * P->n_e; ++i)
+            for (int c = 0; c < 3; ++c) mu_cum[i * 3 + c] = P->h_tab[i * 4 + c];
+    if (mu_max)
+        for (int j = 0; j < P->n_e; ++j) mu_max[j] = P->h_mm[j];
+    if (c_surf)
+        for (size_t i = 0; i < P->h_cs.size(); ++i) c_surf[i] = P->h_cs[i];
+    if (r_surf)
+        for (size_t i = 0; i < P->h_rs.size(); ++i) r_surf[i] = P->h_rs[i];
+    return CTD_OK;
+}
+
+int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e_kev, uint64_t seed, uint64_t n,
+                  double *out)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!out && n) return fail(CTD_EINVAL, "null output");
+    if (kind != 0 && kind != 1) return fail(CTD_EINVAL, "kind is 0 (Compton) or 1 (Rayleigh)");
+    if (material < 0 || material >= static_cast<int>(P->mats.size())) return fail(CTD_EINVAL, "material out of range");
+    if (!(e_kev >= P->phys.e_min_kev && e_kev <= P->phys.e_max_kev)) return fail(CTD_EINVAL, "energy outside the node grid");
+    if ((rc = build_tables(ctx, *P))) return rc;
+    if (n == 0) return CTD_OK;
+    DevBuf<double> buf;
+    if ((rc = buf.ensure(n))) return rc;
+    const float *surf = kind == 0 ? P->cs.p : P->rs.p + static_cast<size_t>(material) * P->n_e * P->phys.n_zeta;
+    CKS(ctd::launch_sample_mu(surf, P->phys.n_zeta, P->n_e, P->phys.e_min_kev, static_cast<float>(e_kev), seed, n,
+                              buf.p, ctx->stream));
+    CK(cudaMemcpyAsync(out, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return CTD_OK;
+}
+
+int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    if (fn != 0 && fn != 1) return fail(CTD_EINVAL, "fn is 0 (log) or 1 (sincos of 2 pi x)");
+    if (n == 0) return CTD_OK;
+    if (!x || !out) return fail(CTD_EINVAL, "null buffer");
+    DevBuf<float> bx, bo;
+    const size_t no = fn == 0 ? n : 2 * n;
+    if ((rc = bx.ensure(n)) || (rc = bo.ensure(no))) return rc;
+    CK(cudaMemcpyAsync(bx.p, x, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CKS(ctd::launch_eval_math(fn, bx.p, bo.p, n, ctx->stream));
+    CK(cudaMemcpyAsync(out, bo.p, no * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return CTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// ctd_internal.h -- internal declarations of the dose engine library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ctd.h"
+
+namespace ctd {
+
+// physical constants (CODATA 2018)
+constexpr double kMec2 = 510.99895;             // electron rest energy, keV
+constexpr double kR0 = 2.8179403262e-13;        // classical electron radius, cm
+constexpr double kNA = 6.02214076e23;           // Avogadro, 1/mol
+constexpr double kHc = 12.398419843320026;      // h c, keV Angstrom
+constexpr double kPi = 3.141592653589793;
+constexpr double kMicrobarn = 1.0e-30;          // cm^2
+constexpr double kBarn = 1.0e-24;               // cm^2
+constexpr double kPeCoef = 1.0e-2;              // photoelectric coefficient, microbarn
+constexpr double kRayCoef = 1.565e-5;           // Rayleigh coefficient, barn MeV^2
+constexpr double kKevToJ = 1.602176634e-16;
+constexpr int kCdfIntervals = 20000;            // mu intervals of the numeric cdf
+
+// ---- host physics (ctd_physics.cpp) ----
+double sigma_kn(double e_kev);
+double mu_pe(const ctd_material &m, double e_kev);
+double mu_compton(const ctd_material &m, double e_kev);
+double mu_rayleigh(const ctd_material &m, double e_kev);
+
+// Node tables: cum[(m*n_e + j)*3 + c] cumulative mass attenuation; mmax[j] majorant.
+void build_tables(const std::vector<ctd_material> &mats, const std::vector<double> &rho_max,
+                  const std::vector<int> &present, int e_min, int n_e, double scale,
+                  std::vector<double> &cum, std::vector<double> &mmax);
+// Inverse-cdf surface rows for node energies e_min..e_min+n_e-1: kind 0 Klein-Nishina, 1 Rayleigh.
+void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out);
+// Largest-remainder allocation; false if the weights are unusable.
+bool allocate(uint64_t n, const std::vector<double> &w, std::vector<uint64_t> &out);
+
+// ---- device-side parameter block of one transport launch ----
+struct DeviceCounts {
+    unsigned long long n[10];   // pe, compton, rayleigh, fictitious, escaped, missed, cutoff, terminated, aborted, steps
+    double e_emitted, e_escaped;
+};
+
+enum { kCntPe = 0, kCntCompton, kCntRayleigh, kCntFict, kCntEscaped, kCntMissed, kCntCutoff,
+       kCntTerminated, kCntAborted, kCntSteps };
+
+struct TransportParams {
+    const uint8_t *mat;
+    const float *rho;
+    const float *tab;        // [n_mat][n_e][4]: c1, c2, c3, 0 (cm^2/g)
+    const float *mmax;       // [n_e] 1/cm
+    const float *csurf;      // [n_e][n_zeta]
+    const float *rsurf;      // [n_mat][n_e][n_zeta]
+    const uint64_t *pref;    // [nbins+1] bin starts inside the batch
+    const float *bin_lo;     // [nbins]
+    const float *bin_hi;     // [nbins]
+    const float *cb;         // [n_proj]
+    const float *sb;         // [n_proj]
+    double *tally;           // [nvox] keV
+    unsigned long long *work;   // claim counter over [local_begin, local_end)
+    DeviceCounts *counts;
+    uint64_t seed;
+    uint64_t h_base;         // global index of local index 0 (first history of the batch)
+    uint64_t local_begin, local_end;
+    int nbins;
+    int nx, ny, nz;
+    float bx0, by0, bz0, bx1, by1, bz1;
+    float ix, iy, iz;
+    int n_mat, n_e, n_zeta, e_min;
+    int src_kind, n_proj, continuous;
+    float D, D2, ulo, uw, vlo, vw, a0t, awt;
+    int mode, max_real;
+    int chunk;
+};
+
+// launches (ctd_transport.cu / ctd_stats.cu)
+int launch_transport(const TransportParams &p, int grid, int block, size_t smem, void *stream);
+size_t transport_smem_bytes(int n_mat, int n_e);
+int launch_fold(double *tally, const float *rho, double *sum_d, double *sum_d2, double *edep, size_t nvox,
+                double scale, void *stream);
+int launch_finalize(const double *sum_d, const double *sum_d2, int nb, double *dose, double *sd, size_t nvox,
+                    void *stream);
+int launch_rsd(const double *dose, const double *sd, const float *rho, size_t nvox, double *partials,
+               int n_parts, double *result, void *stream);
+int launch_sample_mu(const float *surf, int n_zeta, int n_e, int e_min, float e, uint64_t seed, uint64_t n,
+                     double *out, void *stream);
+int launch_eval_math(int fn, const float *x, float *out, size_t n, void *stream);
+int launch_sum(const double *x, size_t n, double *partials, int n_parts, double *result, void *stream);
+
+}  // namespace ctd

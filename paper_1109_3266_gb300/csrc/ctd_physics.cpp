@@ -1,0 +1,176 @@
+// ctd_physics.cpp -- host set-up of the transport: attenuation node tables, the
+// Woodcock majorant, the R and C sampling surfaces and the stratified spectrum
+// allocation.  Compiled with -ffp-contract=off: the binary64 values are rounded
+// to binary32 for the device and must not depend on the host's FMA contraction.
+#include <algorithm>
+#include <cmath>
+
+#include "ctd_internal.h"
+
+namespace ctd {
+
+// Klein-Nishina total cross section per electron in cm^2 (Eq. 2 with S = 1
+// integrated over the sphere), k = E / m_e c^2.
+double sigma_kn(double e_kev)
+{
+    const double k = e_kev / kMec2;
+    const double a = 1.0 + 2.0 * k;
+    const double l = std::log1p(2.0 * k);
+    const double t1 = ((1.0 + k) / (k * k)) * ((2.0 * (1.0 + k)) / a - l / k);
+    const double t2 = l / (2.0 * k);
+    const double t3 = (1.0 + 3.0 * k) / (a * a);
+    return 2.0 * kPi * kR0 * kR0 * ((t1 + t2) - t3);
+}
+
+// Incoherent scattering on free electrons: electrons per gram times sigma_KN (cm^2/g).
+double mu_compton(const ctd_material &m, double e_kev)
+{
+    return (kNA * m.z_over_a) * sigma_kn(e_kev);
+}
+
+// Photoelectric absorption, 1e-2 Z^4 / E_MeV^3 microbarn per formula unit (cm^2/g).
+double mu_pe(const ctd_material &m, double e_kev)
+{
+    const double em = e_kev / 1000.0;
+    const double z2 = m.z_eff * m.z_eff;
+    const double sigma = kPeCoef * (z2 * z2) / (em * em * em);
+    return ((sigma * kMicrobarn) * kNA) / m.a_mol;
+}
+
+// Rayleigh scattering, 1.565e-5 Z^2 / E_MeV^2 barn per formula unit (cm^2/g).
+double mu_rayleigh(const ctd_material &m, double e_kev)
+{
+    const double em = e_kev / 1000.0;
+    const double z2 = m.z_eff * m.z_eff;
+    const double sigma = kRayCoef * z2 / (em * em);
+    return ((sigma * kBarn) * kNA) / m.a_mol;
+}
+
+void build_tables(const std::vector<ctd_material> &mats, const std::vector<double> &rho_max,
+                  const std::vector<int> &present, int e_min, int n_e, double scale,
+                  std::vector<double> &cum, std::vector<double> &mmax)
+{
+    const size_t nm = mats.size();
+    cum.assign(nm * n_e * 3, 0.0);
+    mmax.assign(n_e, 0.0);
+    for (size_t m = 0; m < nm; ++m) {
+        for (int j = 0; j < n_e; ++j) {
+            const double e = static_cast<double>(e_min + j);
+            const double pe = mu_pe(mats[m], e);
+            const double c = mu_compton(mats[m], e);
+            const double r = mu_rayleigh(mats[m], e);
+            double *dst = &cum[(m * n_e + j) * 3];
+            dst[0] = pe;
+            dst[1] = pe + c;
+            dst[2] = (pe + c) + r;
+        }
+    }
+    // mu_max(E): the largest total attenuation anywhere in the volume
+    for (int j = 0; j < n_e; ++j) {
+        double best = 0.0;
+        for (size_t m = 0; m < nm; ++m) {
+            if (!present[m]) continue;
+            const double v = rho_max[m] * cum[(m * n_e + j) * 3 + 2];
+            if (v > best) best = v;
+        }
+        mmax[j] = scale * best;
+    }
+}
+
+namespace {
+
+// unnormalised polar-cosine densities of Eq. 2 (S = 1) and Eq. 1 with F^2 = exp(-q^2/q0^2)
+inline double density_kn(double k, double mu)
+{
+    const double e = 1.0 / (1.0 + k * (1.0 - mu));
+    return (e * e) * ((e + 1.0 / e) - (1.0 - mu * mu));
+}
+
+inline double density_rayleigh(double a, double mu)
+{
+    if (a <= 0.0) return 1.0 + mu * mu;
+    return (1.0 + mu * mu) * std::exp(-a * (1.0 - mu));
+}
+
+inline double grid_mu(int n)
+{
+    return static_cast<double>(2 * n - kCdfIntervals) / static_cast<double>(kCdfIntervals);
+}
+
+}  // namespace
+
+void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out)
+{
+    const int M = kCdfIntervals;
+    std::vector<double> pdf(M + 1), cdf(M + 1);
+    for (int j = 0; j < n_e; ++j) {
+        const double e = static_cast<double>(e_min + j);
+        const double k = e / kMec2;
+        const double kr = e / kHc;
+        const double a = q0 > 0.0 ? (2.0 * kr * kr) / (q0 * q0) : 0.0;
+        for (int n = 0; n <= M; ++n) pdf[n] = kind == 0 ? density_kn(k, grid_mu(n)) : density_rayleigh(a, grid_mu(n));
+        // cumulative trapezoid without the common factor h/2
+        cdf[0] = 0.0;
+        for (int n = 1; n <= M; ++n) cdf[n] = cdf[n - 1] + (pdf[n - 1] + pdf[n]);
+        double *row = out + static_cast<size_t>(j) * n_zeta;
+        const double total = cdf[M];
+        int n = 0;
+        row[0] = -1.0;
+        for (int i = 1; i < n_zeta - 1; ++i) {
+            const double target = (static_cast<double>(i) / static_cast<double>(n_zeta - 1)) * total;
+            while (n < M - 1 && cdf[n + 1] <= target) ++n;
+            const double m0 = grid_mu(n), m1 = grid_mu(n + 1);
+            row[i] = m0 + ((target - cdf[n]) / (cdf[n + 1] - cdf[n])) * (m1 - m0);
+        }
+        row[n_zeta - 1] = 1.0;
+    }
+}
+
+bool allocate(uint64_t n, const std::vector<double> &w, std::vector<uint64_t> &out)
+{
+    const int nb = static_cast<int>(w.size());
+    if (nb <= 0) return false;
+    double total = 0.0;
+    for (double x : w) {
+        if (!(x >= 0.0)) return false;
+        total += x;
+    }
+    if (!(total > 0.0)) return false;
+    out.assign(nb, 0);
+    std::vector<double> frac(nb);
+    uint64_t given = 0;
+    for (int j = 0; j < nb; ++j) {
+        const double q = static_cast<double>(n) * w[j] / total;
+        const double f = std::floor(q);
+        out[j] = static_cast<uint64_t>(f);
+        frac[j] = q - f;
+        given += out[j];
+    }
+    // remainder: largest fractional part first, ties to the lower bin, none to empty bins
+    while (given < n) {
+        int pick = -1;
+        for (int j = 0; j < nb; ++j) {
+            if (w[j] <= 0.0) continue;
+            if (pick < 0 || frac[j] > frac[pick]) pick = j;
+        }
+        if (pick < 0) break;
+        out[pick] += 1;
+        frac[pick] = -1.0;
+        ++given;
+    }
+    // rounding of q can push the floors past n: take back from the smallest fractions
+    while (given > n) {
+        int pick = -1;
+        for (int j = nb - 1; j >= 0; --j) {
+            if (out[j] == 0) continue;
+            if (pick < 0 || frac[j] < frac[pick]) pick = j;
+        }
+        if (pick < 0) break;
+        out[pick] -= 1;
+        frac[pick] = 2.0;
+        --given;
+    }
+    return given == n;
+}
+
+}  // namespace ctd

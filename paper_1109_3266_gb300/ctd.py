@@ -1,0 +1,230 @@
+"""Python binding of the dose engine's C ABI (include/ctd.h).
+
+Argument marshalling only: every step of the transport runs in the CUDA
+library libctd.so, built in-tree by paper_1109_3266_gb300.build.  The
+functions keep the C names.  If the library is missing, loading raises;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libctd.so")
+
+CTD_OK = 0
+STATUS = {0: "CTD_OK", 1: "CTD_EINVAL", 2: "CTD_ENOMEM", 3: "CTD_ECUDA", 4: "CTD_EBUSY", 5: "CTD_ETIMEOUT",
+          6: "CTD_ECANCELLED", 7: "CTD_ENOTFOUND"}
+CTD_SRC_STATIC, CTD_SRC_ARC = 0, 1
+CTD_MODE_FULL, CTD_MODE_MAX_REAL = 0, 1
+
+
+class CtdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ctd_options(C.Structure):
+    _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("blocks_per_sm", C.c_int),
+                ("threads_per_block", C.c_int), ("chunk", C.c_int)]
+
+
+class ctd_material(C.Structure):
+    _fields_ = [("z_over_a", C.c_double), ("a_mol", C.c_double), ("z_eff", C.c_double), ("q0", C.c_double)]
+
+
+class ctd_source(C.Structure):
+    _fields_ = [("kind", C.c_int), ("sad_cm", C.c_double), ("u_lo_cm", C.c_double), ("u_hi_cm", C.c_double),
+                ("v_lo_cm", C.c_double), ("v_hi_cm", C.c_double), ("n_proj", C.c_int), ("arc0_rad", C.c_double),
+                ("arc1_rad", C.c_double), ("continuous", C.c_int)]
+
+
+class ctd_physics(C.Structure):
+    _fields_ = [("e_min_kev", C.c_int), ("e_max_kev", C.c_int), ("n_zeta", C.c_int), ("majorant_scale", C.c_double),
+                ("mode", C.c_int), ("max_real", C.c_int)]
+
+
+class ctd_run_stats(C.Structure):
+    _fields_ = [("histories", C.c_uint64), ("n_batches", C.c_int)] + \
+               [(n, C.c_uint64) for n in ("pe", "compton", "rayleigh", "fictitious", "escaped", "missed", "cutoff",
+                                          "terminated", "aborted", "steps")] + \
+               [(n, C.c_double) for n in ("e_emitted_kev", "e_escaped_kev", "e_deposited_kev", "avg_rsd",
+                                          "paper_sigma_bar", "d_max", "t_total_s", "t_transport_s")] + \
+               [("transport_launches", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise CtdError(3, f"CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, dp, fp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)
+        L.ctd_last_error.restype = C.c_char_p
+        L.ctd_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(ctd_options)]
+        L.ctd_destroy.argtypes = [P]
+        L.ctd_create_phantom.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                         C.POINTER(C.c_uint8), fp, C.c_int, C.POINTER(ctd_material),
+                                         C.POINTER(C.c_int32)]
+        L.ctd_destroy_phantom.argtypes = [P, C.c_int32]
+        L.ctd_set_physics.argtypes = [P, C.c_int32, C.POINTER(ctd_physics)]
+        L.ctd_set_source.argtypes = [P, C.c_int32, C.POINTER(ctd_source)]
+        L.ctd_set_spectrum.argtypes = [P, C.c_int32, dp, dp, dp, C.c_int]
+        L.ctd_run.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int]
+        L.ctd_run_range.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]
+        L.ctd_get_dose_and_stddev.argtypes = [P, C.c_int32, dp, dp, C.c_size_t, C.POINTER(ctd_run_stats)]
+        L.ctd_get_edep.argtypes = [P, C.c_int32, dp, C.c_size_t]
+        L.ctd_get_tables.argtypes = [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     dp, dp, dp, dp]
+        L.ctd_sample_mu.argtypes = [P, C.c_int32, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint64, dp]
+        L.ctd_eval_math.argtypes = [P, C.c_int, fp, fp, C.c_size_t]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != CTD_OK:
+        raise CtdError(rc, lib().ctd_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# --------------------------------------------------------------------------- C names
+def ctd_create(device=0, stream=None, blocks_per_sm=0, threads_per_block=0, chunk=0):
+    """Context handle.  stream: a CUDA stream handle (int), e.g. torch's current stream."""
+    opt = ctd_options(device, stream or None, blocks_per_sm, threads_per_block, chunk)
+    h = C.c_void_p()
+    _check(lib().ctd_create(C.byref(h), C.byref(opt)))
+    return h
+
+
+def ctd_destroy(ctx):
+    _check(lib().ctd_destroy(ctx))
+
+
+def ctd_create_phantom(ctx, nx, ny, nz, dx, dy, dz, mat, density, materials):
+    """materials: records with z_over_a, a_mol, z_eff, q0."""
+    mat = np.ascontiguousarray(mat, dtype=np.uint8).ravel()
+    density = np.ascontiguousarray(density, dtype=np.float32).ravel()
+    n = nx * ny * nz
+    if mat.size != n or density.size != n:
+        raise CtdError(1, "voxel arrays must hold nx*ny*nz values")
+    ms = (ctd_material * len(materials))(*[ctd_material(m.z_over_a, m.a_mol, m.z_eff, m.q0) for m in materials])
+    out = C.c_int32()
+    _check(lib().ctd_create_phantom(ctx, nx, ny, nz, dx, dy, dz, mat.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                    density.ctypes.data_as(C.POINTER(C.c_float)), len(materials), ms, C.byref(out)))
+    return out.value
+
+
+def ctd_destroy_phantom(ctx, ph):
+    _check(lib().ctd_destroy_phantom(ctx, ph))
+
+
+def ctd_set_physics(ctx, ph, e_min_kev=1, e_max_kev=150, n_zeta=1024, majorant_scale=1.0, mode="full", max_real=0):
+    m = {"full": CTD_MODE_FULL, "max_real": CTD_MODE_MAX_REAL}[mode] if isinstance(mode, str) else int(mode)
+    p = ctd_physics(e_min_kev, e_max_kev, n_zeta, majorant_scale, m, max_real)
+    _check(lib().ctd_set_physics(ctx, ph, C.byref(p)))
+
+
+def ctd_set_source(ctx, ph, kind, sad_cm, u_lo_cm, u_hi_cm, v_lo_cm, v_hi_cm, n_proj=1, arc0_rad=0.0,
+                   arc1_rad=2 * np.pi, continuous=False):
+    k = {"static": CTD_SRC_STATIC, "arc": CTD_SRC_ARC}[kind] if isinstance(kind, str) else int(kind)
+    s = ctd_source(k, sad_cm, u_lo_cm, u_hi_cm, v_lo_cm, v_hi_cm, n_proj, arc0_rad, arc1_rad, int(continuous))
+    _check(lib().ctd_set_source(ctx, ph, C.byref(s)))
+
+
+def ctd_set_spectrum(ctx, ph, e_lo, e_hi, w):
+    e_lo = np.ascontiguousarray(e_lo, dtype=np.float64)
+    e_hi = np.ascontiguousarray(e_hi, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _check(lib().ctd_set_spectrum(ctx, ph, _dp(e_lo), _dp(e_hi), _dp(w), len(w)))
+
+
+def ctd_run(ctx, ph, n_histories, seed, n_batches):
+    _check(lib().ctd_run(ctx, ph, int(n_histories), int(seed), int(n_batches)))
+
+
+def ctd_run_range(ctx, ph, n_histories, seed, n_batches, h_begin, h_end, clear=True):
+    _check(lib().ctd_run_range(ctx, ph, int(n_histories), int(seed), int(n_batches), int(h_begin), int(h_end),
+                               int(bool(clear))))
+
+
+def ctd_get_dose_and_stddev(ctx, ph, nvox, want_arrays=True):
+    """(dose, stddev, stats) -- Gy per history, standard error, stats dict."""
+    st = ctd_run_stats()
+    if want_arrays:
+        dose = np.empty(nvox, dtype=np.float64)
+        sd = np.empty(nvox, dtype=np.float64)
+        _check(lib().ctd_get_dose_and_stddev(ctx, ph, _dp(dose), _dp(sd), nvox, C.byref(st)))
+        return dose, sd, st.as_dict()
+    _check(lib().ctd_get_dose_and_stddev(ctx, ph, None, None, 0, C.byref(st)))
+    return None, None, st.as_dict()
+
+
+def ctd_get_edep(ctx, ph, nvox):
+    out = np.empty(nvox, dtype=np.float64)
+    _check(lib().ctd_get_edep(ctx, ph, _dp(out), nvox))
+    return out
+
+
+def ctd_get_tables(ctx, ph):
+    ne, nz, nm = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().ctd_get_tables(ctx, ph, C.byref(ne), C.byref(nz), C.byref(nm), None, None, None, None))
+    ne, nz, nm = ne.value, nz.value, nm.value
+    cum = np.empty((nm, ne, 3))
+    mm = np.empty(ne)
+    cs = np.empty((ne, nz))
+    rs = np.empty((nm, ne, nz))
+    _check(lib().ctd_get_tables(ctx, ph, None, None, None, _dp(cum), _dp(mm), _dp(cs), _dp(rs)))
+    return cum, mm, cs, rs
+
+
+def ctd_sample_mu(ctx, ph, kind, material, e_kev, seed, n):
+    out = np.empty(n, dtype=np.float64)
+    k = {"compton": 0, "rayleigh": 1}[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().ctd_sample_mu(ctx, ph, k, material, e_kev, seed, n, _dp(out)))
+    return out
+
+
+def ctd_eval_math(ctx, fn, x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(x.size * (1 if fn == 0 else 2), dtype=np.float32)
+    _check(lib().ctd_eval_math(ctx, fn, x.ctypes.data_as(C.POINTER(C.c_float)),
+                               out.ctypes.data_as(C.POINTER(C.c_float)), x.size))
+    return out
+
+
+# --------------------------------------------------------------------------- problem helpers
+def load_problem(ctx, problem, physics=True):
+    """Create the phantom of an inputs.Problem and set its source, spectrum and physics."""
+    ph_ = problem.phantom
+    h = ctd_create_phantom(ctx, ph_.nx, ph_.ny, ph_.nz, ph_.dx, ph_.dy, ph_.dz, ph_.mat, ph_.rho, ph_.materials)
+    s = problem.source
+    ctd_set_source(ctx, h, s.kind, s.sad, s.u_lo, s.u_hi, s.v_lo, s.v_hi, s.n_proj, s.arc0, s.arc1, s.continuous)
+    sp = problem.spectrum
+    ctd_set_spectrum(ctx, h, sp.e_lo, sp.e_hi, sp.w)
+    if physics:
+        p = problem.physics
+        ctd_set_physics(ctx, h, p.e_min, p.e_max, p.n_zeta, p.majorant_scale, p.mode, p.max_real)
+    return h
+
+
+def run_problem(ctx, problem, handle=None):
+    """Run a problem end to end: (dose, stddev, stats, handle)."""
+    h = handle if handle is not None else load_problem(ctx, problem)
+    ctd_run(ctx, h, problem.n_hist, problem.seed, problem.n_batches)
+    dose, sd, st = ctd_get_dose_and_stddev(ctx, h, problem.phantom.nvox)
+    return dose, sd, st, h

@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+- The binary32 elementary functions, tables and surfaces equal the oracle's bit
+  for bit.
+- The device's surface samplers give the same cosines as the oracle's, and
+  those follow Eqs. 1-2.
+- In primary-only mode the integer counts equal the binary32 oracle's exactly.
+  In full transport they also equal it, and the dose agrees with the binary64
+  oracle within 3 combined standard errors for >= 99 % of the voxels above
+  10 % of the maximum, with the total deposit within 0.5 %.
+- At the full sizes of the CBCT-water and head workloads, sampled history
+  ranges match the oracle's per-history tracks, and properties that hold at
+  any size are checked."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1109_3266_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+COUNT_KEYS = ("pe", "compton", "rayleigh", "fictitious", "escaped", "missed", "cutoff", "terminated", "aborted",
+              "steps")
+
+
+@pytest.fixture(scope="module")
+def ctd():
+    from paper_1109_3266_gb300 import build, ctd as binding
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(ctd):
+    c = ctd.ctd_create(device=0)
+    yield c
+    ctd.ctd_destroy(c)
+
+
+def small_cbct(n_hist=200_000, seed=2):
+    return I.cbct_water(n_hist=n_hist, seed=seed, shape=(64, 64, 32), d=0.8)
+
+
+def small_head(n_hist=200_000, seed=3):
+    return I.head(n_hist=n_hist, seed=seed, shape=(64, 64, 40), d=0.4)
+
+
+def assert_counts_equal(st, oc):
+    diff = {k: (st[k], oc[k]) for k in COUNT_KEYS if st[k] != oc[k]}
+    assert not diff, diff
+
+
+def dose_parity(dose, sd, ref, ref_sd, frac=0.99):
+    dmax = ref.max()
+    m = ref > 0.1 * dmax
+    z = np.abs(dose[m] - ref[m]) / np.sqrt(sd[m] ** 2 + ref_sd[m] ** 2 + 1e-300)
+    return float(np.mean(z < 3.0)), int(m.sum())
+
+
+# ----------------------------------------------------------------- elementary functions
+def test_device_log_and_sincos_equal_oracle_on_every_uniform(ctd, ctx, oracle):
+    u = ((2 * np.arange(2 ** 23, dtype=np.float64) + 1) * 2.0 ** -24).astype(np.float32)
+    dev = ctd.ctd_eval_math(ctx, 0, u)
+    assert np.array_equal(dev.view(np.uint32), oracle.log_f32(u).view(np.uint32))
+    dev = ctd.ctd_eval_math(ctx, 1, u).reshape(-1, 2)
+    c, s = oracle.sincos_turns_f32(u)
+    assert np.array_equal(dev[:, 0].view(np.uint32), c.view(np.uint32))
+    assert np.array_equal(dev[:, 1].view(np.uint32), s.view(np.uint32))
+
+
+# ----------------------------------------------------------------- tables
+@pytest.mark.parametrize("make", [lambda: I.tiny_water(1000), lambda: small_head(1000)])
+def test_tables_and_surfaces_equal_oracle_bitwise(ctd, ctx, oracle, make):
+    p = make()
+    h = ctd.load_problem(ctx, p)
+    cum, mm, cs, rs = ctd.ctd_get_tables(ctx, h)
+    s = oracle.Setup(p, 32)
+    ocum, omm = s.tables()
+    ocs, ors = s.surfaces()
+    assert np.array_equal(cum, ocum)
+    assert np.array_equal(mm, omm)
+    assert np.array_equal(cs, ocs)
+    assert np.array_equal(rs, ors)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+# ----------------------------------------------------------------- samplers (Figs. 3-4)
+@pytest.mark.parametrize("kind,e", [("compton", 10.0), ("compton", 60.0), ("rayleigh", 10.0), ("rayleigh", 60.0),
+                                    ("compton", 60.5)])
+def test_device_sampler_matches_oracle_and_eq1_eq2(ctd, ctx, oracle, kind, e):
+    from scipy import stats
+    from test_oracle_sampling import _chi2_equal_prob, cdf_factory
+    p = small_head(1000)
+    h = ctd.load_problem(ctx, p)
+    mat = 3 if kind == "rayleigh" else 0          # brain, q0 = 1
+    n = 2_000_000
+    dev = ctd.ctd_sample_mu(ctx, h, kind, mat, e, 77, n)
+    ref = oracle.Setup(p, 32).sample_mu(kind, mat, e, 200_000, seed=77)
+    assert np.array_equal(dev[:200_000], ref)
+    assert _chi2_equal_prob(dev, cdf_factory(kind, e, 1.0)) > 1e-4
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+# ----------------------------------------------------------------- primary-only counts
+@pytest.mark.parametrize("make", [lambda: I.tiny_water(100_000), lambda: small_head(100_000),
+                                  lambda: small_cbct(100_000)])
+def test_primary_only_counts_bit_exact(ctd, ctx, oracle, make):
+    p = make()
+    p = I.scaled(p, physics=I.Physics(p.physics.e_min, p.physics.e_max, mode="max_real", max_real=1))
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r = oracle.run(p, precision=32)
+    assert_counts_equal(st, r.counts)
+    assert st["histories"] == p.n_hist
+    ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
+    assert np.allclose(ed, r.edep, rtol=1e-12, atol=1e-9)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+# ----------------------------------------------------------------- full transport
+@pytest.mark.parametrize("make", [lambda: I.tiny_water(100_000), lambda: small_head(300_000),
+                                  lambda: small_cbct(300_000)])
+def test_full_transport_matches_oracles(ctd, ctx, oracle, make):
+    p = make()
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r32 = oracle.run(p, precision=32)
+    assert_counts_equal(st, r32.counts)
+    assert np.allclose(dose, r32.dose, rtol=1e-9, atol=1e-30)
+    r64 = oracle.run(p, precision=64)
+    frac, nmask = dose_parity(dose, sd, r64.dose, r64.std)
+    assert nmask > 50 and frac >= 0.99, (frac, nmask)
+    e64 = r64.counts["e_deposited"]
+    assert abs(st["e_deposited_kev"] - e64) <= 0.005 * e64
+    # energy bookkeeping on the device
+    assert abs(st["e_deposited_kev"] + st["e_escaped_kev"] - st["e_emitted_kev"]) <= 1e-9 * st["e_emitted_kev"]
+    # avg RSD as the oracle defines it, from the device's own dose and stddev
+    assert st["avg_rsd"] == pytest.approx(oracle.avg_rsd(dose, sd, p.phantom.rho), rel=1e-9)
+    assert st["paper_sigma_bar"] == pytest.approx(oracle.paper_sigma_bar(dose, sd, p.phantom.rho), rel=1e-9)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_independent_seeds_agree_statistically(ctd, ctx, oracle):
+    p = small_head(400_000)
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r64 = oracle.run(I.scaled(p, seed=99), precision=64)
+    frac, nmask = dose_parity(dose, sd, r64.dose, r64.std)
+    assert frac >= 0.99, (frac, nmask)
+    e64 = r64.counts["e_deposited"] / r64.counts["e_emitted"]
+    eg = st["e_deposited_kev"] / st["e_emitted_kev"]
+    assert abs(eg - e64) < 0.005 * e64
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+@pytest.mark.parametrize("scale", [2.0, 10.0])
+def test_majorant_scale_counts_bit_exact(ctd, ctx, oracle, scale):
+    p = small_head(50_000)
+    p = I.scaled(p, physics=I.Physics(1, 150, majorant_scale=scale))
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r = oracle.run(p, precision=32)
+    assert_counts_equal(st, r.counts)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+# ----------------------------------------------------------------- full-size workloads, sampled
+@pytest.mark.parametrize("make,ranges", [
+    (lambda: I.cbct_water(), [(0, 20_000), (123_456_789, 123_476_789), (1_000_000_000 - 15_000, 1_000_000_000)]),
+    (lambda: I.head(), [(0, 10_000), (1_999_990_000, 2_000_000_000)]),
+])
+def test_full_size_sampled_history_ranges(ctd, ctx, oracle, make, ranges):
+    p = make()
+    h = ctd.load_problem(ctx, p)
+    s32 = oracle.Setup(p, 32)
+    for a, b in ranges:
+        ctd.ctd_run_range(ctx, h, p.n_hist, p.seed, p.n_batches, a, b, clear=True)
+        _, _, st = ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)
+        ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
+        oe, oc = s32.transport(a, b, threads=8)
+        assert_counts_equal(st, oc)
+        assert np.allclose(ed, oe, rtol=1e-12, atol=1e-9)
+        assert abs(st["e_deposited_kev"] + st["e_escaped_kev"] - st["e_emitted_kev"]) <= 1e-9 * st["e_emitted_kev"]
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_full_size_cbct_run_properties(ctd, ctx):
+    # the whole 1e9-history workload in its 10 batches: bookkeeping and end states add up
+    p = I.cbct_water()
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    ends = st["pe"] + st["cutoff"] + st["escaped"] + st["missed"] + st["terminated"] + st["aborted"]
+    assert ends == p.n_hist and st["aborted"] == 0
+    assert abs(st["e_deposited_kev"] + st["e_escaped_kev"] - st["e_emitted_kev"]) <= 1e-9 * st["e_emitted_kev"]
+    assert np.all(dose >= 0) and np.all(sd >= 0)
+    assert 0 < st["avg_rsd"] < 0.5
+    # the spectrum's mean energy is what was emitted
+    sp = p.spectrum
+    mean_e = float(np.sum(sp.w * 0.5 * (sp.e_lo + sp.e_hi)) / sp.w.sum())
+    assert st["e_emitted_kev"] / p.n_hist == pytest.approx(mean_e, rel=1e-3)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+# ----------------------------------------------------------------- edge cases
+def test_edge_cases(ctd, ctx, oracle):
+    # ragged batches and a history count equal to the batch count
+    for n, nb in ((1003, 7), (10, 10), (2, 2)):
+        p = I.tiny_water(n_hist=n, n_batches=nb)
+        dose, sd, st, h = ctd.run_problem(ctx, p)
+        r = oracle.run(p, precision=32, threads=1)
+        assert_counts_equal(st, r.counts)
+        ctd.ctd_destroy_phantom(ctx, h)
+    # a single voxel, a field that misses the phantom, a vacuum phantom
+    one = I.Problem("one", I.uniform_box(1, 1, 1, 2.0, I.WATER), I.static_source(10.0, 0.5, 0.5),
+                    I.spectrum_line(40.0), I.Physics(10, 150), 5000, 5, 4)
+    miss = I.Problem("miss", I.uniform_box(4, 4, 4, 1.0, I.WATER), I.Source("static", 50.0, 20.0, 30.0, 20.0, 30.0),
+                     I.spectrum_line(40.0), I.Physics(10, 150), 5000, 5, 4)
+    vac = I.Problem("vac", I.uniform_box(4, 4, 4, 1.0, I.WATER, density=0.0), I.static_source(50.0, 1.0, 1.0),
+                    I.spectrum_line(40.0), I.Physics(10, 150), 5000, 5, 4)
+    for p in (one, miss, vac):
+        dose, sd, st, h = ctd.run_problem(ctx, p)
+        r = oracle.run(p, precision=32, threads=1)
+        assert_counts_equal(st, r.counts)
+        assert np.all(np.isfinite(dose)) and np.all(np.isfinite(sd))
+        ctd.ctd_destroy_phantom(ctx, h)
+    assert st["escaped"] == 5000 and st["steps"] == 5000
+    # an empty range does nothing; bad arguments are refused
+    p = I.tiny_water(1000)
+    h = ctd.load_problem(ctx, p)
+    ctd.ctd_run_range(ctx, h, 1000, 1, 10, 500, 500)
+    assert np.all(ctd.ctd_get_edep(ctx, h, p.phantom.nvox) == 0)
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_run(ctx, h, 1000, 1, 1)
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_run_range(ctx, h, 1000, 1, 10, 10, 2000)
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_set_spectrum(ctx, h, [200.0], [201.0], [1.0]) or ctd.ctd_run(ctx, h, 1000, 1, 10)
+    ctd.ctd_destroy_phantom(ctx, h)
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_destroy_phantom(ctx, h)

@@ -179,6 +179,26 @@ int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e
  * floats; out holds n (fn 0) or 2n (fn 1) host floats. */
 int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n);
 
+/* Allocation-free avg RSD.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the
+ * precision measure, such as code running inside CUDA stream capture (where
+ * cudaMalloc is not permitted) or hosts whose own pool allocator owns all
+ * device memory and forbids library allocations.
+ * It reduces dose and stddev arrays that already live on the device (nvox
+ * doubles each, Gy per history) with densities density_dev (nvox floats) to
+ * the same measures ctd_run reports: result_dev[0] = avg RSD (mean s/D over
+ * D > 0.1 D_max, rho >= 0.1 g/cm^3), [1] = the paper's sigma_bar, [2] = D_max,
+ * written to 3 device doubles, asynchronously on stream (a cudaStream_t; NULL
+ * is the legacy default stream).  No context is needed; it runs on the current
+ * device.  It allocates nothing: its partial sums live in a fixed 160 KB
+ * device array inside the library, which every GPU that loads the library
+ * holds until exit, so nvox may not exceed 67,108,864 (CTD_EINVAL beyond).
+ * The first call on each device looks up that array's device address; make
+ * it before any stream capture.  All calls share the array: a call overwrites
+ * every partial it reads, but calls that overlap on the GPU race on it. */
+int ctd_avg_rsd_noalloc(const double *dose_dev, const double *stddev_dev, const float *density_dev, size_t nvox,
+                        double *result_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

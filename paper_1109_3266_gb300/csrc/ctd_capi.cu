@@ -105,6 +105,10 @@ struct Phantom {
 
 }  // namespace
 
+namespace ctd {
+void set_error(const char *msg) { g_error = msg; }
+}  // namespace ctd
+
 struct ctd_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -23,6 +23,9 @@ constexpr double kRayCoef = 1.565e-5;           // Rayleigh coefficient, barn Me
 constexpr double kKevToJ = 1.602176634e-16;
 constexpr int kCdfIntervals = 20000;            // mu intervals of the numeric cdf
 
+// message returned by ctd_last_error() on the calling thread (ctd_capi.cu)
+void set_error(const char *msg);
+
 // ---- host physics (ctd_physics.cpp) ----
 double sigma_kn(double e_kev);
 double mu_pe(const ctd_material &m, double e_kev);

@@ -89,6 +89,7 @@ def lib():
                                      dp, dp, dp, dp]
         L.ctd_sample_mu.argtypes = [P, C.c_int32, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint64, dp]
         L.ctd_eval_math.argtypes = [P, C.c_int, fp, fp, C.c_size_t]
+        L.ctd_avg_rsd_noalloc.argtypes = [P, P, P, C.c_size_t, P, P]
         _lib = L
     return _lib
 
@@ -205,6 +206,15 @@ def ctd_eval_math(ctx, fn, x):
     _check(lib().ctd_eval_math(ctx, fn, x.ctypes.data_as(C.POINTER(C.c_float)),
                                out.ctypes.data_as(C.POINTER(C.c_float)), x.size))
     return out
+
+
+def ctd_avg_rsd_noalloc(dose_dev, stddev_dev, density_dev, nvox, result_dev, stream=None):
+    """Allocation-free avg RSD of device arrays (integer device addresses, e.g.
+    torch's data_ptr()); writes avg RSD, sigma_bar and D_max to 3 device doubles
+    at result_dev, asynchronously on stream.  For callers that cannot allocate
+    device memory at that point (inside stream capture, or under a host-owned
+    memory pool); it uses a fixed scratch array inside the library instead."""
+    _check(lib().ctd_avg_rsd_noalloc(dose_dev, stddev_dev, density_dev, int(nvox), result_dev, stream or None))
 
 
 # --------------------------------------------------------------------------- problem helpers

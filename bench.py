@@ -214,7 +214,7 @@ def run_ours(args):
     seed = p.seed + 7919 * rank
     nvox = p.phantom.nvox
     ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
-                         threads_per_block=args.threads, chunk=args.chunk)
+                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap)
     h = ctd.load_problem(ctx, p)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
@@ -317,7 +317,8 @@ def run_ours(args):
                        "voxel_cm": p.phantom.dx, "histories_per_step": p.n_hist, "batches": p.n_batches,
                        "kvp": 120 if p.name == "cbct_water" else None, "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (256 MB write outside timed events)",
-                       "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk},
+                       "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk,
+                       "flight_cap": args.flight_cap},
             "sec_to_1pct_avg_rsd": sec_to_1, "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
             "clocks": ck,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -339,6 +340,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--flight-cap", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -45,8 +45,10 @@ typedef struct {
     int device;               /* CUDA device ordinal                                  */
     void *stream;             /* cudaStream_t to launch on; NULL: the context makes one */
     int blocks_per_sm;        /* transport grid = SMs x blocks_per_sm (default 4)     */
-    int threads_per_block;    /* multiple of 32, <= 1024 (default 256)               */
-    int chunk;                /* histories a warp claims per refill (default 64)      */
+    int threads_per_block;    /* multiple of 32, <= 256 (default 256)                */
+    int chunk;                /* histories a warp claims at a time (default 256)      */
+    int flight_cap;           /* Woodcock flights a lane takes in a row, stopping early at a
+                                 real interaction, before its warp moves on (default 4) */
 } ctd_options;
 
 /* Material: the numbers the closed-form cross sections use (Sec. 2.1).

@@ -130,6 +130,22 @@ void or_sincos_turns_f32(float t, float *c, float *s)
     }
 }
 
+/* binary64 -> binary32 by truncating the significand to 23 bits (round toward
+ * zero); magnitudes below 2^-126 give 0. */
+static float or_trunc32(double d)
+{
+    uint64_t b;
+    memcpy(&b, &d, sizeof b);
+    uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    uint32_t ex = (hi >> 20) & 0x7ffu;
+    if (ex < 897u) return 0.0f;
+    uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    uint32_t f = (hi & 0x80000000u) | (((ex - 896u) & 0xffu) << 23) | m;
+    float r;
+    memcpy(&r, &f, sizeof r);
+    return r;
+}
+
 void or_eval_log_f32(const float *u, float *out, size_t n)
 {
     for (size_t i = 0; i < n; ++i) out[i] = or_log_f32(u[i]);

@@ -116,7 +116,8 @@ struct ctd_ctx {
     int num_sms = 0;
     int blocks_per_sm = 4;
     int threads = 256;
-    int chunk = 64;
+    int chunk = 256;
+    int flight_cap = 4;
     std::map<int, std::unique_ptr<Phantom>> phantoms;
     int next_id = 1;
     std::vector<cudaEvent_t> events;
@@ -270,6 +271,7 @@ void fill_params(ctd_ctx *ctx, Phantom &P, uint64_t seed, ctd::TransportParams &
     T.mode = P.phys.mode;
     T.max_real = P.phys.max_real;
     T.chunk = ctx->chunk;
+    T.flight_cap = ctx->flight_cap;
 }
 
 cudaEvent_t event_at(ctd_ctx *ctx, size_t i)
@@ -296,7 +298,8 @@ int transport(ctd_ctx *ctx, Phantom &P, ctd::TransportParams &T, int which_size,
     if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
     CK(cudaEventRecord(e0, ctx->stream));
     const int grid = ctx->num_sms * ctx->blocks_per_sm;
-    CKS(ctd::launch_transport(T, grid, ctx->threads, ctd::transport_smem_bytes(T.n_mat, T.n_e), ctx->stream));
+    CKS(ctd::launch_transport(T, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm,
+                              ctd::transport_smem_bytes(T.n_mat, T.n_e, ctx->threads), ctx->stream));
     CK(cudaEventRecord(e1, ctx->stream));
     return CTD_OK;
 }
@@ -329,8 +332,8 @@ int collect(ctd_ctx *ctx, Phantom &P, size_t n_launch, double t0_wall)
     s.terminated = c.n[ctd::kCntTerminated];
     s.aborted = c.n[ctd::kCntAborted];
     s.steps = c.n[ctd::kCntSteps];
-    s.e_emitted_kev = c.e_emitted;
-    s.e_escaped_kev = c.e_escaped;
+    s.e_emitted_kev = ctd::fixed_kev(c.e_fix[0], c.e_fix[1]);
+    s.e_escaped_kev = ctd::fixed_kev(c.e_fix[2], c.e_fix[3]);
     s.avg_rsd = res[0];
     s.paper_sigma_bar = res[1];
     s.d_max = res[2];
@@ -371,6 +374,7 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
         if (opt->blocks_per_sm > 0) ctx->blocks_per_sm = opt->blocks_per_sm;
         if (opt->threads_per_block > 0) ctx->threads = opt->threads_per_block;
         if (opt->chunk > 0) ctx->chunk = opt->chunk;
+        if (opt->flight_cap > 0) ctx->flight_cap = opt->flight_cap;
     }
     if (ctx->threads % 32 != 0 || ctx->threads > 256) return fail(CTD_EINVAL, "threads_per_block must be a multiple of 32 and at most 256");
     if (ctx->blocks_per_sm > 64) return fail(CTD_EINVAL, "blocks_per_sm at most 64");

@@ -44,8 +44,14 @@ bool allocate(uint64_t n, const std::vector<double> &w, std::vector<uint64_t> &o
 // ---- device-side parameter block of one transport launch ----
 struct DeviceCounts {
     unsigned long long n[10];   // pe, compton, rayleigh, fictitious, escaped, missed, cutoff, terminated, aborted, steps
-    double e_emitted, e_escaped;
+    unsigned long long e_fix[4];  // emitted lo, hi, escaped lo, hi: keV * 2^23 as 128-bit integers
 };
+
+// keV from a 128-bit fixed-point total (lo, hi) in units of 2^-23 keV
+inline double fixed_kev(unsigned long long lo, unsigned long long hi)
+{
+    return static_cast<double>(hi) * 2199023255552.0 + static_cast<double>(lo) * (1.0 / 8388608.0);
+}
 
 enum { kCntPe = 0, kCntCompton, kCntRayleigh, kCntFict, kCntEscaped, kCntMissed, kCntCutoff,
        kCntTerminated, kCntAborted, kCntSteps };
@@ -77,11 +83,12 @@ struct TransportParams {
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
     int mode, max_real;
     int chunk;
+    int flight_cap;          // fictitious flights a lane may take before yielding to the warp
 };
 
 // launches (ctd_transport.cu / ctd_stats.cu)
-int launch_transport(const TransportParams &p, int grid, int block, size_t smem, void *stream);
-size_t transport_smem_bytes(int n_mat, int n_e);
+int launch_transport(const TransportParams &p, int grid, int block, int threads_per_sm, size_t smem, void *stream);
+size_t transport_smem_bytes(int n_mat, int n_e, int threads);
 int launch_fold(double *tally, const float *rho, double *sum_d, double *sum_d2, double *edep, size_t nvox,
                 double scale, void *stream);
 int launch_finalize(const double *sum_d, const double *sum_d2, int nb, double *dose, double *sd, size_t nvox,

@@ -119,15 +119,61 @@ __device__ __forceinline__ void sincos_turns(float t, float &c, float &s)
     }
 }
 
-// Back to unit length: one Newton step for n^-1/2 from 1, in binary64.
+// Exact binary32 -> binary64 widening with integer instructions (GB300's FP64
+// pipe is narrow; this keeps conversions off it).  Zeros keep their sign;
+// subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double(static_cast<int>(u & 0x80000000u), 0);
+    if (ex == 0u || ex == 0xffu) return static_cast<double>(f);
+    const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
+
+// binary64 -> binary32 by truncating the significand to 23 bits (round toward
+// zero); magnitudes below 2^-126 give 0.
+__device__ __forceinline__ float trunc32(double d)
+{
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(d));
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(d));
+    const uint32_t ex = (hi >> 20) & 0x7ffu;
+    if (ex < 897u) return 0.0f;
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float((hi & 0x80000000u) | (((ex - 896u) & 0xffu) << 23) | m);
+}
+
+// Back to unit length after a scatter: the squared norm n2 and the correction
+// e = c - 1 of one Newton step c = 1.5 - 0.5 n2 for 1/sqrt(n2) from 1 are
+// binary64 (the products of widened floats are exact, so the fused forms equal
+// the separately rounded ones); e, truncated to binary32, is applied to each
+// component with one fused multiply-add.
 __device__ __forceinline__ void renorm(float &ux, float &uy, float &uz)
 {
-    const double dx = ux, dy = uy, dz = uz;
-    const double n2 = (dx * dx + dy * dy) + dz * dz;
-    const double c = 1.5 - 0.5 * n2;
-    ux = static_cast<float>(dx * c);
-    uy = static_cast<float>(dy * c);
-    uz = static_cast<float>(dz * c);
+    const double dx = widen(ux), dy = widen(uy), dz = widen(uz);
+    const double n2 = __fma_rn(dz, dz, __fma_rn(dx, dx, __dmul_rn(dy, dy)));
+    const double e = __fma_rn(-0.5, n2, 0.5);
+    const float ef = trunc32(e);
+    ux = __fmaf_rn(ux, ef, ux);
+    uy = __fmaf_rn(uy, ef, uy);
+    uz = __fmaf_rn(uz, ef, uz);
+}
+
+// E 2^23 as an integer: exact for 1 keV <= E < 2^40 keV (every photon energy of
+// the transport is at least the node floor e_min >= 1 keV)
+__device__ __forceinline__ unsigned long long kev_fixed(float e)
+{
+    const uint32_t u = __float_as_uint(e);
+    const int ex = static_cast<int>((u >> 23) & 0xffu) - 127;
+    const unsigned long long m = (u & 0x7fffffu) | 0x800000u;
+    return ex >= 0 ? (m << ex) : (m >> -ex);
+}
+
+// tally deposit of a non-negative binary32 energy into the binary64 grid
+__device__ __forceinline__ void deposit(double *tally, size_t idx, float e)
+{
+    if (e > 0.0f) atomicAdd(tally + idx, widen(e));
 }
 
 // New direction after a scatter of polar cosine mu and azimuth 2 pi tphi.
@@ -195,25 +241,32 @@ struct Photon {
 
 struct LaneCounts {
     uint32_t n[10];
-    double e_emitted, e_escaped;
+    unsigned long long e_emitted, e_escaped;   // keV * 2^23
 };
 
-// Source photon of history h (Secs. 2.2.5-2.2.6).  Returns true if it enters the phantom.
-__device__ __forceinline__ bool source(const TransportParams &P, uint64_t h, uint64_t local, Photon &ph,
-                                       LaneCounts &cnt)
+// Source sampling (Secs. 2.2.5-2.2.6).  Returns true if the photon enters the phantom.
+__device__ __forceinline__ int bin_search(const TransportParams &P, uint64_t local)
 {
-    // 1 keV interval of this history inside its batch
+    // largest bin j with pref[j] <= local
     int lo = 0, hi = P.nbins - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(&P.pref[mid]) <= local) lo = mid;
         else hi = mid - 1;
     }
-    const int bin = lo;
+    return lo;
+}
+
+// Source photon of local history `local` (global index h); `bin` is the 1 keV
+// interval of the warp's claim start, a lower bound for this history's interval.
+__device__ __forceinline__ bool source(const TransportParams &P, uint64_t h, uint64_t local, int bin, Photon &ph,
+                                       LaneCounts &cnt)
+{
+    while (bin < P.nbins - 1 && __ldg(&P.pref[bin + 1]) <= local) ++bin;
     const U4 b0 = block(P.seed, h, 0, kStreamSource);
     const float elo = __ldg(&P.bin_lo[bin]), ehi = __ldg(&P.bin_hi[bin]);
     const float e = elo + (ehi - elo) * uni(b0.x);
-    cnt.e_emitted += static_cast<double>(e);
+    cnt.e_emitted += kev_fixed(e);
     float cb = 1.0f, sb = 0.0f;
     if (P.src_kind == CTD_SRC_ARC) {
         if (P.continuous) {
@@ -241,7 +294,7 @@ __device__ __forceinline__ bool source(const TransportParams &P, uint64_t h, uin
     }
     if (!accepted) {
         cnt.n[kCntAborted]++;
-        cnt.e_escaped += static_cast<double>(e);
+        cnt.e_escaped += kev_fixed(e);
         return false;
     }
     const float inv = 1.0f / sqrtf(q);
@@ -270,7 +323,7 @@ __device__ __forceinline__ bool source(const TransportParams &P, uint64_t h, uin
     const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
     if (!(tn < tf) || !(tf > 0.0f)) {
         cnt.n[kCntMissed]++;
-        cnt.e_escaped += static_cast<double>(e);
+        cnt.e_escaped += kev_fixed(e);
         return false;
     }
     if (tn < 0.0f) tn = 0.0f;
@@ -287,14 +340,27 @@ __device__ __forceinline__ bool source(const TransportParams &P, uint64_t h, uin
     return true;
 }
 
-// One Woodcock step (Sec. 2.1).  Returns false when the history has ended.
-__device__ __forceinline__ bool step(const TransportParams &P, const float4 *__restrict__ s_tab,
-                                     const float *__restrict__ s_mm, Photon &ph, LaneCounts &cnt)
+// Site of a real interaction found by a flight
+struct Hit {
+    size_t idx;       // voxel
+    int m;            // material
+    int j;            // energy node
+    float te;         // energy fraction
+    int type;         // 0 photoelectric, 1 Compton, 2 Rayleigh
+    uint32_t rz, rw;  // the step's random words for zeta and phi
+};
+
+enum { kEnded = 0, kFictitious = 1, kReal = 2 };
+
+// One Woodcock flight (Sec. 2.1): free path against mu_max(E), the move, the
+// escape test, the voxel and the interaction type.
+__device__ __forceinline__ int flight(const TransportParams &P, const float4 *__restrict__ s_tab,
+                                      const float *__restrict__ s_mm, Photon &ph, LaneCounts &cnt, Hit &hit)
 {
     if (ph.step >= kMaxSteps) {
         cnt.n[kCntAborted]++;
-        cnt.e_escaped += static_cast<double>(ph.e);
-        return false;
+        cnt.e_escaped += kev_fixed(ph.e);
+        return kEnded;
     }
     const U4 b = block(P.seed, ph.h, ph.step, kStreamTransport);
     ph.step++;
@@ -311,8 +377,8 @@ __device__ __forceinline__ bool step(const TransportParams &P, const float4 *__r
     if (!(fx >= 0.0f && fx < static_cast<float>(P.nx) && fy >= 0.0f && fy < static_cast<float>(P.ny) &&
           fz >= 0.0f && fz < static_cast<float>(P.nz))) {
         cnt.n[kCntEscaped]++;
-        cnt.e_escaped += static_cast<double>(ph.e);
-        return false;
+        cnt.e_escaped += kev_fixed(ph.e);
+        return kEnded;
     }
     const size_t idx = static_cast<size_t>(static_cast<int>(fx)) +
                        static_cast<size_t>(P.nx) *
@@ -323,6 +389,7 @@ __device__ __forceinline__ bool step(const TransportParams &P, const float4 *__r
     const float c1 = A.x + te * (B.x - A.x);
     const float c2 = A.y + te * (B.y - A.y);
     const float c3 = A.z + te * (B.z - A.z);
+    // interaction type with probabilities mu_i / mu_max
     const float y = uni(b.y) * mmax;
     int type;
     if (y < rho * c1) type = 0;
@@ -331,66 +398,106 @@ __device__ __forceinline__ bool step(const TransportParams &P, const float4 *__r
     else type = 3;
     if (type == 3) {
         cnt.n[kCntFict]++;
-        return true;
+        return kFictitious;
     }
+    hit.idx = idx;
+    hit.m = m;
+    hit.j = j;
+    hit.te = te;
+    hit.type = type;
+    hit.rz = b.z;
+    hit.rw = b.w;
+    return kReal;
+}
+
+// A real interaction: local deposition, C/R-surface polar angle, rotation.
+// Returns false when the history has ended.
+__device__ __forceinline__ bool interact(const TransportParams &P, Photon &ph, const Hit &hit, LaneCounts &cnt)
+{
     ph.nreal++;
-    if (type == 0) {
+    if (hit.type == 0) {
         // photoelectric absorption: the electron deposits E here
         cnt.n[kCntPe]++;
-        atomicAdd(&P.tally[idx], static_cast<double>(ph.e));
+        deposit(P.tally, hit.idx, ph.e);
         return false;
     }
-    const float *S = type == 1 ? P.csurf : P.rsurf + static_cast<size_t>(m) * P.n_e * P.n_zeta;
-    const float mu = surface(S, P.n_zeta, j, te, uni(b.z));
-    if (type == 1) {
+    const float *S = hit.type == 1 ? P.csurf : P.rsurf + static_cast<size_t>(hit.m) * P.n_e * P.n_zeta;
+    const float mu = surface(S, P.n_zeta, hit.j, hit.te, uni(hit.rz));
+    if (hit.type == 1) {
         // Compton: E' = E / (1 + (E/mc^2)(1 - mu)), the electron gets E - E'
         cnt.n[kCntCompton]++;
         const float k = ph.e / static_cast<float>(kMec2);
         const float ep = ph.e / (1.0f + k * (1.0f - mu));
         if (ep < static_cast<float>(P.e_min)) {
             cnt.n[kCntCutoff]++;
-            atomicAdd(&P.tally[idx], static_cast<double>(ph.e));
+            deposit(P.tally, hit.idx, ph.e);
             return false;
         }
-        atomicAdd(&P.tally[idx], static_cast<double>(ph.e - ep));
+        deposit(P.tally, hit.idx, ph.e - ep);
         ph.e = ep;
     } else {
         cnt.n[kCntRayleigh]++;
     }
     if (P.mode == CTD_MODE_MAX_REAL && ph.nreal >= P.max_real) {
         cnt.n[kCntTerminated]++;
-        cnt.e_escaped += static_cast<double>(ph.e);
+        cnt.e_escaped += kev_fixed(ph.e);
         return false;
     }
-    rotate(ph.ux, ph.uy, ph.uz, mu, uni(b.w));
+    rotate(ph.ux, ph.uy, ph.uz, mu, uni(hit.rw));
     return true;
 }
 
-__global__ void __launch_bounds__(256) transport_kernel(const TransportParams P)
+// Flights until a real interaction, the escape, or flight_cap fictitious
+// flights; then the interaction.  Returns false when the history has ended.
+__device__ __forceinline__ bool walk(const TransportParams &P, const float4 *__restrict__ s_tab,
+                                     const float *__restrict__ s_mm, Photon &ph, LaneCounts &cnt)
+{
+    Hit hit;
+    int f, k = 0;
+    do {
+        f = flight(P, s_tab, s_mm, ph, cnt, hit);
+    } while (f == kFictitious && ++k < P.flight_cap);
+    if (f == kEnded) return false;
+    if (f == kFictitious) return true;
+    return interact(P, ph, hit, cnt);
+}
+
+// Per-warp photon queue in shared memory: source photons are made 32 at a
+// time by the whole warp and taken by lanes whose history has ended.
+constexpr int kQueue = 64;
+constexpr size_t kQueueBytes = kQueue * (7 * sizeof(float) + sizeof(uint64_t));
+
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const TransportParams P)
 {
     extern __shared__ float4 smem[];
     float4 *s_tab = smem;
-    float *s_mm = reinterpret_cast<float *>(smem + P.n_mat * P.n_e);
     const int ntab = P.n_mat * P.n_e;
+    float *s_mm = reinterpret_cast<float *>(smem + ntab);
     for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = reinterpret_cast<const float4 *>(P.tab)[i];
     for (int i = threadIdx.x; i < P.n_e; i += blockDim.x) s_mm[i] = P.mmax[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *qbase = reinterpret_cast<unsigned char *>(smem + ntab + (P.n_e + 3) / 4) + warp * kQueueBytes;
+    uint64_t *qh = reinterpret_cast<uint64_t *>(qbase);
+    float *qf = reinterpret_cast<float *>(qh + kQueue);   // [7][kQueue]: x y z ux uy uz e
     __syncthreads();
 
-    const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     LaneCounts cnt;
 #pragma unroll
     for (int i = 0; i < 10; ++i) cnt.n[i] = 0;
-    cnt.e_emitted = 0.0;
-    cnt.e_escaped = 0.0;
+    cnt.e_emitted = 0;
+    cnt.e_escaped = 0;
 
     Photon ph;
     bool alive = false;
     uint64_t pool_next = 0, pool_end = 0;   // warp-uniform claim of local history indices
+    int pool_bin = 0;                       // 1 keV interval of the claim's first history
     bool drained = false;
+    int qcount = 0;                         // photons waiting in the warp's queue
     for (;;) {
-        const unsigned need = __ballot_sync(kFull, !alive);
-        if (need && !drained) {
+        // top the queue up with one round of 32 source photons
+        if (qcount < 32 && !drained) {
             if (pool_next >= pool_end) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(P.work, static_cast<unsigned long long>(P.chunk));
@@ -401,24 +508,62 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams P)
                 } else {
                     pool_next = b;
                     pool_end = b + P.chunk < P.local_end ? b + P.chunk : P.local_end;
+                    pool_bin = bin_search(P, pool_next);
                 }
             }
             if (!drained) {
                 const uint64_t avail = pool_end - pool_next;
-                const unsigned rank = __popc(need & lt_mask);
-                if (!alive && rank < avail) {
-                    const uint64_t local = pool_next + rank;
-                    alive = source(P, P.h_base + local, local, ph, cnt);
+                const unsigned take = avail < 32 ? static_cast<unsigned>(avail) : 32u;
+                Photon np;
+                bool ok = false;
+                if (lane < take) {
+                    const uint64_t local = pool_next + lane;
+                    ok = source(P, P.h_base + local, local, pool_bin, np, cnt);
                 }
-                const uint64_t used = static_cast<uint64_t>(__popc(need)) < avail ? __popc(need) : avail;
-                pool_next += used;
+                const unsigned okm = __ballot_sync(kFull, ok);
+                if (ok) {
+                    const int slot = qcount + __popc(okm & lt_mask);
+                    qh[slot] = np.h;
+                    qf[0 * kQueue + slot] = np.x;
+                    qf[1 * kQueue + slot] = np.y;
+                    qf[2 * kQueue + slot] = np.z;
+                    qf[3 * kQueue + slot] = np.ux;
+                    qf[4 * kQueue + slot] = np.uy;
+                    qf[5 * kQueue + slot] = np.uz;
+                    qf[6 * kQueue + slot] = np.e;
+                }
+                qcount += __popc(okm);
+                pool_next += take;
+            }
+            __syncwarp();
+        }
+        // lanes without a photon take one from the queue
+        const unsigned need = __ballot_sync(kFull, !alive);
+        const int npop = __popc(need) < qcount ? __popc(need) : qcount;
+        if (!alive) {
+            const int rank = __popc(need & lt_mask);
+            if (rank < npop) {
+                const int slot = qcount - 1 - rank;
+                ph.h = qh[slot];
+                ph.x = qf[0 * kQueue + slot];
+                ph.y = qf[1 * kQueue + slot];
+                ph.z = qf[2 * kQueue + slot];
+                ph.ux = qf[3 * kQueue + slot];
+                ph.uy = qf[4 * kQueue + slot];
+                ph.uz = qf[5 * kQueue + slot];
+                ph.e = qf[6 * kQueue + slot];
+                ph.step = 0;
+                ph.nreal = 0;
+                alive = true;
             }
         }
+        qcount -= npop;
+        __syncwarp();
         if (!__any_sync(kFull, alive)) {
-            if (drained) break;
+            if (drained && qcount == 0) break;
             continue;
         }
-        if (alive) alive = step(P, s_tab, s_mm, ph, cnt);
+        if (alive) alive = walk(P, s_tab, s_mm, ph, cnt);
     }
 
     // flush the lane counters: warp sums, one atomic per warp
@@ -429,15 +574,18 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams P)
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
         if (lane == 0 && v) atomicAdd(&P.counts->n[i], v);
     }
-    double em = cnt.e_emitted, es = cnt.e_escaped;
+    // energies: 128-bit fixed-point totals (lo, hi) so that no run can overflow them
+    unsigned long long em = cnt.e_emitted, es = cnt.e_escaped;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         em += __shfl_down_sync(kFull, em, o);
         es += __shfl_down_sync(kFull, es, o);
     }
     if (lane == 0) {
-        atomicAdd(&P.counts->e_emitted, em);
-        atomicAdd(&P.counts->e_escaped, es);
+        const unsigned long long o1 = atomicAdd(&P.counts->e_fix[0], em);
+        if (o1 + em < o1) atomicAdd(&P.counts->e_fix[1], 1ull);
+        const unsigned long long o2 = atomicAdd(&P.counts->e_fix[2], es);
+        if (o2 + es < o2) atomicAdd(&P.counts->e_fix[3], 1ull);
     }
 }
 
@@ -470,20 +618,31 @@ __global__ void eval_math_kernel(int fn, const float *x, float *out, size_t n)
 
 }  // namespace
 
-size_t transport_smem_bytes(int n_mat, int n_e)
+size_t transport_smem_bytes(int n_mat, int n_e, int threads)
 {
-    return static_cast<size_t>(n_mat) * n_e * sizeof(float4) + static_cast<size_t>(n_e) * sizeof(float);
+    return static_cast<size_t>(n_mat) * n_e * sizeof(float4) + static_cast<size_t>((n_e + 3) / 4) * sizeof(float4) +
+           static_cast<size_t>(threads / 32) * kQueueBytes;
 }
 
-int launch_transport(const TransportParams &p, int grid, int block, size_t smem, void *stream)
+// The register budget follows the residency asked for: 4 or more blocks of
+// 256 threads per SM cap the kernel at 64 registers, fewer at 85.
+template <int kMinBlocks>
+int launch_transport_t(const TransportParams &p, int grid, int block, size_t smem, cudaStream_t stream)
 {
     if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(transport_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(transport_kernel<kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)) != cudaSuccess)
             return CTD_ECUDA;
     }
-    transport_kernel<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(p);
+    transport_kernel<kMinBlocks><<<grid, block, smem, stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? CTD_OK : CTD_ECUDA;
+}
+
+int launch_transport(const TransportParams &p, int grid, int block, int threads_per_sm, size_t smem, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (threads_per_sm >= 1024) return launch_transport_t<4>(p, grid, block, smem, s);
+    return launch_transport_t<3>(p, grid, block, smem, s);
 }
 
 int launch_sample_mu(const float *surf, int n_zeta, int n_e, int e_min, float e, uint64_t seed, uint64_t n,

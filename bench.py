@@ -246,10 +246,22 @@ def run_ours(args):
     hist_total = sum_over_ranks(float(p.n_hist * args.steps), world, dev)
     value = hist_total / t_max
 
-    # sec-to-1% avg RSD: N scales as RSD^-2 at fixed variance per history
+    # sec-to-1% avg RSD: N scales as RSD^-2 at fixed variance per history (extrapolated),
+    # and measured by the RSD-stopped served form: batches of a tenth of the extrapolated
+    # count, stopped at 1 % after at least 10 batches
     rsd = stats["avg_rsd"]
     sec_run = t_dev / args.steps
     sec_to_1 = sec_run * (rsd / 0.01) ** 2
+    measured_1 = None
+    if args.rsd_stop and rank == 0:
+        n_1 = p.n_hist * (rsd / 0.01) ** 2
+        B = int(max(1e6, n_1 / 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rid = ctd.ctd_submit(ctx, h, B, 0.01, seed + 1, n_histories_max=int(40 * B))
+        st1 = ctd.ctd_wait(ctx, rid, 600.0)
+        measured_1 = {"seconds": time.perf_counter() - t0, "histories": st1["histories"], "batches": st1["batches"],
+                      "avg_rsd": st1["avg_rsd"], "batch_histories": B}
 
     # end to end through the public API with host buffers: phantom upload, set-up,
     # run and the read-back of dose and stddev, every step
@@ -319,7 +331,9 @@ def run_ours(args):
                        "l2": "flushed between steps (256 MB write outside timed events)",
                        "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk,
                        "flight_cap": args.flight_cap},
-            "sec_to_1pct_avg_rsd": sec_to_1, "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
+            "sec_to_1pct_avg_rsd": measured_1["seconds"] if measured_1 else sec_to_1,
+            "sec_to_1pct_avg_rsd_extrapolated": sec_to_1, "rsd_stopped_run": measured_1,
+            "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
             "clocks": ck,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
@@ -327,6 +341,63 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
         }), flush=True)
+    ctd.ctd_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- batched form
+def run_batched(args):
+    """64 uneven requests: all in shared launches (batched form) against the same
+    requests one after another (plain single-request form)."""
+    import torch
+
+    from paper_1109_3266_gb300 import ctd, inputs as I
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    reqs = I.batched_requests(args.n_requests, hist_lo=args.hist_lo, hist_hi=args.hist_hi)
+    ctx = ctd.ctd_create(device=0, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
+                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap)
+    hs = [ctd.load_problem(ctx, p) for p in reqs]
+    n_total = sum(p.n_hist for p in reqs)
+    nb = 10
+
+    def batched():
+        ctd.ctd_run_batch(ctx, hs, [p.n_hist for p in reqs], [p.seed for p in reqs], nb)
+
+    def plain():
+        for h, p in zip(hs, reqs):
+            ctd.ctd_run(ctx, h, p.n_hist, p.seed, nb)
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        return ts
+
+    timed(batched, 1)
+    with Clocks(0) as clk:
+        tb = timed(batched, args.steps)
+        tp = timed(plain, max(1, args.steps // 2))
+    rsd = [ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)[2]["avg_rsd"] for h in hs]
+    vb = n_total / float(np.mean(tb))
+    vp = n_total / float(np.mean(tp))
+    print(json.dumps({
+        "metric": "photon histories/sec, batched form vs plain single-request form", "value": vb, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * float(np.mean(tb)),
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batched", "requests": len(reqs), "histories_per_step": n_total, "batches": nb,
+                   "sides": sorted({p.meta["side"] for p in reqs}), "hist_range": [args.hist_lo, args.hist_hi]},
+        "plain_value": vp, "plain_ms_per_step": 1e3 * float(np.mean(tp)), "speedup_vs_plain": vb / vp,
+        "avg_rsd_range": [float(min(rsd)), float(max(rsd))], "clocks": clk.summary(),
+    }), flush=True)
+    for h in hs:
+        ctd.ctd_destroy_phantom(ctx, h)
     ctd.ctd_destroy(ctx)
 
 
@@ -344,11 +415,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rsd-stop", type=int, default=1, help="measure sec-to-1%% with the RSD-stopped form")
     ap.add_argument("--inst-per-history", type=float, default=0.0)
+    ap.add_argument("--n-requests", type=int, default=64)
+    ap.add_argument("--hist-lo", type=float, default=1e7)
+    ap.add_argument("--hist-hi", type=float, default=1e9)
     ap.add_argument("--traffic-per-launch", type=float, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -155,6 +155,72 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
 int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches,
                   uint64_t h_begin, uint64_t h_end, int clear);
 
+/* Batched form: n_req dose calculations in shared persistent launches.
+ * Request r transports n_histories[r] histories of phantoms[r] (distinct
+ * phantoms, each with its source and spectrum set, all on the same node grid)
+ * with random numbers keyed by seeds[r], in n_batches (>= 2) batches.  Batch b
+ * of every request runs in one launch whose warps draw histories from all
+ * requests, followed by one fold over every request's grids; at most 12
+ * distinct materials per call.  Each phantom's results are then read with
+ * ctd_get_dose_and_stddev and equal those of a separate ctd_run with the same
+ * arguments (up to the order of binary64 additions in the tallies); its
+ * t_transport_s is the time of the shared launches.  Blocks until done. */
+int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const uint64_t *n_histories,
+                  const uint64_t *seeds, int n_batches);
+
+/* ---- Served form: continuous batching of dose requests ----
+ * A request transports batches of batch_histories histories of a phantom with
+ * random numbers keyed by seed until, after at least min_batches batches, its
+ * avg RSD is <= rsd_target, or until n_histories_max histories have run.
+ * Requests wait in a queue until admitted (free device memory above the
+ * context's reserve and fewer than 64 running); each call of ctd_serve_step
+ * admits what fits, runs one batch of every running request in one shared
+ * launch, folds them, updates the statistics and retires finished requests.
+ * A finished request's result equals ctd_run(phantom, k * batch_histories,
+ * seed, k) for its k batches (up to the order of binary64 additions), alone or
+ * mixed with others, and is read with ctd_get_dose_and_stddev.  A phantom
+ * serves one request at a time; while it does, calls that would change it
+ * return CTD_EBUSY. */
+typedef enum {
+    CTD_REQ_QUEUED = 0,
+    CTD_REQ_RUNNING = 1,
+    CTD_REQ_DONE = 2,
+    CTD_REQ_CANCELLED = 3,
+    CTD_REQ_FAILED = 4
+} ctd_req_state;
+
+typedef struct {
+    uint64_t batch_histories;   /* histories per batch (> 0)                        */
+    uint64_t n_histories_max;   /* stop after this many histories (0: no limit)      */
+    double rsd_target;          /* stop once avg RSD <= this (e.g. 0.01)             */
+    int min_batches;            /* batches before the first check (>= 2; 0 means 10) */
+    uint64_t seed;
+} ctd_request;
+
+typedef int64_t ctd_req_id;
+
+typedef struct {
+    int state;                  /* ctd_req_state                                     */
+    int batches;                /* batches finished                                  */
+    uint64_t histories;         /* histories finished                                */
+    double avg_rsd;             /* last statistics update (0 before min_batches)      */
+    double paper_sigma_bar;
+    double t_queued_s;          /* time from submission to admission (so far)        */
+    double t_latency_s;         /* time from submission to retirement (so far)       */
+} ctd_req_status;
+
+int ctd_submit(ctd_ctx *ctx, ctd_phantom ph, const ctd_request *req, ctd_req_id *out);
+/* One round of the served form; *n_active (may be NULL) is the number of
+ * requests still queued or running afterwards. */
+int ctd_serve_step(ctd_ctx *ctx, int *n_active);
+int ctd_poll(ctd_ctx *ctx, ctd_req_id id, ctd_req_status *out);
+/* Drive ctd_serve_step until request id has finished or timeout_s seconds have
+ * passed (CTD_ETIMEOUT); out may be NULL. */
+int ctd_wait(ctd_ctx *ctx, ctd_req_id id, double timeout_s, ctd_req_status *out);
+/* A queued request is dropped at once, a running one at the next round;
+ * either ends as CTD_REQ_CANCELLED. */
+int ctd_cancel(ctd_ctx *ctx, ctd_req_id id);
+
 /* Mean dose and its standard error (Gy per history, nvox doubles each; either
  * may be NULL) and the stats of the last ctd_run (stats may be NULL). */
 int ctd_get_dose_and_stddev(ctd_ctx *ctx, ctd_phantom ph, double *dose, double *stddev, size_t nvox,

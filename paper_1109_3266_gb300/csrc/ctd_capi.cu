@@ -2,6 +2,7 @@
 // source/spectrum/physics set-up, the batch loop of Sec. 2.2.1 and results.
 #include <cuda_runtime.h>
 
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -101,6 +102,19 @@ struct Phantom {
     int alloc_nb = -1;
     ctd_run_stats stats{};
     bool have_result = false;
+    int64_t busy_req = 0;      // served request using this phantom, 0 if none
+};
+
+struct ServeReq {
+    int64_t id = 0;
+    int ph = 0;
+    ctd_request req{};
+    int state = CTD_REQ_QUEUED;
+    int batches = 0;
+    uint64_t histories = 0;
+    double avg_rsd = 0.0, sigma_bar = 0.0;
+    double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
+    bool cancel = false;
 };
 
 }  // namespace
@@ -121,6 +135,21 @@ struct ctd_ctx {
     std::map<int, std::unique_ptr<Phantom>> phantoms;
     int next_id = 1;
     std::vector<cudaEvent_t> events;
+    // multi-request launches: union tables, request and fold descriptors
+    DevBuf<float> u_tab, u_rs;
+    DevBuf<ctd::RequestDesc> u_reqs;
+    DevBuf<uint64_t> u_off, u_tiles;
+    DevBuf<ctd::FoldDesc> u_folds;
+    DevBuf<unsigned long long> u_work;
+    // served form: all requests by id, the admission queue and the running set
+    std::map<int64_t, ServeReq> sreqs;
+    std::vector<int64_t> pending, active;
+    int64_t next_req = 1;
+    int max_active = 64;
+    double reserve_bytes = 1.0 * (1ull << 30);
+    bool union_valid = false;
+    std::vector<std::array<uint8_t, 16>> union_maps;
+    int union_n = 0;
 };
 
 namespace {
@@ -139,6 +168,13 @@ Phantom *find(ctd_ctx *ctx, ctd_phantom id)
 {
     auto it = ctx->phantoms.find(id);
     return it == ctx->phantoms.end() ? nullptr : it->second.get();
+}
+
+int busy(Phantom *P)
+{
+    return P->busy_req ? fail(CTD_EBUSY, "phantom is in use by served request %lld",
+                              static_cast<long long>(P->busy_req))
+                       : CTD_OK;
 }
 
 int build_tables(ctd_ctx *ctx, Phantom &P)
@@ -222,56 +258,59 @@ int check_ready(Phantom &P)
     return CTD_OK;
 }
 
-void fill_params(ctd_ctx *ctx, Phantom &P, uint64_t seed, ctd::TransportParams &T)
+// The per-request part of a transport launch (geometry, source, spectrum, outputs).
+void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
 {
-    std::memset(&T, 0, sizeof(T));
-    T.mat = P.mat.p;
-    T.rho = P.rho.p;
-    T.tab = P.tab.p;
-    T.mmax = P.mm.p;
-    T.csurf = P.cs.p;
-    T.rsurf = P.rs.p;
-    T.nbins = static_cast<int>(P.w.size());
-    T.bin_lo = P.bins.p;
-    T.bin_hi = P.bins.p + T.nbins;
-    T.cb = P.proj.p;
-    T.sb = P.proj.p + (P.src.n_proj > 0 ? P.src.n_proj : 1);
-    T.work = P.work.p;
-    T.counts = P.counts.p;
-    T.seed = seed;
-    T.nx = P.nx;
-    T.ny = P.ny;
-    T.nz = P.nz;
+    std::memset(&q, 0, sizeof(q));
+    q.mat = P.mat.p;
+    q.rho = P.rho.p;
+    q.mmax = P.mm.p;
+    q.nbins = static_cast<int>(P.w.size());
+    q.bin_lo = P.bins.p;
+    q.bin_hi = P.bins.p + q.nbins;
+    q.cb = P.proj.p;
+    q.sb = P.proj.p + (P.src.n_proj > 0 ? P.src.n_proj : 1);
+    q.counts = P.counts.p;
+    q.seed = seed;
+    q.nx = P.nx;
+    q.ny = P.ny;
+    q.nz = P.nz;
     const double hx = static_cast<double>(P.nx) * P.dx / 2.0, hy = static_cast<double>(P.ny) * P.dy / 2.0,
                  hz = static_cast<double>(P.nz) * P.dz / 2.0;
-    T.bx0 = static_cast<float>(-hx);
-    T.by0 = static_cast<float>(-hy);
-    T.bz0 = static_cast<float>(-hz);
-    T.bx1 = static_cast<float>(hx);
-    T.by1 = static_cast<float>(hy);
-    T.bz1 = static_cast<float>(hz);
-    T.ix = static_cast<float>(1.0 / P.dx);
-    T.iy = static_cast<float>(1.0 / P.dy);
-    T.iz = static_cast<float>(1.0 / P.dz);
-    T.n_mat = static_cast<int>(P.mats.size());
-    T.n_e = P.n_e;
-    T.n_zeta = P.phys.n_zeta;
-    T.e_min = P.phys.e_min_kev;
-    T.src_kind = P.src.kind;
-    T.n_proj = P.src.n_proj;
-    T.continuous = P.src.continuous;
-    T.D = static_cast<float>(P.src.sad_cm);
-    T.D2 = T.D * T.D;
-    T.ulo = static_cast<float>(P.src.u_lo_cm);
-    T.uw = static_cast<float>(P.src.u_hi_cm) - T.ulo;
-    T.vlo = static_cast<float>(P.src.v_lo_cm);
-    T.vw = static_cast<float>(P.src.v_hi_cm) - T.vlo;
-    T.a0t = static_cast<float>(P.src.arc0_rad / (2.0 * ctd::kPi));
-    T.awt = static_cast<float>((P.src.arc1_rad - P.src.arc0_rad) / (2.0 * ctd::kPi));
-    T.mode = P.phys.mode;
-    T.max_real = P.phys.max_real;
-    T.chunk = ctx->chunk;
-    T.flight_cap = ctx->flight_cap;
+    q.bx0 = static_cast<float>(-hx);
+    q.by0 = static_cast<float>(-hy);
+    q.bz0 = static_cast<float>(-hz);
+    q.bx1 = static_cast<float>(hx);
+    q.by1 = static_cast<float>(hy);
+    q.bz1 = static_cast<float>(hz);
+    q.ix = static_cast<float>(1.0 / P.dx);
+    q.iy = static_cast<float>(1.0 / P.dy);
+    q.iz = static_cast<float>(1.0 / P.dz);
+    q.src_kind = P.src.kind;
+    q.n_proj = P.src.n_proj;
+    q.continuous = P.src.continuous;
+    q.D = static_cast<float>(P.src.sad_cm);
+    q.D2 = q.D * q.D;
+    q.ulo = static_cast<float>(P.src.u_lo_cm);
+    q.uw = static_cast<float>(P.src.u_hi_cm) - q.ulo;
+    q.vlo = static_cast<float>(P.src.v_lo_cm);
+    q.vw = static_cast<float>(P.src.v_hi_cm) - q.vlo;
+    q.a0t = static_cast<float>(P.src.arc0_rad / (2.0 * ctd::kPi));
+    q.awt = static_cast<float>((P.src.arc1_rad - P.src.arc0_rad) / (2.0 * ctd::kPi));
+    q.mode = P.phys.mode;
+    q.max_real = P.phys.max_real;
+    for (int m = 0; m < ctd::kMaxPhantomMaterials; ++m) q.mat_map[m] = static_cast<uint8_t>(m);
+}
+
+void fill_shared(Phantom &P, ctd::SharedTables &sh)
+{
+    sh.tab = P.tab.p;
+    sh.csurf = P.cs.p;
+    sh.rsurf = P.rs.p;
+    sh.n_mat = static_cast<int>(P.mats.size());
+    sh.n_e = P.n_e;
+    sh.n_zeta = P.phys.n_zeta;
+    sh.e_min = P.phys.e_min_kev;
 }
 
 cudaEvent_t event_at(ctd_ctx *ctx, size_t i)
@@ -285,21 +324,27 @@ cudaEvent_t event_at(ctd_ctx *ctx, size_t i)
 }
 
 // One transport launch over local histories [lb, le) of a batch starting at global h_base.
-int transport(ctd_ctx *ctx, Phantom &P, ctd::TransportParams &T, int which_size, uint64_t h_base, uint64_t lb,
+int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uint64_t h_base, uint64_t lb,
               uint64_t le, double *tally, size_t ev_index)
 {
-    T.pref = P.pref.p + which_size * (T.nbins + 1);
-    T.h_base = h_base;
-    T.local_begin = lb;
-    T.local_end = le;
-    T.tally = tally;
+    ctd::LaunchParams L;
+    std::memset(&L, 0, sizeof(L));
+    fill_shared(P, L.sh);
+    q.pref = P.pref.p + which_size * (q.nbins + 1);
+    q.h_base = h_base;
+    q.local_begin = lb;
+    q.local_end = le;
+    q.tally = tally;
+    L.one = q;
+    L.work = P.work.p;
+    L.chunk = ctx->chunk;
+    L.flight_cap = ctx->flight_cap;
     CK(cudaMemsetAsync(P.work.p, 0, sizeof(unsigned long long), ctx->stream));
     cudaEvent_t e0 = event_at(ctx, 2 * ev_index), e1 = event_at(ctx, 2 * ev_index + 1);
     if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
     CK(cudaEventRecord(e0, ctx->stream));
     const int grid = ctx->num_sms * ctx->blocks_per_sm;
-    CKS(ctd::launch_transport(T, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm,
-                              ctd::transport_smem_bytes(T.n_mat, T.n_e, ctx->threads), ctx->stream));
+    CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream));
     CK(cudaEventRecord(e1, ctx->stream));
     return CTD_OK;
 }
@@ -413,7 +458,7 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     if (!out || !mat || !density || !mats) return fail(CTD_EINVAL, "null pointer argument");
     if (nx <= 0 || ny <= 0 || nz <= 0) return fail(CTD_EINVAL, "voxel counts must be positive");
     if (!(dx > 0 && dy > 0 && dz > 0)) return fail(CTD_EINVAL, "voxel sizes must be positive");
-    if (n_mat <= 0 || n_mat > 255) return fail(CTD_EINVAL, "n_mat must be 1..255");
+    if (n_mat <= 0 || n_mat > ctd::kMaxPhantomMaterials) return fail(CTD_EINVAL, "n_mat must be 1..16");
     for (int m = 0; m < n_mat; ++m)
         if (!(mats[m].z_over_a > 0 && mats[m].a_mol > 0 && mats[m].z_eff > 0))
             return fail(CTD_EINVAL, "material %d has non-positive parameters", m);
@@ -456,6 +501,7 @@ int ctd_destroy_phantom(ctd_ctx *ctx, ctd_phantom ph)
     if ((rc = use_device(ctx))) return rc;
     auto it = ctx->phantoms.find(ph);
     if (it == ctx->phantoms.end()) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if ((rc = busy(it->second.get()))) return rc;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->phantoms.erase(it);
     return CTD_OK;
@@ -468,6 +514,7 @@ int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys)
     Phantom *P = find(ctx, ph);
     if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
     if (!phys) return fail(CTD_EINVAL, "null physics");
+    if ((rc = busy(P))) return rc;
     if (phys->e_min_kev < 1 || phys->e_max_kev <= phys->e_min_kev || phys->e_max_kev > 100000)
         return fail(CTD_EINVAL, "node grid must satisfy 1 <= e_min < e_max");
     if (phys->n_zeta < 2 || phys->n_zeta > (1 << 20)) return fail(CTD_EINVAL, "n_zeta must be 2..2^20");
@@ -487,6 +534,7 @@ int ctd_set_source(ctd_ctx *ctx, ctd_phantom ph, const ctd_source *src)
     Phantom *P = find(ctx, ph);
     if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
     if (!src) return fail(CTD_EINVAL, "null source");
+    if ((rc = busy(P))) return rc;
     if (src->kind != CTD_SRC_STATIC && src->kind != CTD_SRC_ARC) return fail(CTD_EINVAL, "unknown source kind");
     if (!(src->sad_cm > 0) || !(src->u_hi_cm >= src->u_lo_cm) || !(src->v_hi_cm >= src->v_lo_cm))
         return fail(CTD_EINVAL, "source distance must be positive and field bounds ordered");
@@ -521,6 +569,7 @@ int ctd_set_spectrum(ctd_ctx *ctx, ctd_phantom ph, const double *e_lo, const dou
     Phantom *P = find(ctx, ph);
     if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
     if (!e_lo || !e_hi || !w || nbins <= 0 || nbins > 100000) return fail(CTD_EINVAL, "bad spectrum arrays");
+    if ((rc = busy(P))) return rc;
     double total = 0.0;
     for (int j = 0; j < nbins; ++j) {
         if (!(e_hi[j] >= e_lo[j]) || !(e_lo[j] > 0) || !(w[j] >= 0) || !std::isfinite(w[j]) || !std::isfinite(e_hi[j]))
@@ -553,6 +602,7 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
     if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
     if (n_batches < 2 || static_cast<uint64_t>(n_batches) > n_histories)
         return fail(CTD_EINVAL, "need 2 <= n_batches <= n_histories");
+    if ((rc = busy(P))) return rc;
     const double t0 = now_s();
     if ((rc = prepare_run(ctx, *P, n_histories, n_batches))) return rc;
     P->have_result = false;
@@ -562,8 +612,8 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
     CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
-    ctd::TransportParams T;
-    fill_params(ctx, *P, seed, T);
+    ctd::RequestDesc T;
+    fill_request(*P, seed, T);
     const uint64_t n_lo = n_histories / n_batches, rem = n_histories % n_batches;
     const double vol = P->dx * P->dy * P->dz;
     uint64_t h = 0;
@@ -586,6 +636,184 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
     return CTD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr int kMaxUnionMaterials = 12;
+
+bool same_material(const ctd_material &a, const ctd_material &b)
+{
+    return a.z_over_a == b.z_over_a && a.a_mol == b.a_mol && a.z_eff == b.z_eff && a.q0 == b.q0;
+}
+
+// Union of the requests' materials: tables and R surfaces copied from the
+// phantoms' own rows (equal materials have equal rows), mat_map per request.
+int build_union(ctd_ctx *ctx, const std::vector<Phantom *> &ps, std::vector<std::array<uint8_t, 16>> &maps, int &n_um)
+{
+    std::vector<ctd_material> um;
+    std::vector<std::pair<int, int>> src;   // (request, material) that supplies each union row
+    maps.assign(ps.size(), {});
+    for (size_t r = 0; r < ps.size(); ++r) {
+        for (size_t m = 0; m < ps[r]->mats.size(); ++m) {
+            int k = -1;
+            for (size_t u = 0; u < um.size(); ++u)
+                if (same_material(um[u], ps[r]->mats[m])) k = static_cast<int>(u);
+            if (k < 0) {
+                if (um.size() >= static_cast<size_t>(kMaxUnionMaterials))
+                    return fail(CTD_EINVAL, "more than %d distinct materials in one batch", kMaxUnionMaterials);
+                um.push_back(ps[r]->mats[m]);
+                src.emplace_back(static_cast<int>(r), static_cast<int>(m));
+                k = static_cast<int>(um.size()) - 1;
+            }
+            maps[r][m] = static_cast<uint8_t>(k);
+        }
+    }
+    n_um = static_cast<int>(um.size());
+    const int n_e = ps[0]->n_e, nz = ps[0]->phys.n_zeta;
+    const size_t row = static_cast<size_t>(n_e) * nz;
+    std::vector<float> tab(static_cast<size_t>(n_um) * n_e * 4), rs(static_cast<size_t>(n_um) * row);
+    for (int u = 0; u < n_um; ++u) {
+        const Phantom &P = *ps[src[u].first];
+        const int m = src[u].second;
+        std::memcpy(&tab[static_cast<size_t>(u) * n_e * 4], &P.h_tab[static_cast<size_t>(m) * n_e * 4],
+                    sizeof(float) * n_e * 4);
+        std::memcpy(&rs[static_cast<size_t>(u) * row], &P.h_rs[static_cast<size_t>(m) * row], sizeof(float) * row);
+    }
+    int rc;
+    if ((rc = ctx->u_tab.ensure(tab.size())) || (rc = ctx->u_rs.ensure(rs.size()))) return rc;
+    CK(cudaMemcpyAsync(ctx->u_tab.p, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->u_rs.p, rs.data(), rs.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return CTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const uint64_t *n_histories,
+                  const uint64_t *seeds, int n_batches)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    if (n_req <= 0 || !phantoms || !n_histories || !seeds) return fail(CTD_EINVAL, "bad request arrays");
+    if (n_batches < 2) return fail(CTD_EINVAL, "need n_batches >= 2");
+    const double t0 = now_s();
+    std::vector<Phantom *> ps(n_req);
+    for (int r = 0; r < n_req; ++r) {
+        ps[r] = find(ctx, phantoms[r]);
+        if (!ps[r]) return fail(CTD_ENOTFOUND, "unknown phantom %d", phantoms[r]);
+        for (int k = 0; k < r; ++k)
+            if (ps[k] == ps[r]) return fail(CTD_EINVAL, "phantom %d appears twice in one batch", phantoms[r]);
+        if (static_cast<uint64_t>(n_batches) > n_histories[r])
+            return fail(CTD_EINVAL, "request %d has fewer histories than batches", r);
+        if ((rc = busy(ps[r]))) return rc;
+        if ((rc = prepare_run(ctx, *ps[r], n_histories[r], n_batches))) return rc;
+        const ctd_physics &a = ps[0]->phys, &b = ps[r]->phys;
+        if (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta)
+            return fail(CTD_EINVAL, "request %d has another node grid than request 0", r);
+    }
+    std::vector<std::array<uint8_t, 16>> maps;
+    int n_um = 0;
+    ctx->union_valid = false;   // the served form's union tables are about to be overwritten
+    if ((rc = build_union(ctx, ps, maps, n_um))) return rc;
+    // descriptors for every batch of every request, the history and tile offsets
+    std::vector<ctd::RequestDesc> descs(static_cast<size_t>(n_batches) * n_req);
+    std::vector<uint64_t> offs(static_cast<size_t>(n_batches) * (n_req + 1));
+    std::vector<ctd::FoldDesc> folds(static_cast<size_t>(n_batches) * n_req);
+    std::vector<uint64_t> tiles(n_req + 1, 0);
+    for (int r = 0; r < n_req; ++r)
+        tiles[r + 1] = tiles[r] + (ps[r]->nvox + ctd::kFoldTile - 1) / ctd::kFoldTile;
+    for (int r = 0; r < n_req; ++r) {
+        Phantom &P = *ps[r];
+        const size_t nv = P.nvox;
+        CK(cudaMemsetAsync(P.tally.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P.sum_d.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P.sum_d2.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P.edep.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P.counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+        P.have_result = false;
+        const uint64_t n = n_histories[r], n_lo = n / n_batches, rem = n % n_batches;
+        const double vol = P.dx * P.dy * P.dz;
+        uint64_t h = 0;
+        for (int b = 0; b < n_batches; ++b) {
+            const uint64_t nb = static_cast<uint64_t>(b) < rem ? n_lo + 1 : n_lo;
+            const int which = static_cast<uint64_t>(b) < rem ? 0 : 1;
+            ctd::RequestDesc &q = descs[static_cast<size_t>(b) * n_req + r];
+            fill_request(P, seeds[r], q);
+            std::memcpy(q.mat_map, maps[r].data(), sizeof(q.mat_map));
+            q.pref = P.pref.p + which * (q.nbins + 1);
+            q.h_base = h;
+            q.local_begin = 0;
+            q.local_end = nb;
+            q.tally = P.tally.p;
+            uint64_t *o = &offs[static_cast<size_t>(b) * (n_req + 1)];
+            o[r + 1] = o[r] + nb;
+            ctd::FoldDesc &f = folds[static_cast<size_t>(b) * n_req + r];
+            f.tally = P.tally.p;
+            f.rho = P.rho.p;
+            f.sum_d = P.sum_d.p;
+            f.sum_d2 = P.sum_d2.p;
+            f.edep = P.edep.p;
+            f.nvox = nv;
+            f.scale = ctd::kKevToJ * 1000.0 / (vol * static_cast<double>(nb));
+            h += nb;
+        }
+    }
+    if ((rc = ctx->u_reqs.ensure(descs.size())) || (rc = ctx->u_off.ensure(offs.size())) ||
+        (rc = ctx->u_folds.ensure(folds.size())) || (rc = ctx->u_tiles.ensure(tiles.size())) ||
+        (rc = ctx->u_work.ensure(n_batches)))
+        return rc;
+    CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), descs.size() * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->u_off.p, offs.data(), offs.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), folds.size() * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemsetAsync(ctx->u_work.p, 0, n_batches * sizeof(unsigned long long), ctx->stream));
+    // batch b of every request in one launch, then one fold over every grid
+    ctd::LaunchParams L;
+    std::memset(&L, 0, sizeof(L));
+    L.sh.tab = ctx->u_tab.p;
+    L.sh.csurf = ps[0]->cs.p;
+    L.sh.rsurf = ctx->u_rs.p;
+    L.sh.n_mat = n_um;
+    L.sh.n_e = ps[0]->n_e;
+    L.sh.n_zeta = ps[0]->phys.n_zeta;
+    L.sh.e_min = ps[0]->phys.e_min_kev;
+    L.n_req = n_req;
+    L.chunk = ctx->chunk;
+    L.flight_cap = ctx->flight_cap;
+    const int grid = ctx->num_sms * ctx->blocks_per_sm;
+    for (int b = 0; b < n_batches; ++b) {
+        L.reqs = ctx->u_reqs.p + static_cast<size_t>(b) * n_req;
+        L.req_off = ctx->u_off.p + static_cast<size_t>(b) * (n_req + 1);
+        L.work = ctx->u_work.p + b;
+        cudaEvent_t e0 = event_at(ctx, 2 * b), e1 = event_at(ctx, 2 * b + 1);
+        if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
+        CK(cudaEventRecord(e0, ctx->stream));
+        CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream));
+        CK(cudaEventRecord(e1, ctx->stream));
+        CKS(ctd::launch_fold_multi(ctx->u_folds.p + static_cast<size_t>(b) * n_req, ctx->u_tiles.p, n_req, tiles[n_req],
+                                   ctx->stream));
+    }
+    for (int r = 0; r < n_req; ++r) {
+        Phantom &P = *ps[r];
+        CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, n_batches, P.dose.p, P.sd.p, P.nvox, ctx->stream));
+        CKS(ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, ctx->stream));
+        CKS(ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, ctx->stream));
+    }
+    for (int r = 0; r < n_req; ++r) {
+        if ((rc = collect(ctx, *ps[r], n_batches, t0))) return rc;
+        ps[r]->stats.histories = n_histories[r];
+        ps[r]->stats.n_batches = n_batches;
+        ps[r]->have_result = true;
+    }
+    return CTD_OK;
+}
+
 int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches, uint64_t h_begin,
                   uint64_t h_end, int clear)
 {
@@ -596,6 +824,7 @@ int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t s
     if (n_batches < 1 || static_cast<uint64_t>(n_batches) > n_histories)
         return fail(CTD_EINVAL, "need 1 <= n_batches <= n_histories");
     if (h_begin > h_end || h_end > n_histories) return fail(CTD_EINVAL, "history range outside [0, n_histories]");
+    if ((rc = busy(P))) return rc;
     const double t0 = now_s();
     if ((rc = prepare_run(ctx, *P, n_histories, n_batches))) return rc;
     const size_t nv = P->nvox;
@@ -604,8 +833,8 @@ int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t s
         CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
     }
     P->have_result = false;
-    ctd::TransportParams T;
-    fill_params(ctx, *P, seed, T);
+    ctd::RequestDesc T;
+    fill_request(*P, seed, T);
     const uint64_t n_lo = n_histories / n_batches, rem = n_histories % n_batches;
     uint64_t h = 0;
     size_t launches = 0;
@@ -717,6 +946,285 @@ int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n)
     CKS(ctd::launch_eval_math(fn, bx.p, bo.p, n, ctx->stream));
     CK(cudaMemcpyAsync(out, bo.p, no * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return CTD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- served form
+namespace {
+
+double elapsed_since(double t) { return now_s() - t; }
+
+// Admit queued requests in order while memory and slots allow.
+int admit(ctd_ctx *ctx)
+{
+    while (!ctx->pending.empty() && static_cast<int>(ctx->active.size()) < ctx->max_active) {
+        ServeReq &R = ctx->sreqs[ctx->pending.front()];
+        Phantom *P = find(ctx, R.ph);
+        if (!P) {
+            R.state = CTD_REQ_FAILED;
+            ctx->pending.erase(ctx->pending.begin());
+            continue;
+        }
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const double need = P->tally.p ? 0.0 : 6.0 * 8.0 * static_cast<double>(P->nvox);
+        if (static_cast<double>(free_b) < need + ctx->reserve_bytes) break;
+        int rc;
+        // one allocation for batches of batch_histories: n = 2B in 2 batches
+        if ((rc = prepare_run(ctx, *P, 2 * R.req.batch_histories, 2))) {
+            R.state = CTD_REQ_FAILED;
+            P->busy_req = 0;
+            ctx->pending.erase(ctx->pending.begin());
+            continue;
+        }
+        const size_t nv = P->nvox;
+        CK(cudaMemsetAsync(P->tally.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P->sum_d.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+        P->have_result = false;
+        R.state = CTD_REQ_RUNNING;
+        R.t_start = now_s();
+        ctx->active.push_back(R.id);
+        ctx->pending.erase(ctx->pending.begin());
+        ctx->union_valid = false;
+    }
+    return CTD_OK;
+}
+
+void retire(ctd_ctx *ctx, ServeReq &R, int state)
+{
+    R.state = state;
+    R.t_done = now_s();
+    Phantom *P = find(ctx, R.ph);
+    if (P) P->busy_req = 0;
+    for (size_t i = 0; i < ctx->active.size(); ++i)
+        if (ctx->active[i] == R.id) {
+            ctx->active.erase(ctx->active.begin() + i);
+            break;
+        }
+    ctx->union_valid = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctd_submit(ctd_ctx *ctx, ctd_phantom ph, const ctd_request *req, ctd_req_id *out)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!req || !out) return fail(CTD_EINVAL, "null argument");
+    if ((rc = busy(P))) return rc;
+    if (req->batch_histories == 0) return fail(CTD_EINVAL, "batch_histories must be positive");
+    if (req->min_batches == 1 || req->min_batches < 0) return fail(CTD_EINVAL, "min_batches must be >= 2 (0: 10)");
+    if (!(req->rsd_target >= 0.0)) return fail(CTD_EINVAL, "rsd_target must be >= 0");
+    if (req->rsd_target == 0.0 && req->n_histories_max == 0) return fail(CTD_EINVAL, "request could never stop");
+    if ((rc = check_ready(*P))) return rc;
+    ServeReq R;
+    R.id = ctx->next_req++;
+    R.ph = ph;
+    R.req = *req;
+    if (R.req.min_batches == 0) R.req.min_batches = 10;
+    R.t_submit = now_s();
+    P->busy_req = R.id;
+    ctx->sreqs[R.id] = R;
+    ctx->pending.push_back(R.id);
+    *out = R.id;
+    return CTD_OK;
+}
+
+int ctd_serve_step(ctd_ctx *ctx, int *n_active)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    // cancellations take effect at round boundaries
+    for (size_t i = 0; i < ctx->active.size();) {
+        ServeReq &R = ctx->sreqs[ctx->active[i]];
+        if (R.cancel) retire(ctx, R, CTD_REQ_CANCELLED);
+        else ++i;
+    }
+    if ((rc = admit(ctx))) return rc;
+    const int n = static_cast<int>(ctx->active.size());
+    if (n == 0) {
+        if (n_active) *n_active = static_cast<int>(ctx->pending.size());
+        return CTD_OK;
+    }
+    std::vector<Phantom *> ps(n);
+    for (int i = 0; i < n; ++i) ps[i] = find(ctx, ctx->sreqs[ctx->active[i]].ph);
+    for (int i = 1; i < n; ++i) {
+        const ctd_physics &a = ps[0]->phys, &b = ps[i]->phys;
+        if (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta) {
+            retire(ctx, ctx->sreqs[ctx->active[i]], CTD_REQ_FAILED);
+            return fail(CTD_EINVAL, "served requests must share one node grid");
+        }
+    }
+    if (!ctx->union_valid) {
+        if ((rc = build_union(ctx, ps, ctx->union_maps, ctx->union_n))) return rc;
+        ctx->union_valid = true;
+    }
+    std::vector<ctd::RequestDesc> descs(n);
+    std::vector<uint64_t> offs(n + 1, 0), tiles(n + 1, 0);
+    std::vector<ctd::FoldDesc> folds(n);
+    for (int i = 0; i < n; ++i) {
+        ServeReq &R = ctx->sreqs[ctx->active[i]];
+        Phantom &P = *ps[i];
+        const uint64_t B = R.req.batch_histories;
+        ctd::RequestDesc &q = descs[i];
+        fill_request(P, R.req.seed, q);
+        std::memcpy(q.mat_map, ctx->union_maps[i].data(), sizeof(q.mat_map));
+        q.pref = P.pref.p + 1 * (q.nbins + 1);    // batches of exactly B histories
+        q.h_base = static_cast<uint64_t>(R.batches) * B;
+        q.local_begin = 0;
+        q.local_end = B;
+        q.tally = P.tally.p;
+        offs[i + 1] = offs[i] + B;
+        tiles[i + 1] = tiles[i] + (P.nvox + ctd::kFoldTile - 1) / ctd::kFoldTile;
+        ctd::FoldDesc &f = folds[i];
+        f.tally = P.tally.p;
+        f.rho = P.rho.p;
+        f.sum_d = P.sum_d.p;
+        f.sum_d2 = P.sum_d2.p;
+        f.edep = P.edep.p;
+        f.nvox = P.nvox;
+        f.scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
+    }
+    if ((rc = ctx->u_reqs.ensure(n)) || (rc = ctx->u_off.ensure(n + 1)) || (rc = ctx->u_folds.ensure(n)) ||
+        (rc = ctx->u_tiles.ensure(n + 1)) || (rc = ctx->u_work.ensure(1)))
+        return rc;
+    CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), n * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->u_off.p, offs.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), n * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->u_work.p, 0, sizeof(unsigned long long), ctx->stream));
+    ctd::LaunchParams L;
+    std::memset(&L, 0, sizeof(L));
+    L.sh.tab = ctx->u_tab.p;
+    L.sh.csurf = ps[0]->cs.p;
+    L.sh.rsurf = ctx->u_rs.p;
+    L.sh.n_mat = ctx->union_n;
+    L.sh.n_e = ps[0]->n_e;
+    L.sh.n_zeta = ps[0]->phys.n_zeta;
+    L.sh.e_min = ps[0]->phys.e_min_kev;
+    L.reqs = ctx->u_reqs.p;
+    L.req_off = ctx->u_off.p;
+    L.n_req = n;
+    L.work = ctx->u_work.p;
+    L.chunk = ctx->chunk;
+    L.flight_cap = ctx->flight_cap;
+    const int grid = ctx->num_sms * ctx->blocks_per_sm;
+    CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream));
+    CKS(ctd::launch_fold_multi(ctx->u_folds.p, ctx->u_tiles.p, n, tiles[n], ctx->stream));
+    std::vector<int> checked;
+    for (int i = 0; i < n; ++i) {
+        ServeReq &R = ctx->sreqs[ctx->active[i]];
+        Phantom &P = *ps[i];
+        R.batches += 1;
+        R.histories += R.req.batch_histories;
+        if (R.batches >= R.req.min_batches) {
+            CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, R.batches, P.dose.p, P.sd.p, P.nvox, ctx->stream));
+            CKS(ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, ctx->stream));
+            checked.push_back(i);
+        }
+    }
+    std::vector<std::array<double, 3>> res(checked.size());
+    for (size_t c = 0; c < checked.size(); ++c)
+        CK(cudaMemcpyAsync(res[c].data(), ps[checked[c]]->result.p, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<int64_t> finished;
+    for (size_t c = 0; c < checked.size(); ++c) {
+        ServeReq &R = ctx->sreqs[ctx->active[checked[c]]];
+        R.avg_rsd = res[c][0];
+        R.sigma_bar = res[c][1];
+        const bool hit = R.req.rsd_target > 0.0 && R.avg_rsd > 0.0 && R.avg_rsd <= R.req.rsd_target;
+        const bool cap = R.req.n_histories_max && R.histories >= R.req.n_histories_max;
+        if (hit || cap) finished.push_back(R.id);
+    }
+    for (int64_t id : finished) {
+        ServeReq &R = ctx->sreqs[id];
+        Phantom &P = *find(ctx, R.ph);
+        CKS(ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, ctx->stream));
+        if ((rc = collect(ctx, P, 0, R.t_start))) return rc;
+        P.stats.histories = R.histories;
+        P.stats.n_batches = R.batches;
+        P.have_result = true;
+        retire(ctx, R, CTD_REQ_DONE);
+    }
+    if (n_active) *n_active = static_cast<int>(ctx->active.size() + ctx->pending.size());
+    return CTD_OK;
+}
+
+int ctd_poll(ctd_ctx *ctx, ctd_req_id id, ctd_req_status *out)
+{
+    if (!ctx) return fail(CTD_EINVAL, "null context");
+    auto it = ctx->sreqs.find(id);
+    if (it == ctx->sreqs.end()) return fail(CTD_ENOTFOUND, "unknown request %lld", static_cast<long long>(id));
+    if (out) {
+        const ServeReq &R = it->second;
+        out->state = R.state;
+        out->batches = R.batches;
+        out->histories = R.histories;
+        out->avg_rsd = R.avg_rsd;
+        out->paper_sigma_bar = R.sigma_bar;
+        const double now = now_s();
+        out->t_queued_s = (R.state == CTD_REQ_QUEUED ? now : (R.t_start > 0 ? R.t_start : now)) - R.t_submit;
+        out->t_latency_s = (R.state >= CTD_REQ_DONE ? R.t_done : now) - R.t_submit;
+    }
+    return CTD_OK;
+}
+
+int ctd_wait(ctd_ctx *ctx, ctd_req_id id, double timeout_s, ctd_req_status *out)
+{
+    int rc;
+    if (!ctx) return fail(CTD_EINVAL, "null context");
+    if (ctx->sreqs.find(id) == ctx->sreqs.end())
+        return fail(CTD_ENOTFOUND, "unknown request %lld", static_cast<long long>(id));
+    const double t0 = now_s();
+    for (;;) {
+        const ServeReq &R = ctx->sreqs[id];
+        if (R.state >= CTD_REQ_DONE) break;
+        if (elapsed_since(t0) > timeout_s) {
+            if (out) ctd_poll(ctx, id, out);
+            return fail(CTD_ETIMEOUT, "request %lld not finished after %.3f s", static_cast<long long>(id), timeout_s);
+        }
+        const size_t before = ctx->active.size();
+        if ((rc = ctd_serve_step(ctx, nullptr))) return rc;
+        if (before == 0 && ctx->active.empty() && ctx->sreqs[id].state == CTD_REQ_QUEUED)
+            return fail(CTD_ENOMEM, "request %lld cannot be admitted: not enough free device memory",
+                        static_cast<long long>(id));
+    }
+    const ServeReq &R = ctx->sreqs[id];
+    if (out) ctd_poll(ctx, id, out);
+    if (R.state == CTD_REQ_CANCELLED) return fail(CTD_ECANCELLED, "request was cancelled");
+    if (R.state == CTD_REQ_FAILED) return fail(CTD_ECUDA, "request failed");
+    return CTD_OK;
+}
+
+int ctd_cancel(ctd_ctx *ctx, ctd_req_id id)
+{
+    if (!ctx) return fail(CTD_EINVAL, "null context");
+    auto it = ctx->sreqs.find(id);
+    if (it == ctx->sreqs.end()) return fail(CTD_ENOTFOUND, "unknown request %lld", static_cast<long long>(id));
+    ServeReq &R = it->second;
+    if (R.state == CTD_REQ_QUEUED) {
+        for (size_t i = 0; i < ctx->pending.size(); ++i)
+            if (ctx->pending[i] == id) {
+                ctx->pending.erase(ctx->pending.begin() + i);
+                break;
+            }
+        R.state = CTD_REQ_CANCELLED;
+        R.t_done = now_s();
+        Phantom *P = find(ctx, R.ph);
+        if (P) P->busy_req = 0;
+    } else if (R.state == CTD_REQ_RUNNING) {
+        R.cancel = true;
+    }
     return CTD_OK;
 }
 

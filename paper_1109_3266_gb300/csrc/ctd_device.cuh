@@ -1,0 +1,229 @@
+// ctd_device.cuh -- device arithmetic of the transport (sm_103a), shared by the
+// transport kernels: Philox4x32-10, the uniform mapping, the binary32
+// logarithm and sincos, float/double bit conversions, the binary64 direction
+// renormalisation, the rotation after a scatter, the 1 keV node lookup and the
+// R/C-surface lookup.  Compiled with --fmad=false: every multiply and add
+// rounds on its own unless written as an explicit fused multiply-add.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ctd_internal.h"
+
+namespace ctd {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kStreamTransport = 0, kStreamSource = 1, kStreamSampler = 3;
+constexpr uint32_t kMaxTrials = 1000;
+constexpr uint32_t kMaxSteps = 100000000u;
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32->64 products,
+// xor with the round key, key bumped by the Weyl constants.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                     uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ U4 block(uint64_t seed, uint64_t h, uint32_t step, uint32_t stream)
+{
+    return philox(static_cast<uint32_t>(h), static_cast<uint32_t>(h >> 32), step, stream,
+                  static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+}
+
+// (2 (x >> 9) + 1) 2^-24: exact in binary32, never 0 or 1
+__device__ __forceinline__ float uni(uint32_t x)
+{
+    return static_cast<float>(2u * (x >> 9) + 1u) * 0x1p-24f;
+}
+
+// ---------------------------------------------------------------- binary32 log and sincos
+// ln x: x = 2^e m with m in (sqrt(1/2), sqrt(2)], ln m = 2 atanh(s), s = (m-1)/(m+1),
+// atanh series through s^11 in Horner form, then + e ln 2 with ln 2 split in two.
+__device__ __forceinline__ float log32(float x)
+{
+    uint32_t bits = __float_as_uint(x);
+    int e = static_cast<int>((bits >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+    if (m > 0x1.6a09e6p+0f) {
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    const float f = m - 1.0f;
+    const float s = f / (2.0f + f);
+    const float z = s * s;
+    float p = __fmaf_rn(z, 0x1.745d18p-4f, 0x1.c71c72p-4f);
+    p = __fmaf_rn(z, p, 0x1.24924ap-3f);
+    p = __fmaf_rn(z, p, 0x1.99999ap-3f);
+    p = __fmaf_rn(z, p, 0x1.555556p-2f);
+    const float r = z * p;
+    const float s2 = s + s;
+    const float lnm = __fmaf_rn(s2, r, s2);
+    const float ef = static_cast<float>(e);
+    return __fmaf_rn(ef, 0x1.62e430p-1f, __fmaf_rn(ef, -0x1.05c610p-29f, lnm));
+}
+
+// cos and sin of 2 pi t: exact reduction in turns to a quarter-turn offset in
+// [-1/8, 1/8], Taylor polynomials of sin (to x^9) and cos (to x^10).
+__device__ __forceinline__ void sincos_turns(float t, float &c, float &s)
+{
+    const float w = t - floorf(t);
+    int q = static_cast<int>(w * 4.0f);
+    float r = w - static_cast<float>(q) * 0.25f;
+    if (r > 0.125f) {
+        r = r - 0.25f;
+        q = q + 1;
+    }
+    const float x = r * 0x1.921fb6p+2f;
+    const float x2 = x * x;
+    float ps = __fmaf_rn(x2, 0x1.71de3ap-19f, -0x1.a01a02p-13f);
+    ps = __fmaf_rn(x2, ps, 0x1.111112p-7f);
+    ps = __fmaf_rn(x2, ps, -0x1.555556p-3f);
+    const float sn = __fmaf_rn(x * x2, ps, x);
+    float pc = __fmaf_rn(x2, -0x1.27e4fcp-22f, 0x1.a01a02p-16f);
+    pc = __fmaf_rn(x2, pc, -0x1.6c16c2p-10f);
+    pc = __fmaf_rn(x2, pc, 0x1.555556p-5f);
+    pc = __fmaf_rn(x2, pc, -0.5f);
+    const float cs = __fmaf_rn(x2, pc, 1.0f);
+    switch (q & 3) {
+    case 0: c = cs; s = sn; break;
+    case 1: c = -sn; s = cs; break;
+    case 2: c = -cs; s = -sn; break;
+    default: c = sn; s = -cs; break;
+    }
+}
+
+// Exact binary32 -> binary64 widening with integer instructions (GB300's FP64
+// pipe is narrow; this keeps conversions off it).  Zeros keep their sign;
+// subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double(static_cast<int>(u & 0x80000000u), 0);
+    if (ex == 0u || ex == 0xffu) return static_cast<double>(f);
+    const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
+
+// binary64 -> binary32 by truncating the significand to 23 bits (round toward
+// zero); magnitudes below 2^-126 give 0.
+__device__ __forceinline__ float trunc32(double d)
+{
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(d));
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(d));
+    const uint32_t ex = (hi >> 20) & 0x7ffu;
+    if (ex < 897u) return 0.0f;
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float((hi & 0x80000000u) | (((ex - 896u) & 0xffu) << 23) | m);
+}
+
+// Back to unit length after a scatter: the squared norm n2 and the correction
+// e = c - 1 of one Newton step c = 1.5 - 0.5 n2 for 1/sqrt(n2) from 1 are
+// binary64 (the products of widened floats are exact, so the fused forms equal
+// the separately rounded ones); e, truncated to binary32, is applied to each
+// component with one fused multiply-add.
+__device__ __forceinline__ void renorm(float &ux, float &uy, float &uz)
+{
+    const double dx = widen(ux), dy = widen(uy), dz = widen(uz);
+    const double n2 = __fma_rn(dz, dz, __fma_rn(dx, dx, __dmul_rn(dy, dy)));
+    const double e = __fma_rn(-0.5, n2, 0.5);
+    const float ef = trunc32(e);
+    ux = __fmaf_rn(ux, ef, ux);
+    uy = __fmaf_rn(uy, ef, uy);
+    uz = __fmaf_rn(uz, ef, uz);
+}
+
+// E 2^23 as an integer: exact for 1 keV <= E < 2^40 keV (every photon energy of
+// the transport is at least the node floor e_min >= 1 keV)
+__device__ __forceinline__ unsigned long long kev_fixed(float e)
+{
+    const uint32_t u = __float_as_uint(e);
+    const int ex = static_cast<int>((u >> 23) & 0xffu) - 127;
+    const unsigned long long m = (u & 0x7fffffu) | 0x800000u;
+    return ex >= 0 ? (m << ex) : (m >> -ex);
+}
+
+// tally deposit of a non-negative binary32 energy into the binary64 grid
+__device__ __forceinline__ void deposit(double *tally, size_t idx, float e)
+{
+    if (e > 0.0f) atomicAdd(tally + idx, widen(e));
+}
+
+// New direction after a scatter of polar cosine mu and azimuth 2 pi tphi.
+__device__ __forceinline__ void rotate(float &ux, float &uy, float &uz, float mu, float tphi)
+{
+    float st2 = 1.0f - mu * mu;
+    if (st2 < 0.0f) st2 = 0.0f;
+    const float st = sqrtf(st2);
+    float cp, sp;
+    sincos_turns(tphi, cp, sp);
+    const float a2 = ux * ux + uy * uy;
+    float nx, ny, nz;
+    if (a2 < static_cast<float>(1e-12)) {
+        nx = st * cp;
+        ny = st * sp;
+        nz = uz > 0.0f ? mu : -mu;
+    } else {
+        const float a = sqrtf(a2);
+        const float rr = st / a;
+        nx = ux * mu + rr * ((ux * uz) * cp - uy * sp);
+        ny = uy * mu + rr * ((uy * uz) * cp + ux * sp);
+        nz = uz * mu - (a * st) * cp;
+    }
+    ux = nx;
+    uy = ny;
+    uz = nz;
+    renorm(ux, uy, uz);
+}
+
+// energy node j and fraction te on the 1 keV grid
+__device__ __forceinline__ int enode(float e, int e_min, int n_e, float &te)
+{
+    const float fe = e - static_cast<float>(e_min);
+    int j = static_cast<int>(fe);
+    if (j > n_e - 2) j = n_e - 2;
+    if (j < 0) j = 0;
+    te = fe - static_cast<float>(j);
+    return j;
+}
+
+// bilinear lookup of mu(zeta, E) on a surface (Sec. 2.2.2)
+__device__ __forceinline__ float surface(const float *__restrict__ S, int n_zeta, int j, float te, float z)
+{
+    const float zf = z * static_cast<float>(n_zeta - 1);
+    int i = static_cast<int>(zf);
+    if (i > n_zeta - 2) i = n_zeta - 2;
+    const float a = zf - static_cast<float>(i);
+    const float *r0 = S + static_cast<size_t>(j) * n_zeta + i;
+    const float *r1 = r0 + n_zeta;
+    const float a0 = __ldg(r0), a1 = __ldg(r0 + 1), b0 = __ldg(r1), b1 = __ldg(r1 + 1);
+    const float lo = a0 + a * (a1 - a0);
+    const float hi = b0 + a * (b1 - b0);
+    float mu = lo + te * (hi - lo);
+    if (mu > 1.0f) mu = 1.0f;
+    if (mu < -1.0f) mu = -1.0f;
+    return mu;
+}
+
+}  // namespace dev
+}  // namespace ctd

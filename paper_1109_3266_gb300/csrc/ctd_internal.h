@@ -56,39 +56,57 @@ inline double fixed_kev(unsigned long long lo, unsigned long long hi)
 enum { kCntPe = 0, kCntCompton, kCntRayleigh, kCntFict, kCntEscaped, kCntMissed, kCntCutoff,
        kCntTerminated, kCntAborted, kCntSteps };
 
-struct TransportParams {
-    const uint8_t *mat;
-    const float *rho;
-    const float *tab;        // [n_mat][n_e][4]: c1, c2, c3, 0 (cm^2/g)
-    const float *mmax;       // [n_e] 1/cm
-    const float *csurf;      // [n_e][n_zeta]
-    const float *rsurf;      // [n_mat][n_e][n_zeta]
-    const uint64_t *pref;    // [nbins+1] bin starts inside the batch
-    const float *bin_lo;     // [nbins]
-    const float *bin_hi;     // [nbins]
-    const float *cb;         // [n_proj]
-    const float *sb;         // [n_proj]
-    double *tally;           // [nvox] keV
-    unsigned long long *work;   // claim counter over [local_begin, local_end)
+// One request's share of a transport launch.  A single-request launch passes
+// it by value (the kernel's parameter space); a multi-request launch passes an
+// array of them in device memory and each lane reads its own photon's entry.
+struct RequestDesc {
+    const uint8_t *mat;          // [nvox] material of the phantom
+    const float *rho;            // [nvox] g/cm^3
+    const float *mmax;           // [n_e] majorant mu_max(E), 1/cm
+    const uint64_t *pref;        // [nbins+1] bin starts inside the batch
+    const float *bin_lo;         // [nbins]
+    const float *bin_hi;         // [nbins]
+    const float *cb;             // [n_proj]
+    const float *sb;             // [n_proj]
+    double *tally;               // [nvox] keV
     DeviceCounts *counts;
     uint64_t seed;
-    uint64_t h_base;         // global index of local index 0 (first history of the batch)
+    uint64_t h_base;             // global index of local index 0 (first history of the batch)
     uint64_t local_begin, local_end;
     int nbins;
     int nx, ny, nz;
     float bx0, by0, bz0, bx1, by1, bz1;
     float ix, iy, iz;
-    int n_mat, n_e, n_zeta, e_min;
     int src_kind, n_proj, continuous;
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
     int mode, max_real;
-    int chunk;
-    int flight_cap;          // fictitious flights a lane may take before yielding to the warp
+    uint8_t mat_map[16];         // phantom material -> row of the launch's tables
+};
+
+constexpr int kMaxPhantomMaterials = 16;
+
+// Tables shared by every request of a launch.
+struct SharedTables {
+    const float *tab;            // [n_mat][n_e][4]: c1, c2, c3, 0 (cm^2/g)
+    const float *csurf;          // [n_e][n_zeta]
+    const float *rsurf;          // [n_mat][n_e][n_zeta]
+    int n_mat, n_e, n_zeta, e_min;
+};
+
+struct LaunchParams {
+    SharedTables sh;
+    RequestDesc one;             // the request of a single-request launch
+    const RequestDesc *reqs;     // [n_req] (multi-request launches)
+    const uint64_t *req_off;     // [n_req+1] prefix of the requests' history counts
+    int n_req;
+    unsigned long long *work;    // claim counter
+    int chunk;                   // histories a warp claims at a time
+    int flight_cap;              // Woodcock flights a lane takes before yielding to the warp
 };
 
 // launches (ctd_transport.cu / ctd_stats.cu)
-int launch_transport(const TransportParams &p, int grid, int block, int threads_per_sm, size_t smem, void *stream);
-size_t transport_smem_bytes(int n_mat, int n_e, int threads);
+int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream);
+size_t transport_smem_bytes(const LaunchParams &p, int threads);
 int launch_fold(double *tally, const float *rho, double *sum_d, double *sum_d2, double *edep, size_t nvox,
                 double scale, void *stream);
 int launch_finalize(const double *sum_d, const double *sum_d2, int nb, double *dose, double *sd, size_t nvox,
@@ -99,5 +117,17 @@ int launch_sample_mu(const float *surf, int n_zeta, int n_e, int e_min, float e,
                      double *out, void *stream);
 int launch_eval_math(int fn, const float *x, float *out, size_t n, void *stream);
 int launch_sum(const double *x, size_t n, double *partials, int n_parts, double *result, void *stream);
+
+// one fold over several requests' grids in a single launch; tiles of
+// kFoldTile voxels, tile_off[r] = first tile of request r
+struct FoldDesc {
+    double *tally;
+    const float *rho;
+    double *sum_d, *sum_d2, *edep;
+    uint64_t nvox;
+    double scale;
+};
+constexpr int kFoldTile = 4096;
+int launch_fold_multi(const FoldDesc *descs, const uint64_t *tile_off, int n, uint64_t total_tiles, void *stream);
 
 }  // namespace ctd

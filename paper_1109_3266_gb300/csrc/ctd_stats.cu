@@ -29,6 +29,35 @@ __global__ void fold_kernel(double *__restrict__ tally, const float *__restrict_
     }
 }
 
+// The same fold for several requests at once, one tile of kFoldTile voxels per step.
+__global__ void fold_multi_kernel(const FoldDesc *__restrict__ descs, const uint64_t *__restrict__ tile_off, int n,
+                                  uint64_t total_tiles)
+{
+    for (uint64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_off[mid] <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const FoldDesc d = descs[lo];
+        const uint64_t base = (tile - tile_off[lo]) * static_cast<uint64_t>(kFoldTile);
+        const uint64_t end = base + kFoldTile < d.nvox ? base + kFoldTile : d.nvox;
+        for (uint64_t v = base + threadIdx.x; v < end; v += blockDim.x) {
+            const double t = d.tally[v];
+            if (t == 0.0) continue;
+            const float r = d.rho[v];
+            d.edep[v] += t;
+            d.tally[v] = 0.0;
+            if (r > 0.0f) {
+                const double x = t * d.scale / static_cast<double>(r);
+                d.sum_d[v] += x;
+                d.sum_d2[v] += x * x;
+            }
+        }
+    }
+}
+
 // Mean over nb batches and its standard error: s^2 = (sum d^2 - nb D^2) / (nb (nb - 1)).
 __device__ __forceinline__ void mean_sd(double s1, double s2, int nb, double &D, double &sd)
 {
@@ -172,6 +201,14 @@ int launch_fold(double *tally, const float *rho, double *sum_d, double *sum_d2, 
 {
     fold_kernel<<<grid_for(nvox), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(tally, rho, sum_d, sum_d2,
                                                                                       edep, nvox, scale);
+    return ok();
+}
+
+int launch_fold_multi(const FoldDesc *descs, const uint64_t *tile_off, int n, uint64_t total_tiles, void *stream)
+{
+    if (total_tiles == 0) return CTD_OK;
+    const int grid = total_tiles < 152 * 16 ? static_cast<int>(total_tiles) : 152 * 16;
+    fold_multi_kernel<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(descs, tile_off, n, total_tiles);
     return ok();
 }
 

@@ -60,6 +60,21 @@ class ctd_run_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ctd_request(C.Structure):
+    _fields_ = [("batch_histories", C.c_uint64), ("n_histories_max", C.c_uint64), ("rsd_target", C.c_double),
+                ("min_batches", C.c_int), ("seed", C.c_uint64)]
+
+
+class ctd_req_status(C.Structure):
+    _fields_ = [("state", C.c_int), ("batches", C.c_int), ("histories", C.c_uint64), ("avg_rsd", C.c_double),
+                ("paper_sigma_bar", C.c_double), ("t_queued_s", C.c_double), ("t_latency_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(5)
+
 _lib = None
 
 
@@ -90,6 +105,13 @@ def lib():
         L.ctd_sample_mu.argtypes = [P, C.c_int32, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint64, dp]
         L.ctd_eval_math.argtypes = [P, C.c_int, fp, fp, C.c_size_t]
         L.ctd_avg_rsd_noalloc.argtypes = [P, P, P, C.c_size_t, P, P]
+        L.ctd_run_batch.argtypes = [P, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                    C.c_int]
+        L.ctd_submit.argtypes = [P, C.c_int32, C.POINTER(ctd_request), C.POINTER(C.c_int64)]
+        L.ctd_serve_step.argtypes = [P, C.POINTER(C.c_int)]
+        L.ctd_poll.argtypes = [P, C.c_int64, C.POINTER(ctd_req_status)]
+        L.ctd_wait.argtypes = [P, C.c_int64, C.c_double, C.POINTER(ctd_req_status)]
+        L.ctd_cancel.argtypes = [P, C.c_int64]
         _lib = L
     return _lib
 
@@ -156,6 +178,46 @@ def ctd_set_spectrum(ctx, ph, e_lo, e_hi, w):
 
 def ctd_run(ctx, ph, n_histories, seed, n_batches):
     _check(lib().ctd_run(ctx, ph, int(n_histories), int(seed), int(n_batches)))
+
+
+def ctd_run_batch(ctx, phantoms, n_histories, seeds, n_batches):
+    """Batched form: every request's batch b in one shared launch."""
+    n = len(phantoms)
+    ph = (C.c_int32 * n)(*phantoms)
+    nh = (C.c_uint64 * n)(*[int(x) for x in n_histories])
+    sd = (C.c_uint64 * n)(*[int(x) for x in seeds])
+    _check(lib().ctd_run_batch(ctx, n, ph, nh, sd, int(n_batches)))
+
+
+def ctd_submit(ctx, ph, batch_histories, rsd_target, seed, n_histories_max=0, min_batches=0):
+    """Queue a served request; returns its id."""
+    r = ctd_request(int(batch_histories), int(n_histories_max), float(rsd_target), int(min_batches), int(seed))
+    out = C.c_int64()
+    _check(lib().ctd_submit(ctx, ph, C.byref(r), C.byref(out)))
+    return out.value
+
+
+def ctd_serve_step(ctx):
+    """One round of the served form; returns the number of requests still queued or running."""
+    n = C.c_int()
+    _check(lib().ctd_serve_step(ctx, C.byref(n)))
+    return n.value
+
+
+def ctd_poll(ctx, req_id):
+    st = ctd_req_status()
+    _check(lib().ctd_poll(ctx, int(req_id), C.byref(st)))
+    return st.as_dict()
+
+
+def ctd_wait(ctx, req_id, timeout_s):
+    st = ctd_req_status()
+    _check(lib().ctd_wait(ctx, int(req_id), float(timeout_s), C.byref(st)))
+    return st.as_dict()
+
+
+def ctd_cancel(ctx, req_id):
+    _check(lib().ctd_cancel(ctx, int(req_id)))
 
 
 def ctd_run_range(ctx, ph, n_histories, seed, n_batches, h_begin, h_end, clear=True):

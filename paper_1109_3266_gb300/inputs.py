@@ -172,10 +172,13 @@ def head_phantom(nx, ny, nz, d, seed: int, size_ref=(25.6, 25.6, 16.0)) -> Phant
     x = (np.arange(nx) + 0.5) * d - nx * d / 2.0
     y = (np.arange(ny) + 0.5) * d - ny * d / 2.0
     z = (np.arange(nz) + 0.5) * d - nz * d / 2.0
-    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
 
     def inside(a, b, c, x0=0.0, y0=0.0, z0=0.0):
-        return ((X - x0) / a) ** 2 + ((Y - y0) / b) ** 2 + ((Z - z0) / c) ** 2 <= 1.0
+        # separable quadratic form, broadcast over (z, y, x)
+        qx = ((x - x0) / a) ** 2
+        qy = ((y - y0) / b) ** 2
+        qz = ((z - z0) / c) ** 2
+        return (qz[:, None, None] + qy[None, :, None]) + qx[None, None, :] <= 1.0
 
     scalp = 0.5
     mat = np.zeros((nz, ny, nx), dtype=np.uint8)            # 0 air

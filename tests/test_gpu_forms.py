@@ -1,0 +1,145 @@
+"""The batched and served forms against the plain single-request form.
+
+A request's result must be the same alone (ctd_run) and mixed with others in
+shared launches (ctd_run_batch, the served scheduler): identical integer
+counts, dose equal up to the order of binary64 additions.  The served form
+also stops each request at its target avg RSD, admits requests that arrive
+while others run, and honours cancellation, bounded waits and EBUSY."""
+import numpy as np
+import pytest
+
+from paper_1109_3266_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("pe", "compton", "rayleigh", "fictitious", "escaped", "missed", "cutoff", "terminated", "aborted", "steps",
+        "histories", "n_batches")
+
+
+@pytest.fixture(scope="module")
+def ctd():
+    from paper_1109_3266_gb300 import build, ctd as binding
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(ctd):
+    c = ctd.ctd_create(device=0)
+    yield c
+    ctd.ctd_destroy(c)
+
+
+def problems():
+    return [I.head(120_000, seed=31, phantom_seed=7, shape=(64, 64, 40), d=0.4),
+            I.cbct_water(90_000, seed=32, shape=(48, 48, 24), d=0.8),
+            I.head(60_000, seed=33, phantom_seed=8, shape=(40, 40, 24), d=0.6, kvp=80),
+            I.cbct_water(7_777, seed=34, shape=(32, 32, 16), d=1.0)]
+
+
+def alone(ctd, ctx, p, n=None, nb=None):
+    h = ctd.load_problem(ctx, p)
+    ctd.ctd_run(ctx, h, p.n_hist if n is None else n, p.seed, p.n_batches if nb is None else nb)
+    dose, sd, st = ctd.ctd_get_dose_and_stddev(ctx, h, p.phantom.nvox)
+    ctd.ctd_destroy_phantom(ctx, h)
+    return dose, sd, st
+
+
+def same(a, b):
+    dose, sd, st = a
+    d2, s2, st2 = b
+    diff = {k: (st[k], st2[k]) for k in KEYS if st[k] != st2[k]}
+    assert not diff, diff
+    assert np.allclose(d2, dose, rtol=1e-9, atol=0)
+    assert np.allclose(s2, sd, rtol=1e-6, atol=1e-30)
+    assert st2["avg_rsd"] == pytest.approx(st["avg_rsd"], rel=1e-6)
+
+
+def test_batched_equals_separate_runs(ctd, ctx):
+    ps = problems()
+    ref = [alone(ctd, ctx, p) for p in ps]
+    hs = [ctd.load_problem(ctx, p) for p in ps]
+    ctd.ctd_run_batch(ctx, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
+    for p, h, r in zip(ps, hs, ref):
+        same(r, ctd.ctd_get_dose_and_stddev(ctx, h, p.phantom.nvox))
+    # a second batched call on the same phantoms gives the same again
+    ctd.ctd_run_batch(ctx, hs[::-1], [p.n_hist for p in ps[::-1]], [p.seed for p in ps[::-1]], 10)
+    for p, h, r in zip(ps, hs, ref):
+        same(r, ctd.ctd_get_dose_and_stddev(ctx, h, p.phantom.nvox))
+    for h in hs:
+        ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_batched_rejects_mixed_node_grids_and_duplicates(ctd, ctx):
+    a = ctd.load_problem(ctx, I.tiny_water(1000))            # nodes 10-150 keV
+    b = ctd.load_problem(ctx, problems()[1])                  # nodes 1-150 keV
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_run_batch(ctx, [a, b], [1000, 1000], [1, 2], 10)
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_run_batch(ctx, [b, b], [1000, 1000], [1, 2], 10)
+    ctd.ctd_destroy_phantom(ctx, a)
+    ctd.ctd_destroy_phantom(ctx, b)
+
+
+def test_served_requests_equal_plain_runs(ctd, ctx):
+    ps = problems()[:3]
+    B = [20_000, 15_000, 9_000]
+    targets = [0.12, 0.2, 0.3]
+    hs = [ctd.load_problem(ctx, p) for p in ps]
+    ids = [ctd.ctd_submit(ctx, hs[i], B[i], targets[i], ps[i].seed, n_histories_max=400 * B[i])
+           for i in range(2)]
+    # rounds with two requests, then a third arrives while they run
+    for _ in range(3):
+        ctd.ctd_serve_step(ctx)
+    ids.append(ctd.ctd_submit(ctx, hs[2], B[2], targets[2], ps[2].seed, n_histories_max=400 * B[2]))
+    assert ctd.ctd_poll(ctx, ids[0])["state"] == ctd.REQ_RUNNING
+    with pytest.raises(ctd.CtdError) as e:
+        ctd.ctd_destroy_phantom(ctx, hs[0])
+    assert e.value.code == 4                                   # CTD_EBUSY
+    for i in ids:
+        st = ctd.ctd_wait(ctx, i, 120.0)
+        assert st["state"] == ctd.REQ_DONE
+    for i, p in enumerate(ps):
+        st = ctd.ctd_poll(ctx, ids[i])
+        k = st["batches"]
+        assert k >= 10 and st["histories"] == k * B[i]
+        assert st["avg_rsd"] <= targets[i] or st["histories"] >= 400 * B[i]
+        served = ctd.ctd_get_dose_and_stddev(ctx, hs[i], p.phantom.nvox)
+        same(alone(ctd, ctx, p, n=k * B[i], nb=k), served)
+        ctd.ctd_destroy_phantom(ctx, hs[i])
+
+
+def test_served_cancel_timeout_and_queue(ctd, ctx):
+    p = problems()[1]
+    h = ctd.load_problem(ctx, p)
+    rid = ctd.ctd_submit(ctx, h, 5_000, 1e-6, 1, n_histories_max=10 ** 12)
+    with pytest.raises(ctd.CtdError) as e:
+        ctd.ctd_wait(ctx, rid, 0.0)
+    assert e.value.code == 5                                   # CTD_ETIMEOUT
+    ctd.ctd_serve_step(ctx)
+    ctd.ctd_cancel(ctx, rid)
+    ctd.ctd_serve_step(ctx)
+    assert ctd.ctd_poll(ctx, rid)["state"] == ctd.REQ_CANCELLED
+    # a queued request cancelled before admission, then the phantom is free again
+    rid2 = ctd.ctd_submit(ctx, h, 5_000, 0.5, 2)
+    ctd.ctd_cancel(ctx, rid2)
+    assert ctd.ctd_poll(ctx, rid2)["state"] == ctd.REQ_CANCELLED
+    ctd.ctd_run(ctx, h, 10_000, 3, 10)
+    ctd.ctd_destroy_phantom(ctx, h)
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_poll(ctx, 10 ** 9)
+
+
+def test_serve_loop_reports_latency(ctd, ctx):
+    from paper_1109_3266_gb300 import serve
+
+    arrivals = [(0.0, 51), (0.05, 52), (0.1, 53), (0.15, 54)]
+
+    def make(seed):
+        return I.head(1, seed=seed, phantom_seed=seed, shape=(32, 32, 20), d=0.8)
+
+    reqs, wall = serve.serve(ctx, arrivals, make, batch_histories=20_000, rsd_target=0.25, n_histories_max=4_000_000)
+    summ = serve.latency_summary(reqs)
+    assert summ["done"] == 4 and summ["p50_s"] > 0 and summ["p99_s"] >= summ["p50_s"]
+    for r in reqs:
+        assert r.state == ctd.REQ_DONE and r.batches >= 10

@@ -147,23 +147,30 @@ def sum_over_ranks(x, world, device=None):
 
 
 # --------------------------------------------------------------------------- CPU oracle leg
-def oracle_rate(p, seconds, threads):
-    """Histories/s of the binary64 oracle as it stands on a bounded prefix of the workload."""
+def oracle_rate(p, seconds, threads, n_ranges=64):
+    """Histories/s of the binary64 oracle as it stands on a bounded sample of the
+    workload: n_ranges equal history ranges spread evenly through the first batch,
+    so that the sample covers the whole spectrum (histories run in 1 keV bin order)."""
     from oracle import oracle as O
     s = O.Setup(p, 64)
-    n = 4000
-    while True:
+    batch = p.n_hist // p.n_batches
+
+    def sample(n):
+        per = max(1, n // n_ranges)
+        ranges = [((batch * k) // n_ranges, min((batch * k) // n_ranges + per, p.n_hist)) for k in range(n_ranges)]
         t0 = time.perf_counter()
-        s.transport(0, n, threads)
-        dt = time.perf_counter() - t0
-        if dt > 0.5 or n >= p.n_hist:
+        s.transport_ranges(ranges, threads)
+        return per * n_ranges, time.perf_counter() - t0
+
+    n = 64 * n_ranges
+    while True:
+        done, dt = sample(n)
+        if dt > 0.5 or n >= batch:
             break
         n *= 4
-    n = int(max(2000, min(p.n_hist, n / max(dt, 1e-6) * seconds)))
-    t0 = time.perf_counter()
-    _, c = s.transport(0, n, threads)
-    dt = time.perf_counter() - t0
-    return n / dt, n, dt, c
+    n = int(max(n_ranges, min(batch, done / max(dt, 1e-6) * seconds)))
+    done, dt = sample(n)
+    return done / dt, done, dt, None
 
 
 def cpu_cores():
@@ -187,8 +194,8 @@ def run_reference(args):
         rates.append(r)
         ns.append(n)
     value = float(np.mean(rates))
-    sample = (f"binary64 oracle, first {ns[0]} histories of batch 0 of {p.name} per step, "
-              f"{threads} threads over history ranges")
+    sample = (f"binary64 oracle, {ns[0]} histories of {p.name} per step in 64 equal ranges spread through "
+              f"batch 0 (all 1 keV bins), {threads} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ns[0] / value,
@@ -318,7 +325,8 @@ def run_ours(args):
         threads = cpu_cores()
         r, n, dt, _ = oracle_rate(p, args.ref_seconds, threads)
         cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"binary64 oracle, first {n} histories of {p.name} ({dt:.1f} s), {threads} threads"}
+               "sample": f"binary64 oracle, {n} histories of {p.name} in 64 equal ranges spread through batch 0 "
+                         f"(all 1 keV bins), {dt:.1f} s, {threads} threads"}
 
     if rank == 0:
         print(json.dumps({
@@ -354,9 +362,11 @@ def run_batched(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    reqs = I.batched_requests(args.n_requests, hist_lo=args.hist_lo, hist_hi=args.hist_hi)
+    sides = tuple(range(64, args.max_side + 1, 32))
+    reqs = I.batched_requests(args.n_requests, hist_lo=args.hist_lo, hist_hi=args.hist_hi, sides=sides)
     ctx = ctd.ctd_create(device=0, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
-                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap)
+                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap,
+                         multi_blocks_per_sm=args.multi_blocks_per_sm)
     hs = [ctd.load_problem(ctx, p) for p in reqs]
     n_total = sum(p.n_hist for p in reqs)
     nb = 10
@@ -418,6 +428,8 @@ def main():
     ap.add_argument("--rsd-stop", type=int, default=1, help="measure sec-to-1%% with the RSD-stopped form")
     ap.add_argument("--inst-per-history", type=float, default=0.0)
     ap.add_argument("--n-requests", type=int, default=64)
+    ap.add_argument("--max-side", type=int, default=256)
+    ap.add_argument("--multi-blocks-per-sm", type=int, default=0)
     ap.add_argument("--hist-lo", type=float, default=1e7)
     ap.add_argument("--hist-hi", type=float, default=1e9)
     ap.add_argument("--traffic-per-launch", type=float, default=None)

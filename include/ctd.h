@@ -49,6 +49,7 @@ typedef struct {
     int chunk;                /* histories a warp claims at a time (default 256)      */
     int flight_cap;           /* Woodcock flights a lane takes in a row, stopping early at a
                                  real interaction, before its warp moves on (default 4) */
+    int multi_blocks_per_sm;  /* grid of multi-request launches (batched, served; default 3) */
 } ctd_options;
 
 /* Material: the numbers the closed-form cross sections use (Sec. 2.1).
@@ -159,9 +160,9 @@ int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t s
  * Request r transports n_histories[r] histories of phantoms[r] (distinct
  * phantoms, each with its source and spectrum set, all on the same node grid)
  * with random numbers keyed by seeds[r], in n_batches (>= 2) batches.  Batch b
- * of every request runs in one launch whose warps draw histories from all
- * requests, followed by one fold over every request's grids; at most 12
- * distinct materials per call.  Each phantom's results are then read with
+ * of every request runs in one launch, in which each block works on one
+ * request at a time and moves on to the next when it runs out of histories,
+ * followed by one fold over every request's grids.  Each phantom's results are then read with
  * ctd_get_dose_and_stddev and equal those of a separate ctd_run with the same
  * arguments (up to the order of binary64 additions in the tallies); its
  * t_transport_s is the time of the shared launches.  Blocks until done. */

@@ -286,6 +286,32 @@ class Setup:
         return edep, counts
 
 
+    def transport_ranges(self, ranges, threads: int = 1):
+        """Transport a list of history ranges [(h0, h1), ...] on `threads` threads,
+        each thread with one deposit buffer for all its ranges; returns the summed
+        deposits and counts."""
+        nvox = self._rho.size
+        fn = lib().or_transport_f64 if self.precision == 64 else lib().or_transport_f32
+        threads = max(1, min(int(threads), len(ranges)))
+        bufs = [np.zeros(nvox, dtype=np.float64) for _ in range(threads)]
+        cnts = [OrCounts() for _ in range(threads)]
+
+        def work(i):
+            for a, b in ranges[i::threads]:
+                if fn(self.handle, a, b, _ptr(bufs[i], C.c_double), C.byref(cnts[i])) != 0:
+                    raise ValueError("oracle transport rejected its arguments")
+
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(work, range(threads)))
+        edep = bufs[0]
+        for b in bufs[1:]:
+            edep += b
+        counts = {k: sum(getattr(c, k) for c in cnts) for k in COUNT_KEYS}
+        for k in ("e_emitted", "e_escaped", "e_deposited"):
+            counts[k] = float(sum(getattr(c, k) for c in cnts))
+        return edep, counts
+
+
 # --------------------------------------------------------------------------
 # batch statistics (Sec. 2.2.1) and precision measures (Sec. 3.1)
 # --------------------------------------------------------------------------

@@ -129,16 +129,16 @@ struct ctd_ctx {
     bool own_stream = false;
     int num_sms = 0;
     int blocks_per_sm = 4;
+    int multi_blocks_per_sm = 3;   // multi-request launches hold more state per lane
     int threads = 256;
     int chunk = 256;
     int flight_cap = 4;
     std::map<int, std::unique_ptr<Phantom>> phantoms;
     int next_id = 1;
     std::vector<cudaEvent_t> events;
-    // multi-request launches: union tables, request and fold descriptors
-    DevBuf<float> u_tab, u_rs;
+    // multi-request launches: request and fold descriptors, claim counters
     DevBuf<ctd::RequestDesc> u_reqs;
-    DevBuf<uint64_t> u_off, u_tiles;
+    DevBuf<uint64_t> u_tiles;
     DevBuf<ctd::FoldDesc> u_folds;
     DevBuf<unsigned long long> u_work;
     // served form: all requests by id, the admission queue and the running set
@@ -147,9 +147,6 @@ struct ctd_ctx {
     int64_t next_req = 1;
     int max_active = 64;
     double reserve_bytes = 1.0 * (1ull << 30);
-    bool union_valid = false;
-    std::vector<std::array<uint8_t, 16>> union_maps;
-    int union_n = 0;
 };
 
 namespace {
@@ -264,7 +261,11 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     std::memset(&q, 0, sizeof(q));
     q.mat = P.mat.p;
     q.rho = P.rho.p;
+    q.tab = P.tab.p;
     q.mmax = P.mm.p;
+    q.rsurf = P.rs.p;
+    q.n_mat = static_cast<int>(P.mats.size());
+    q.work = P.work.p;
     q.nbins = static_cast<int>(P.w.size());
     q.bin_lo = P.bins.p;
     q.bin_hi = P.bins.p + q.nbins;
@@ -299,18 +300,15 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     q.awt = static_cast<float>((P.src.arc1_rad - P.src.arc0_rad) / (2.0 * ctd::kPi));
     q.mode = P.phys.mode;
     q.max_real = P.phys.max_real;
-    for (int m = 0; m < ctd::kMaxPhantomMaterials; ++m) q.mat_map[m] = static_cast<uint8_t>(m);
 }
 
 void fill_shared(Phantom &P, ctd::SharedTables &sh)
 {
-    sh.tab = P.tab.p;
     sh.csurf = P.cs.p;
-    sh.rsurf = P.rs.p;
-    sh.n_mat = static_cast<int>(P.mats.size());
     sh.n_e = P.n_e;
     sh.n_zeta = P.phys.n_zeta;
     sh.e_min = P.phys.e_min_kev;
+    sh.max_n_mat = static_cast<int>(P.mats.size());
 }
 
 cudaEvent_t event_at(ctd_ctx *ctx, size_t i)
@@ -335,8 +333,8 @@ int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uin
     q.local_begin = lb;
     q.local_end = le;
     q.tally = tally;
+    q.work = P.work.p;
     L.one = q;
-    L.work = P.work.p;
     L.chunk = ctx->chunk;
     L.flight_cap = ctx->flight_cap;
     CK(cudaMemsetAsync(P.work.p, 0, sizeof(unsigned long long), ctx->stream));
@@ -417,12 +415,13 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
     if (opt) {
         ctx->device = opt->device;
         if (opt->blocks_per_sm > 0) ctx->blocks_per_sm = opt->blocks_per_sm;
+        if (opt->multi_blocks_per_sm > 0) ctx->multi_blocks_per_sm = opt->multi_blocks_per_sm;
         if (opt->threads_per_block > 0) ctx->threads = opt->threads_per_block;
         if (opt->chunk > 0) ctx->chunk = opt->chunk;
         if (opt->flight_cap > 0) ctx->flight_cap = opt->flight_cap;
     }
     if (ctx->threads % 32 != 0 || ctx->threads > 256) return fail(CTD_EINVAL, "threads_per_block must be a multiple of 32 and at most 256");
-    if (ctx->blocks_per_sm > 64) return fail(CTD_EINVAL, "blocks_per_sm at most 64");
+    if (ctx->blocks_per_sm > 64 || ctx->multi_blocks_per_sm > 64) return fail(CTD_EINVAL, "blocks_per_sm at most 64");
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
     if (ctx->device < 0 || ctx->device >= ndev) return fail(CTD_EINVAL, "device %d out of range (%d devices)", ctx->device, ndev);
@@ -640,54 +639,6 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
 
 namespace {
 
-constexpr int kMaxUnionMaterials = 12;
-
-bool same_material(const ctd_material &a, const ctd_material &b)
-{
-    return a.z_over_a == b.z_over_a && a.a_mol == b.a_mol && a.z_eff == b.z_eff && a.q0 == b.q0;
-}
-
-// Union of the requests' materials: tables and R surfaces copied from the
-// phantoms' own rows (equal materials have equal rows), mat_map per request.
-int build_union(ctd_ctx *ctx, const std::vector<Phantom *> &ps, std::vector<std::array<uint8_t, 16>> &maps, int &n_um)
-{
-    std::vector<ctd_material> um;
-    std::vector<std::pair<int, int>> src;   // (request, material) that supplies each union row
-    maps.assign(ps.size(), {});
-    for (size_t r = 0; r < ps.size(); ++r) {
-        for (size_t m = 0; m < ps[r]->mats.size(); ++m) {
-            int k = -1;
-            for (size_t u = 0; u < um.size(); ++u)
-                if (same_material(um[u], ps[r]->mats[m])) k = static_cast<int>(u);
-            if (k < 0) {
-                if (um.size() >= static_cast<size_t>(kMaxUnionMaterials))
-                    return fail(CTD_EINVAL, "more than %d distinct materials in one batch", kMaxUnionMaterials);
-                um.push_back(ps[r]->mats[m]);
-                src.emplace_back(static_cast<int>(r), static_cast<int>(m));
-                k = static_cast<int>(um.size()) - 1;
-            }
-            maps[r][m] = static_cast<uint8_t>(k);
-        }
-    }
-    n_um = static_cast<int>(um.size());
-    const int n_e = ps[0]->n_e, nz = ps[0]->phys.n_zeta;
-    const size_t row = static_cast<size_t>(n_e) * nz;
-    std::vector<float> tab(static_cast<size_t>(n_um) * n_e * 4), rs(static_cast<size_t>(n_um) * row);
-    for (int u = 0; u < n_um; ++u) {
-        const Phantom &P = *ps[src[u].first];
-        const int m = src[u].second;
-        std::memcpy(&tab[static_cast<size_t>(u) * n_e * 4], &P.h_tab[static_cast<size_t>(m) * n_e * 4],
-                    sizeof(float) * n_e * 4);
-        std::memcpy(&rs[static_cast<size_t>(u) * row], &P.h_rs[static_cast<size_t>(m) * row], sizeof(float) * row);
-    }
-    int rc;
-    if ((rc = ctx->u_tab.ensure(tab.size())) || (rc = ctx->u_rs.ensure(rs.size()))) return rc;
-    CK(cudaMemcpyAsync(ctx->u_tab.p, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->u_rs.p, rs.data(), rs.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return CTD_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -714,13 +665,11 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
         if (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta)
             return fail(CTD_EINVAL, "request %d has another node grid than request 0", r);
     }
-    std::vector<std::array<uint8_t, 16>> maps;
-    int n_um = 0;
-    ctx->union_valid = false;   // the served form's union tables are about to be overwritten
-    if ((rc = build_union(ctx, ps, maps, n_um))) return rc;
+    int max_n_mat = 0;
+    for (int r = 0; r < n_req; ++r) max_n_mat = std::max(max_n_mat, static_cast<int>(ps[r]->mats.size()));
+    if ((rc = ctx->u_work.ensure(static_cast<size_t>(n_batches) * n_req))) return rc;
     // descriptors for every batch of every request, the history and tile offsets
     std::vector<ctd::RequestDesc> descs(static_cast<size_t>(n_batches) * n_req);
-    std::vector<uint64_t> offs(static_cast<size_t>(n_batches) * (n_req + 1));
     std::vector<ctd::FoldDesc> folds(static_cast<size_t>(n_batches) * n_req);
     std::vector<uint64_t> tiles(n_req + 1, 0);
     for (int r = 0; r < n_req; ++r)
@@ -742,14 +691,12 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
             const int which = static_cast<uint64_t>(b) < rem ? 0 : 1;
             ctd::RequestDesc &q = descs[static_cast<size_t>(b) * n_req + r];
             fill_request(P, seeds[r], q);
-            std::memcpy(q.mat_map, maps[r].data(), sizeof(q.mat_map));
+            q.work = ctx->u_work.p + static_cast<size_t>(b) * n_req + r;
             q.pref = P.pref.p + which * (q.nbins + 1);
             q.h_base = h;
             q.local_begin = 0;
             q.local_end = nb;
             q.tally = P.tally.p;
-            uint64_t *o = &offs[static_cast<size_t>(b) * (n_req + 1)];
-            o[r + 1] = o[r] + nb;
             ctd::FoldDesc &f = folds[static_cast<size_t>(b) * n_req + r];
             f.tally = P.tally.p;
             f.rho = P.rho.p;
@@ -761,40 +708,32 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
             h += nb;
         }
     }
-    if ((rc = ctx->u_reqs.ensure(descs.size())) || (rc = ctx->u_off.ensure(offs.size())) ||
-        (rc = ctx->u_folds.ensure(folds.size())) || (rc = ctx->u_tiles.ensure(tiles.size())) ||
-        (rc = ctx->u_work.ensure(n_batches)))
+    if ((rc = ctx->u_reqs.ensure(descs.size())) ||
+        (rc = ctx->u_folds.ensure(folds.size())) || (rc = ctx->u_tiles.ensure(tiles.size())))
         return rc;
     CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), descs.size() * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice,
                        ctx->stream));
-    CK(cudaMemcpyAsync(ctx->u_off.p, offs.data(), offs.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), folds.size() * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
                        ctx->stream));
-    CK(cudaMemsetAsync(ctx->u_work.p, 0, n_batches * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long),
+                       ctx->stream));
     // batch b of every request in one launch, then one fold over every grid
     ctd::LaunchParams L;
     std::memset(&L, 0, sizeof(L));
-    L.sh.tab = ctx->u_tab.p;
-    L.sh.csurf = ps[0]->cs.p;
-    L.sh.rsurf = ctx->u_rs.p;
-    L.sh.n_mat = n_um;
-    L.sh.n_e = ps[0]->n_e;
-    L.sh.n_zeta = ps[0]->phys.n_zeta;
-    L.sh.e_min = ps[0]->phys.e_min_kev;
+    fill_shared(*ps[0], L.sh);
+    L.sh.max_n_mat = max_n_mat;
     L.n_req = n_req;
     L.chunk = ctx->chunk;
     L.flight_cap = ctx->flight_cap;
-    const int grid = ctx->num_sms * ctx->blocks_per_sm;
+    const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
     for (int b = 0; b < n_batches; ++b) {
         L.reqs = ctx->u_reqs.p + static_cast<size_t>(b) * n_req;
-        L.req_off = ctx->u_off.p + static_cast<size_t>(b) * (n_req + 1);
-        L.work = ctx->u_work.p + b;
         cudaEvent_t e0 = event_at(ctx, 2 * b), e1 = event_at(ctx, 2 * b + 1);
         if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
         CK(cudaEventRecord(e0, ctx->stream));
-        CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream));
+        CKS(ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, ctx->stream));
         CK(cudaEventRecord(e1, ctx->stream));
         CKS(ctd::launch_fold_multi(ctx->u_folds.p + static_cast<size_t>(b) * n_req, ctx->u_tiles.p, n_req, tiles[n_req],
                                    ctx->stream));
@@ -990,7 +929,6 @@ int admit(ctd_ctx *ctx)
         R.t_start = now_s();
         ctx->active.push_back(R.id);
         ctx->pending.erase(ctx->pending.begin());
-        ctx->union_valid = false;
     }
     return CTD_OK;
 }
@@ -1006,7 +944,6 @@ void retire(ctd_ctx *ctx, ServeReq &R, int state)
             ctx->active.erase(ctx->active.begin() + i);
             break;
         }
-    ctx->union_valid = false;
 }
 
 }  // namespace
@@ -1064,12 +1001,12 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
             return fail(CTD_EINVAL, "served requests must share one node grid");
         }
     }
-    if (!ctx->union_valid) {
-        if ((rc = build_union(ctx, ps, ctx->union_maps, ctx->union_n))) return rc;
-        ctx->union_valid = true;
-    }
+    int max_n_mat = 0;
+    for (int i = 0; i < n; ++i) max_n_mat = std::max(max_n_mat, static_cast<int>(ps[i]->mats.size()));
+    int rc2;
+    if ((rc2 = ctx->u_work.ensure(n))) return rc2;
     std::vector<ctd::RequestDesc> descs(n);
-    std::vector<uint64_t> offs(n + 1, 0), tiles(n + 1, 0);
+    std::vector<uint64_t> tiles(n + 1, 0);
     std::vector<ctd::FoldDesc> folds(n);
     for (int i = 0; i < n; ++i) {
         ServeReq &R = ctx->sreqs[ctx->active[i]];
@@ -1077,13 +1014,12 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
         const uint64_t B = R.req.batch_histories;
         ctd::RequestDesc &q = descs[i];
         fill_request(P, R.req.seed, q);
-        std::memcpy(q.mat_map, ctx->union_maps[i].data(), sizeof(q.mat_map));
+        q.work = ctx->u_work.p + i;
         q.pref = P.pref.p + 1 * (q.nbins + 1);    // batches of exactly B histories
         q.h_base = static_cast<uint64_t>(R.batches) * B;
         q.local_begin = 0;
         q.local_end = B;
         q.tally = P.tally.p;
-        offs[i + 1] = offs[i] + B;
         tiles[i + 1] = tiles[i] + (P.nvox + ctd::kFoldTile - 1) / ctd::kFoldTile;
         ctd::FoldDesc &f = folds[i];
         f.tally = P.tally.p;
@@ -1094,31 +1030,23 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
         f.nvox = P.nvox;
         f.scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
     }
-    if ((rc = ctx->u_reqs.ensure(n)) || (rc = ctx->u_off.ensure(n + 1)) || (rc = ctx->u_folds.ensure(n)) ||
-        (rc = ctx->u_tiles.ensure(n + 1)) || (rc = ctx->u_work.ensure(1)))
+    if ((rc = ctx->u_reqs.ensure(n)) || (rc = ctx->u_folds.ensure(n)) ||
+        (rc = ctx->u_tiles.ensure(n + 1)))
         return rc;
     CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), n * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->u_off.p, offs.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), n * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemsetAsync(ctx->u_work.p, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->u_work.p, 0, n * sizeof(unsigned long long), ctx->stream));
     ctd::LaunchParams L;
     std::memset(&L, 0, sizeof(L));
-    L.sh.tab = ctx->u_tab.p;
-    L.sh.csurf = ps[0]->cs.p;
-    L.sh.rsurf = ctx->u_rs.p;
-    L.sh.n_mat = ctx->union_n;
-    L.sh.n_e = ps[0]->n_e;
-    L.sh.n_zeta = ps[0]->phys.n_zeta;
-    L.sh.e_min = ps[0]->phys.e_min_kev;
+    fill_shared(*ps[0], L.sh);
+    L.sh.max_n_mat = max_n_mat;
     L.reqs = ctx->u_reqs.p;
-    L.req_off = ctx->u_off.p;
     L.n_req = n;
-    L.work = ctx->u_work.p;
     L.chunk = ctx->chunk;
     L.flight_cap = ctx->flight_cap;
-    const int grid = ctx->num_sms * ctx->blocks_per_sm;
-    CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream));
+    const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
+    CKS(ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, ctx->stream));
     CKS(ctd::launch_fold_multi(ctx->u_folds.p, ctx->u_tiles.p, n, tiles[n], ctx->stream));
     std::vector<int> checked;
     for (int i = 0; i < n; ++i) {

@@ -58,11 +58,14 @@ enum { kCntPe = 0, kCntCompton, kCntRayleigh, kCntFict, kCntEscaped, kCntMissed,
 
 // One request's share of a transport launch.  A single-request launch passes
 // it by value (the kernel's parameter space); a multi-request launch passes an
-// array of them in device memory and each lane reads its own photon's entry.
-struct RequestDesc {
+// array of them in device memory, and each block copies the entry of the
+// request it is working on into shared memory.
+struct alignas(16) RequestDesc {
     const uint8_t *mat;          // [nvox] material of the phantom
     const float *rho;            // [nvox] g/cm^3
+    const float *tab;            // [n_mat][n_e][4]: c1, c2, c3, 0 (cm^2/g)
     const float *mmax;           // [n_e] majorant mu_max(E), 1/cm
+    const float *rsurf;          // [n_mat][n_e][n_zeta] R surfaces
     const uint64_t *pref;        // [nbins+1] bin starts inside the batch
     const float *bin_lo;         // [nbins]
     const float *bin_hi;         // [nbins]
@@ -70,9 +73,11 @@ struct RequestDesc {
     const float *sb;             // [n_proj]
     double *tally;               // [nvox] keV
     DeviceCounts *counts;
+    unsigned long long *work;    // claim counter over [local_begin, local_end)
     uint64_t seed;
     uint64_t h_base;             // global index of local index 0 (first history of the batch)
     uint64_t local_begin, local_end;
+    int n_mat;
     int nbins;
     int nx, ny, nz;
     float bx0, by0, bz0, bx1, by1, bz1;
@@ -80,26 +85,25 @@ struct RequestDesc {
     int src_kind, n_proj, continuous;
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
     int mode, max_real;
-    uint8_t mat_map[16];         // phantom material -> row of the launch's tables
 };
+
+// blocks copy a descriptor into shared memory in 16-byte words
+static_assert(sizeof(RequestDesc) % 16 == 0, "RequestDesc must be a whole number of 16-byte words");
 
 constexpr int kMaxPhantomMaterials = 16;
 
-// Tables shared by every request of a launch.
+// What every request of a launch shares: the node grid and the C surface.
 struct SharedTables {
-    const float *tab;            // [n_mat][n_e][4]: c1, c2, c3, 0 (cm^2/g)
     const float *csurf;          // [n_e][n_zeta]
-    const float *rsurf;          // [n_mat][n_e][n_zeta]
-    int n_mat, n_e, n_zeta, e_min;
+    int n_e, n_zeta, e_min;
+    int max_n_mat;               // largest n_mat of the launch's requests (shared-memory size)
 };
 
 struct LaunchParams {
     SharedTables sh;
     RequestDesc one;             // the request of a single-request launch
-    const RequestDesc *reqs;     // [n_req] (multi-request launches)
-    const uint64_t *req_off;     // [n_req+1] prefix of the requests' history counts
+    const RequestDesc *reqs;     // [n_req] (multi-request launches; n_req == 0: single)
     int n_req;
-    unsigned long long *work;    // claim counter
     int chunk;                   // histories a warp claims at a time
     int flight_cap;              // Woodcock flights a lane takes before yielding to the warp
 };

@@ -11,9 +11,8 @@
 // C or R surface (Secs. 2.2.2-2.2.3), rotation.
 //
 // One kernel template serves one request (its parameters in the kernel's
-// parameter space, its tables in shared memory) and many requests at once (a
-// request table in device memory, each photon carrying its request index,
-// the union of the requests' material tables in shared memory).
+// parameter space) and many requests at once (blocks walk through a request
+// table, one request at a time, its descriptor and tables in shared memory).
 #include "ctd_device.cuh"
 
 namespace ctd {
@@ -26,63 +25,48 @@ struct Photon {
     uint64_t h;
     uint32_t step;
     int nreal;
-    int r;            // request index (multi-request launches)
 };
 
+// Event counts of a lane, in registers.
 struct LaneCounts {
     uint32_t n[10];
     unsigned long long e_emitted, e_escaped;   // keV * 2^23
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) n[i] = 0;
+        e_emitted = 0;
+        e_escaped = 0;
+    }
+    __device__ __forceinline__ void event(int k) { n[k]++; }
+    __device__ __forceinline__ void emitted(float e) { e_emitted += kev_fixed(e); }
+    __device__ __forceinline__ void escaped(float e) { e_escaped += kev_fixed(e); }
 };
 
-__device__ __forceinline__ void clear(LaneCounts &c)
+// A warp's counts added to a request's totals: warp sums, one atomic per
+// counter (energies as 128-bit fixed-point totals).  Leaves the counts cleared.
+__device__ __forceinline__ void flush_warp(DeviceCounts *dst, LaneCounts &c, int lane)
 {
 #pragma unroll
-    for (int i = 0; i < 10; ++i) c.n[i] = 0;
-    c.e_emitted = 0;
-    c.e_escaped = 0;
-}
-
-// Add a lane's counts to a request's totals (energies as 128-bit fixed point).
-__device__ __forceinline__ void flush_lane(DeviceCounts *dst, LaneCounts &c)
-{
+    for (int i = 0; i < 10; ++i) {
+        unsigned long long v = c.n[i];
 #pragma unroll
-    for (int i = 0; i < 10; ++i)
-        if (c.n[i]) atomicAdd(&dst->n[i], static_cast<unsigned long long>(c.n[i]));
-    if (c.e_emitted) {
-        const unsigned long long o = atomicAdd(&dst->e_fix[0], c.e_emitted);
-        if (o + c.e_emitted < o) atomicAdd(&dst->e_fix[1], 1ull);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+        if (lane == 0 && v) atomicAdd(&dst->n[i], v);
     }
-    if (c.e_escaped) {
-        const unsigned long long o = atomicAdd(&dst->e_fix[2], c.e_escaped);
-        if (o + c.e_escaped < o) atomicAdd(&dst->e_fix[3], 1ull);
+    unsigned long long em = c.e_emitted, es = c.e_escaped;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        em += __shfl_down_sync(kFull, em, o);
+        es += __shfl_down_sync(kFull, es, o);
     }
-    clear(c);
-}
-
-// Counts of a lane belong to one request at a time; switching flushes them.
-template <bool kMulti>
-struct Counter {
-    LaneCounts c;
-    int owner;
-    __device__ __forceinline__ void begin()
-    {
-        clear(c);
-        owner = 0;
+    if (lane == 0) {
+        const unsigned long long o1 = atomicAdd(&dst->e_fix[0], em);
+        if (o1 + em < o1) atomicAdd(&dst->e_fix[1], 1ull);
+        const unsigned long long o2 = atomicAdd(&dst->e_fix[2], es);
+        if (o2 + es < o2) atomicAdd(&dst->e_fix[3], 1ull);
     }
-    __device__ __forceinline__ LaneCounts &to(const LaunchParams &P, int r)
-    {
-        if (kMulti && r != owner) {
-            flush_lane(P.reqs[owner].counts, c);
-            owner = r;
-        }
-        return c;
-    }
-};
-
-template <bool kMulti>
-__device__ __forceinline__ const RequestDesc &req(const LaunchParams &P, int r)
-{
-    return kMulti ? P.reqs[r] : P.one;
+    c.clear();
 }
 
 __device__ __forceinline__ int bin_search(const RequestDesc &q, uint64_t local)
@@ -107,7 +91,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     const U4 b0 = block(q.seed, h, 0, kStreamSource);
     const float elo = __ldg(&q.bin_lo[bin]), ehi = __ldg(&q.bin_hi[bin]);
     const float e = elo + (ehi - elo) * uni(b0.x);
-    cnt.e_emitted += kev_fixed(e);
+    cnt.emitted(e);
     float cb = 1.0f, sb = 0.0f;
     if (q.src_kind == CTD_SRC_ARC) {
         if (q.continuous) {
@@ -136,8 +120,8 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
         }
     }
     if (!accepted) {
-        cnt.n[kCntAborted]++;
-        cnt.e_escaped += kev_fixed(e);
+        cnt.event(kCntAborted);
+        cnt.escaped(e);
         return false;
     }
     const float inv = 1.0f / sqrtf(qq);
@@ -165,8 +149,8 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
     const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
     if (!(tn < tf) || !(tf > 0.0f)) {
-        cnt.n[kCntMissed]++;
-        cnt.e_escaped += kev_fixed(e);
+        cnt.event(kCntMissed);
+        cnt.escaped(e);
         return false;
     }
     if (tn < 0.0f) tn = 0.0f;
@@ -184,7 +168,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
 // Site of a real interaction found by a flight
 struct Hit {
     size_t idx;       // voxel
-    int m;            // row of the tables
+    int m;            // material
     int j;            // energy node
     float te;         // energy fraction
     int type;         // 0 photoelectric, 1 Compton, 2 Rayleigh
@@ -193,36 +177,24 @@ struct Hit {
 
 enum { kEnded = 0, kFictitious = 1, kReal = 2 };
 
-struct Smem {
-    const float4 *tab;    // [n_mat][n_e]
-    const float *mm;      // [n_e] majorant of a single-request launch
-};
-
 // One Woodcock flight (Sec. 2.1): free path against mu_max(E), the move, the
-// escape test, the voxel and the interaction type.
-template <bool kMulti>
-__device__ __forceinline__ int flight(const LaunchParams &P, const RequestDesc &q, const Smem &sm, Photon &ph,
-                                      LaneCounts &cnt, Hit &hit)
+// escape test, the voxel and the interaction type.  s_tab and s_mm are the
+// request's attenuation table and majorant in shared memory.
+__device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc &q, const float4 *__restrict__ s_tab,
+                                      const float *__restrict__ s_mm, Photon &ph, LaneCounts &cnt, Hit &hit)
 {
     if (ph.step >= kMaxSteps) {
-        cnt.n[kCntAborted]++;
-        cnt.e_escaped += kev_fixed(ph.e);
+        cnt.event(kCntAborted);
+        cnt.escaped(ph.e);
         return kEnded;
     }
     const U4 b = block(q.seed, ph.h, ph.step, kStreamTransport);
     ph.step++;
     cnt.n[kCntSteps]++;
     float te;
-    const int n_e = P.sh.n_e;
-    const int j = enode(ph.e, P.sh.e_min, n_e, te);
-    float m0, m1;
-    if (kMulti) {
-        m0 = __ldg(&q.mmax[j]);
-        m1 = __ldg(&q.mmax[j + 1]);
-    } else {
-        m0 = sm.mm[j];
-        m1 = sm.mm[j + 1];
-    }
+    const int n_e = sh.n_e;
+    const int j = enode(ph.e, sh.e_min, n_e, te);
+    const float m0 = s_mm[j], m1 = s_mm[j + 1];
     const float mmax = m0 + te * (m1 - m0);
     const float path = (-log32(uni(b.x))) / mmax;
     ph.x = ph.x + path * ph.ux;
@@ -231,17 +203,16 @@ __device__ __forceinline__ int flight(const LaunchParams &P, const RequestDesc &
     const float fx = (ph.x - q.bx0) * q.ix, fy = (ph.y - q.by0) * q.iy, fz = (ph.z - q.bz0) * q.iz;
     if (!(fx >= 0.0f && fx < static_cast<float>(q.nx) && fy >= 0.0f && fy < static_cast<float>(q.ny) &&
           fz >= 0.0f && fz < static_cast<float>(q.nz))) {
-        cnt.n[kCntEscaped]++;
-        cnt.e_escaped += kev_fixed(ph.e);
+        cnt.event(kCntEscaped);
+        cnt.escaped(ph.e);
         return kEnded;
     }
     const size_t idx = static_cast<size_t>(static_cast<int>(fx)) +
                        static_cast<size_t>(q.nx) * (static_cast<size_t>(static_cast<int>(fy)) +
                                                     static_cast<size_t>(q.ny) * static_cast<size_t>(static_cast<int>(fz)));
-    int m = __ldg(&q.mat[idx]);
-    if (kMulti) m = q.mat_map[m];
+    const int m = __ldg(&q.mat[idx]);
     const float rho = __ldg(&q.rho[idx]);
-    const float4 A = sm.tab[m * n_e + j], B = sm.tab[m * n_e + j + 1];
+    const float4 A = s_tab[m * n_e + j], B = s_tab[m * n_e + j + 1];
     const float c1 = A.x + te * (B.x - A.x);
     const float c2 = A.y + te * (B.y - A.y);
     const float c3 = A.z + te * (B.z - A.z);
@@ -268,152 +239,127 @@ __device__ __forceinline__ int flight(const LaunchParams &P, const RequestDesc &
 
 // A real interaction: local deposition, C/R-surface polar angle, rotation.
 // Returns false when the history has ended.
-__device__ __forceinline__ bool interact(const LaunchParams &P, const RequestDesc &q, Photon &ph, const Hit &hit,
+__device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDesc &q, Photon &ph, const Hit &hit,
                                          LaneCounts &cnt)
 {
     ph.nreal++;
     if (hit.type == 0) {
         // photoelectric absorption: the electron deposits E here
-        cnt.n[kCntPe]++;
+        cnt.event(kCntPe);
         deposit(q.tally, hit.idx, ph.e);
         return false;
     }
-    const float *S = hit.type == 1 ? P.sh.csurf : P.sh.rsurf + static_cast<size_t>(hit.m) * P.sh.n_e * P.sh.n_zeta;
-    const float mu = surface(S, P.sh.n_zeta, hit.j, hit.te, uni(hit.rz));
+    const float *S = hit.type == 1 ? sh.csurf : q.rsurf + static_cast<size_t>(hit.m) * sh.n_e * sh.n_zeta;
+    const float mu = surface(S, sh.n_zeta, hit.j, hit.te, uni(hit.rz));
     if (hit.type == 1) {
         // Compton: E' = E / (1 + (E/mc^2)(1 - mu)), the electron gets E - E'
         cnt.n[kCntCompton]++;
         const float k = ph.e / static_cast<float>(kMec2);
         const float ep = ph.e / (1.0f + k * (1.0f - mu));
-        if (ep < static_cast<float>(P.sh.e_min)) {
-            cnt.n[kCntCutoff]++;
+        if (ep < static_cast<float>(sh.e_min)) {
+            cnt.event(kCntCutoff);
             deposit(q.tally, hit.idx, ph.e);
             return false;
         }
         deposit(q.tally, hit.idx, ph.e - ep);
         ph.e = ep;
     } else {
-        cnt.n[kCntRayleigh]++;
+        cnt.event(kCntRayleigh);
     }
     if (q.mode == CTD_MODE_MAX_REAL && ph.nreal >= q.max_real) {
-        cnt.n[kCntTerminated]++;
-        cnt.e_escaped += kev_fixed(ph.e);
+        cnt.event(kCntTerminated);
+        cnt.escaped(ph.e);
         return false;
     }
     rotate(ph.ux, ph.uy, ph.uz, mu, uni(hit.rw));
     return true;
 }
 
-// Flights until a real interaction, the escape, or flight_cap flights; then the
-// interaction.  Returns false when the history has ended.
-template <bool kMulti>
-__device__ __forceinline__ bool walk(const LaunchParams &P, const Smem &sm, Photon &ph, LaneCounts &cnt)
-{
-    const RequestDesc &q = req<kMulti>(P, ph.r);
-    Hit hit;
-    int f, k = 0;
-    do {
-        f = flight<kMulti>(P, q, sm, ph, cnt, hit);
-    } while (f == kFictitious && ++k < P.flight_cap);
-    if (f == kEnded) return false;
-    if (f == kFictitious) return true;
-    return interact(P, q, ph, hit, cnt);
-}
-
 // Per-warp photon queue in shared memory: source photons are made 32 at a
 // time by the whole warp and taken by lanes whose history has ended.
 constexpr int kQueue = 64;
-constexpr size_t kQueueBytes = kQueue * (7 * sizeof(float) + sizeof(uint64_t) + sizeof(int));
+constexpr size_t kQueueBytes = kQueue * (7 * sizeof(float) + sizeof(uint64_t));
 
-template <int kMinBlocks, bool kMulti>
-__global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const LaunchParams P)
+// A warp's claim of local history indices [next, end) and the 1 keV interval
+// of its first history, kept in shared memory (read only when the queue is
+// topped up).
+struct WarpPool {
+    uint64_t next, end;
+    int bin;
+    int pad[3];
+};
+
+struct Queue {
+    uint64_t *h;
+    float *f;   // [7][kQueue]: x y z ux uy uz e
+    WarpPool *pool;
+};
+
+constexpr size_t kWarpBytes = kQueueBytes + sizeof(WarpPool);
+
+// All histories [q.local_begin, q.local_end) of one request, claimed by warps
+// from q.work in runs of `chunk`.  Returns when the warp has no photon left.
+__device__ __forceinline__ void run_request(const LaunchParams &P, const RequestDesc &q, const float4 *s_tab,
+                                            const float *s_mm, const Queue &Q, int lane, LaneCounts &cnt)
 {
-    extern __shared__ float4 smem[];
-    float4 *s_tab = smem;
-    const int ntab = P.sh.n_mat * P.sh.n_e;
-    float *s_mm = reinterpret_cast<float *>(smem + ntab);
-    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = reinterpret_cast<const float4 *>(P.sh.tab)[i];
-    if (!kMulti)
-        for (int i = threadIdx.x; i < P.sh.n_e; i += blockDim.x) s_mm[i] = P.one.mmax[i];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *qbase =
-        reinterpret_cast<unsigned char *>(smem + ntab + (kMulti ? 0 : (P.sh.n_e + 3) / 4)) + warp * kQueueBytes;
-    uint64_t *qh = reinterpret_cast<uint64_t *>(qbase);
-    float *qf = reinterpret_cast<float *>(qh + kQueue);   // [7][kQueue]: x y z ux uy uz e
-    int *qr = reinterpret_cast<int *>(qf + 7 * kQueue);
-    __syncthreads();
-    const Smem sm{s_tab, s_mm};
-
     const unsigned lt_mask = (1u << lane) - 1u;
-    Counter<kMulti> cnt;
-    cnt.begin();
-
     Photon ph;
-    ph.r = 0;
     bool alive = false;
-    uint64_t pool_next = 0, pool_end = 0;   // warp-uniform claim (multi: over all requests' histories)
-    int pool_bin = 0;                       // 1 keV interval of the round's first history
-    int pool_req = 0;                       // request of pool_next (multi)
     bool drained = false;
     int qcount = 0;                         // photons waiting in the warp's queue
-    const uint64_t range_begin = kMulti ? 0 : P.one.local_begin;
-    const uint64_t range_end = kMulti ? P.req_off[P.n_req] : P.one.local_end;
+    if (lane == 0) {
+        Q.pool->next = 0;
+        Q.pool->end = 0;
+        Q.pool->bin = 0;
+    }
+    __syncwarp();
     for (;;) {
-        // top the queue up with one round of up to 32 source photons of one request
+        // top the queue up with one round of up to 32 source photons
         if (qcount < 32 && !drained) {
+            uint64_t pool_next = Q.pool->next, pool_end = Q.pool->end;
+            int pool_bin = Q.pool->bin;
             if (pool_next >= pool_end) {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(P.work, static_cast<unsigned long long>(P.chunk));
+                if (lane == 0) base = atomicAdd(q.work, static_cast<unsigned long long>(P.chunk));
                 base = __shfl_sync(kFull, base, 0);
-                const uint64_t b = range_begin + base;
-                if (b >= range_end) {
+                const uint64_t b = q.local_begin + base;
+                if (b >= q.local_end) {
                     drained = true;
                 } else {
                     pool_next = b;
-                    pool_end = b + P.chunk < range_end ? b + P.chunk : range_end;
-                    if (!kMulti) pool_bin = bin_search(P.one, pool_next);
+                    pool_end = b + P.chunk < q.local_end ? b + P.chunk : q.local_end;
+                    pool_bin = bin_search(q, pool_next);
                 }
             }
             if (!drained) {
-                uint64_t avail = pool_end - pool_next;
-                uint64_t local = pool_next;
-                if (kMulti) {
-                    // the request holding pool_next; a round stops at its end
-                    int lo = 0, hi = P.n_req - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (__ldg(&P.req_off[mid]) <= pool_next) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    pool_req = lo;
-                    const uint64_t rend = __ldg(&P.req_off[lo + 1]);
-                    if (rend - pool_next < avail) avail = rend - pool_next;
-                    local = P.reqs[lo].local_begin + (pool_next - __ldg(&P.req_off[lo]));
-                    pool_bin = bin_search(P.reqs[lo], local);
-                }
+                const uint64_t avail = pool_end - pool_next;
                 const unsigned take = avail < 32 ? static_cast<unsigned>(avail) : 32u;
-                const RequestDesc &q = req<kMulti>(P, pool_req);
                 Photon np;
                 bool ok = false;
                 if (lane < take) {
-                    LaneCounts &c = cnt.to(P, pool_req);
-                    ok = source(q, q.h_base + local + lane, local + lane, pool_bin, np, c);
+                    const uint64_t local = pool_next + lane;
+                    ok = source(q, q.h_base + local, local, pool_bin, np, cnt);
                 }
                 const unsigned okm = __ballot_sync(kFull, ok);
                 if (ok) {
                     const int slot = qcount + __popc(okm & lt_mask);
-                    qh[slot] = np.h;
-                    qf[0 * kQueue + slot] = np.x;
-                    qf[1 * kQueue + slot] = np.y;
-                    qf[2 * kQueue + slot] = np.z;
-                    qf[3 * kQueue + slot] = np.ux;
-                    qf[4 * kQueue + slot] = np.uy;
-                    qf[5 * kQueue + slot] = np.uz;
-                    qf[6 * kQueue + slot] = np.e;
-                    qr[slot] = pool_req;
+                    Q.h[slot] = np.h;
+                    Q.f[0 * kQueue + slot] = np.x;
+                    Q.f[1 * kQueue + slot] = np.y;
+                    Q.f[2 * kQueue + slot] = np.z;
+                    Q.f[3 * kQueue + slot] = np.ux;
+                    Q.f[4 * kQueue + slot] = np.uy;
+                    Q.f[5 * kQueue + slot] = np.uz;
+                    Q.f[6 * kQueue + slot] = np.e;
                 }
                 qcount += __popc(okm);
                 pool_next += take;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                Q.pool->next = pool_next;
+                Q.pool->end = pool_end;
+                Q.pool->bin = pool_bin;
             }
             __syncwarp();
         }
@@ -424,15 +370,14 @@ __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const Launch
             const int rank = __popc(need & lt_mask);
             if (rank < npop) {
                 const int slot = qcount - 1 - rank;
-                ph.h = qh[slot];
-                ph.x = qf[0 * kQueue + slot];
-                ph.y = qf[1 * kQueue + slot];
-                ph.z = qf[2 * kQueue + slot];
-                ph.ux = qf[3 * kQueue + slot];
-                ph.uy = qf[4 * kQueue + slot];
-                ph.uz = qf[5 * kQueue + slot];
-                ph.e = qf[6 * kQueue + slot];
-                ph.r = qr[slot];
+                ph.h = Q.h[slot];
+                ph.x = Q.f[0 * kQueue + slot];
+                ph.y = Q.f[1 * kQueue + slot];
+                ph.z = Q.f[2 * kQueue + slot];
+                ph.ux = Q.f[3 * kQueue + slot];
+                ph.uy = Q.f[4 * kQueue + slot];
+                ph.uz = Q.f[5 * kQueue + slot];
+                ph.e = Q.f[6 * kQueue + slot];
                 ph.step = 0;
                 ph.nreal = 0;
                 alive = true;
@@ -444,33 +389,91 @@ __global__ void __launch_bounds__(256, kMinBlocks) transport_kernel(const Launch
             if (drained && qcount == 0) break;
             continue;
         }
-        if (alive) alive = walk<kMulti>(P, sm, ph, cnt.to(P, ph.r));
+        if (alive) {
+            // flights until a real interaction, the escape or flight_cap flights; then the interaction
+            Hit hit;
+            int f, k = 0;
+            do {
+                f = flight(P.sh, q, s_tab, s_mm, ph, cnt, hit);
+            } while (f == kFictitious && ++k < P.flight_cap);
+            if (f == kEnded) alive = false;
+            else if (f == kReal) alive = interact(P.sh, q, ph, hit, cnt);
+        }
     }
+}
 
-    if (kMulti) {
-        flush_lane(P.reqs[cnt.owner].counts, cnt.c);
+__device__ __forceinline__ void load_tables(const RequestDesc &q, int n_e, float4 *s_tab, float *s_mm)
+{
+    const int ntab = q.n_mat * n_e;
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = reinterpret_cast<const float4 *>(q.tab)[i];
+    for (int i = threadIdx.x; i < n_e; i += blockDim.x) s_mm[i] = q.mmax[i];
+}
+
+// Single request (kMulti = false): the request lives in the kernel's parameter
+// space.  Several requests: each block works on one request at a time, a copy
+// of its descriptor, attenuation table and majorant in shared memory, and when
+// that request has no history left to claim the block moves on to the next
+// one, so that one request's tail overlaps the next one's start.
+template <int kMaxThreads, int kMinBlocks, bool kMulti>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(const LaunchParams P)
+{
+    extern __shared__ float4 smem[];
+    const int n_e = P.sh.n_e;
+    float4 *s_tab = smem;
+    float *s_mm = reinterpret_cast<float *>(smem + P.sh.max_n_mat * n_e);
+    float4 *s_req4 = smem + P.sh.max_n_mat * n_e + (n_e + 3) / 4;
+    constexpr int kReqWords = sizeof(RequestDesc) / 16;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *wbase = reinterpret_cast<unsigned char *>(s_req4 + kReqWords) + warp * kWarpBytes;
+    Queue Q;
+    Q.h = reinterpret_cast<uint64_t *>(wbase);
+    Q.f = reinterpret_cast<float *>(Q.h + kQueue);
+    Q.pool = reinterpret_cast<WarpPool *>(wbase + kQueueBytes);
+    LaneCounts cnt;
+    cnt.clear();
+
+    if (!kMulti) {
+        load_tables(P.one, n_e, s_tab, s_mm);
+        __syncthreads();
+        run_request(P, P.one, s_tab, s_mm, Q, lane, cnt);
+        flush_warp(P.one.counts, cnt, lane);
         return;
     }
-    // single request: warp sums, one atomic per warp
-    LaneCounts &c = cnt.c;
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        unsigned long long v = c.n[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-        if (lane == 0 && v) atomicAdd(&P.one.counts->n[i], v);
-    }
-    unsigned long long em = c.e_emitted, es = c.e_escaped;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        em += __shfl_down_sync(kFull, em, o);
-        es += __shfl_down_sync(kFull, es, o);
-    }
-    if (lane == 0) {
-        const unsigned long long o1 = atomicAdd(&P.one.counts->e_fix[0], em);
-        if (o1 + em < o1) atomicAdd(&P.one.counts->e_fix[1], 1ull);
-        const unsigned long long o2 = atomicAdd(&P.one.counts->e_fix[2], es);
-        if (o2 + es < o2) atomicAdd(&P.one.counts->e_fix[3], 1ull);
+    // every block starts at the first request and walks forward to the next
+    // request with histories left, so that the blocks of an SM mostly work on
+    // one request (its phantom and tally stay in L2) and a request's tail
+    // overlaps the next one's start
+    __shared__ int s_r;
+    const RequestDesc &q = *reinterpret_cast<const RequestDesc *>(s_req4);
+    int r = 0;
+    for (int visited = 0;;) {
+        if (threadIdx.x == 0) {
+            int found = -1;
+            for (; visited + r < P.n_req; ++visited) {
+                const int rr = r + visited;
+                const RequestDesc &c = P.reqs[rr];
+                const unsigned long long claimed = *reinterpret_cast<volatile unsigned long long *>(c.work);
+                if (c.local_begin + claimed < c.local_end) {
+                    found = rr;
+                    break;
+                }
+            }
+            s_r = found;
+        }
+        __syncthreads();
+        const int cur = s_r;
+        if (cur < 0) break;
+        const float4 *src = reinterpret_cast<const float4 *>(P.reqs + cur);
+        for (int i = threadIdx.x; i < kReqWords; i += blockDim.x) s_req4[i] = src[i];
+        __syncthreads();
+        load_tables(q, n_e, s_tab, s_mm);
+        __syncthreads();
+        run_request(P, q, s_tab, s_mm, Q, lane, cnt);
+        flush_warp(q.counts, cnt, lane);
+        __syncthreads();
+        // the same request is exhausted now; continue the walk from it
+        r = cur;
+        visited = 0;
     }
 }
 
@@ -501,38 +504,44 @@ __global__ void eval_math_kernel(int fn, const float *x, float *out, size_t n)
     }
 }
 
-template <int kMinBlocks, bool kMulti>
+template <int kMaxThreads, int kMinBlocks, bool kMulti>
 int launch_t(const LaunchParams &p, int grid, int block, size_t smem, cudaStream_t stream)
 {
+    auto *k = transport_kernel<kMaxThreads, kMinBlocks, kMulti>;
     if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(transport_kernel<kMinBlocks, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem)) != cudaSuccess)
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
             return CTD_ECUDA;
     }
-    transport_kernel<kMinBlocks, kMulti><<<grid, block, smem, stream>>>(p);
+    k<<<grid, block, smem, stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? CTD_OK : CTD_ECUDA;
+}
+
+template <bool kMulti>
+int launch_m(const LaunchParams &p, int grid, int block, int threads_per_sm, size_t smem, cudaStream_t s)
+{
+    // the register budget follows the residency asked for (65536 registers per SM)
+    if (block <= 128 && threads_per_sm >= 896) return launch_t<128, 7, kMulti>(p, grid, block, smem, s);
+    if (threads_per_sm >= 1024) return launch_t<256, 4, kMulti>(p, grid, block, smem, s);
+    return launch_t<256, 3, kMulti>(p, grid, block, smem, s);
 }
 
 }  // namespace
 
 size_t transport_smem_bytes(const LaunchParams &p, int threads)
 {
-    const bool multi = p.n_req > 0;
-    return static_cast<size_t>(p.sh.n_mat) * p.sh.n_e * sizeof(float4) +
-           (multi ? 0 : static_cast<size_t>((p.sh.n_e + 3) / 4) * sizeof(float4)) +
-           static_cast<size_t>(threads / 32) * kQueueBytes;
+    return (static_cast<size_t>(p.sh.max_n_mat) * p.sh.n_e + (p.sh.n_e + 3) / 4 +
+            sizeof(RequestDesc) / 16) * sizeof(float4) +
+           static_cast<size_t>(threads / 32) * kWarpBytes;
 }
 
-// The register budget follows the residency asked for: 4 or more blocks of
-// 256 threads per SM cap the kernel at 64 registers, fewer at 85.
+// Kernel variants by residency: 4 blocks of 256 threads per SM cap it at 64
+// registers, 7 blocks of 128 at 73, fewer at 85.
 int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t smem = transport_smem_bytes(p, block);
-    const bool multi = p.n_req > 0;
-    if (threads_per_sm >= 1024)
-        return multi ? launch_t<4, true>(p, grid, block, smem, s) : launch_t<4, false>(p, grid, block, smem, s);
-    return multi ? launch_t<3, true>(p, grid, block, smem, s) : launch_t<3, false>(p, grid, block, smem, s);
+    return p.n_req > 0 ? launch_m<true>(p, grid, block, threads_per_sm, smem, s)
+                       : launch_m<false>(p, grid, block, threads_per_sm, smem, s);
 }
 
 int launch_sample_mu(const float *surf, int n_zeta, int n_e, int e_min, float e, uint64_t seed, uint64_t n,

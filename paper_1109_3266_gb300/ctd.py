@@ -30,7 +30,8 @@ class CtdError(RuntimeError):
 
 class ctd_options(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("blocks_per_sm", C.c_int),
-                ("threads_per_block", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int)]
+                ("threads_per_block", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int),
+                ("multi_blocks_per_sm", C.c_int)]
 
 
 class ctd_material(C.Structure):
@@ -126,9 +127,10 @@ def _dp(a):
 
 
 # --------------------------------------------------------------------------- C names
-def ctd_create(device=0, stream=None, blocks_per_sm=0, threads_per_block=0, chunk=0, flight_cap=0):
+def ctd_create(device=0, stream=None, blocks_per_sm=0, threads_per_block=0, chunk=0, flight_cap=0,
+               multi_blocks_per_sm=0):
     """Context handle.  stream: a CUDA stream handle (int), e.g. torch's current stream."""
-    opt = ctd_options(device, stream or None, blocks_per_sm, threads_per_block, chunk, flight_cap)
+    opt = ctd_options(device, stream or None, blocks_per_sm, threads_per_block, chunk, flight_cap, multi_blocks_per_sm)
     h = C.c_void_p()
     _check(lib().ctd_create(C.byref(h), C.byref(opt)))
     return h

@@ -37,6 +37,16 @@ SM_COUNT = 152
 LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes issue per SM clock
 
 
+# Transport-kernel figures from one ncu capture of one launch of the same workload
+# (profiles/transport_kernel_*_full.md): lane instructions per history
+# (smsp__inst_executed x thread-per-instruction ratio / histories) and DRAM
+# bytes per launch (dram__bytes_read + dram__bytes_write).
+KERNEL_PROFILE = {
+    "cbct_water": {"lane_inst_per_history": 3254.0, "dram_bytes_per_launch": 13.60e9, "histories_per_launch": 1e8},
+    "head": {"lane_inst_per_history": 5219.0, "dram_bytes_per_launch": 23.21e9, "histories_per_launch": 2e8},
+}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -303,10 +313,13 @@ def run_ours(args):
     ck = clk.summary()
     mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = SM_COUNT * LANES_PER_SM_CLK * mhz * 1e6 / 1e12        # tera lane-instructions / s
-    inst_per_hist = args.inst_per_history
+    prof = KERNEL_PROFILE.get(p.name, {})
+    inst_per_hist = args.inst_per_history or prof.get("lane_inst_per_history")
     achieved = p.n_hist * args.steps * inst_per_hist / t_transport / 1e12 if inst_per_hist else None
+    traffic = args.traffic_per_launch or prof.get("dram_bytes_per_launch")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-inst/s",
-            "frac": achieved / peak if achieved else None, "traffic": args.traffic_per_launch,
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "lane_inst_per_history": inst_per_hist,
             "kernel": "transport_kernel", "launches": launches,
             "avg_launch_ms": 1e3 * t_transport / max(launches, 1),
             "peak_source": f"{SM_COUNT} SM x {LANES_PER_SM_CLK} lanes x {mhz:.0f} MHz ({peak_kind} max clock)"}
@@ -411,6 +424,51 @@ def run_batched(args):
     ctd.ctd_destroy(ctx)
 
 
+# --------------------------------------------------------------------------- served form
+def run_served(args):
+    """Poisson stream of head requests, each stopped at 1 % avg RSD: continuous
+    batching against one request at a time (the plain single-request form)."""
+    import torch
+
+    from paper_1109_3266_gb300 import ctd, inputs as I, serve
+
+    torch.cuda.set_device(0)
+    d = args.served_voxel_cm
+    nx, ny, nz = int(round(25.6 / d)), int(round(25.6 / d)), int(round(16.0 / d))
+    pool = [I.head_phantom(nx, ny, nz, d, seed=3 + k) for k in range(args.pool)]
+    arrivals = I.served_arrivals(args.n_requests, args.rate, seed=5)
+
+    def make(seed):
+        return I.head_request(pool[seed % len(pool)], seed)
+
+    out = {}
+    for label, max_active in (("continuous", 0), ("one_at_a_time", 1)):
+        ctx = ctd.ctd_create(device=0, multi_blocks_per_sm=args.multi_blocks_per_sm, serve_max_active=max_active)
+        # warm-up: one request alone
+        serve.serve(ctx, [(0.0, 4999)], make, args.batch_histories, 0.01, n_histories_max=40 * args.batch_histories)
+        with Clocks(0) as clk:
+            reqs, wall = serve.serve(ctx, arrivals, make, args.batch_histories, 0.01,
+                                     n_histories_max=40 * args.batch_histories, time_limit_s=args.time_limit)
+        done = [r for r in reqs if np.isfinite(r.latency)]
+        hist = sum(r.histories for r in done)
+        out[label] = dict(serve.latency_summary(reqs), histories_per_s=hist / wall, wall_s=wall,
+                          submitted=len(reqs), mean_batches=float(np.mean([r.batches for r in done])) if done else None,
+                          mean_histories=float(np.mean([r.histories for r in done])) if done else None,
+                          clocks=clk.summary())
+        ctd.ctd_destroy(ctx)
+    c, o = out["continuous"], out["one_at_a_time"]
+    print(json.dumps({
+        "metric": "served p50/p99 latency (s) and histories/sec at 1% avg RSD", "value": c["histories_per_s"],
+        "unit": UNIT, "p50_s": c["p50_s"], "p99_s": c["p99_s"], "n_gpus": 1, "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "served", "phantom": [nx, ny, nz], "voxel_cm": d, "rate_per_s": args.rate,
+                   "requests": args.n_requests, "batch_histories": args.batch_histories, "rsd_target": 0.01,
+                   "min_batches": 10, "phantom_pool": args.pool, "time_limit_s": args.time_limit},
+        "continuous": c, "one_at_a_time": o,
+        "throughput_vs_one_at_a_time": (c["histories_per_s"] / o["histories_per_s"]) if o["histories_per_s"] else None,
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,6 +487,11 @@ def main():
     ap.add_argument("--inst-per-history", type=float, default=0.0)
     ap.add_argument("--n-requests", type=int, default=64)
     ap.add_argument("--max-side", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=4.0)
+    ap.add_argument("--pool", type=int, default=4)
+    ap.add_argument("--served-voxel-cm", type=float, default=0.1)
+    ap.add_argument("--batch-histories", type=int, default=int(9e9))
+    ap.add_argument("--time-limit", type=float, default=None)
     ap.add_argument("--multi-blocks-per-sm", type=int, default=0)
     ap.add_argument("--hist-lo", type=float, default=1e7)
     ap.add_argument("--hist-hi", type=float, default=1e9)
@@ -438,6 +501,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

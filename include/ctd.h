@@ -50,6 +50,10 @@ typedef struct {
     int flight_cap;           /* Woodcock flights a lane takes in a row, stopping early at a
                                  real interaction, before its warp moves on (default 4) */
     int multi_blocks_per_sm;  /* grid of multi-request launches (batched, served; default 3) */
+    int serve_max_active;     /* served requests running at once (default 64)         */
+    double serve_round_histories; /* requests are admitted first in, first out while one
+                                 batch of every running request stays within this many
+                                 histories (default 1e8); one request always runs     */
 } ctd_options;
 
 /* Material: the numbers the closed-form cross sections use (Sec. 2.1).
@@ -173,8 +177,9 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
  * A request transports batches of batch_histories histories of a phantom with
  * random numbers keyed by seed until, after at least min_batches batches, its
  * avg RSD is <= rsd_target, or until n_histories_max histories have run.
- * Requests wait in a queue until admitted (free device memory above the
- * context's reserve and fewer than 64 running); each call of ctd_serve_step
+ * Requests wait in a queue until admitted, first in, first out (free device
+ * memory above the context's 1 GiB reserve, fewer than serve_max_active
+ * running, one round within serve_round_histories); each call of ctd_serve_step
  * admits what fits, runs one batch of every running request in one shared
  * launch, folds them, updates the statistics and retires finished requests.
  * A finished request's result equals ctd_run(phantom, k * batch_histories,
@@ -221,6 +226,24 @@ int ctd_wait(ctd_ctx *ctx, ctd_req_id id, double timeout_s, ctd_req_status *out)
 /* A queued request is dropped at once, a running one at the next round;
  * either ends as CTD_REQ_CANCELLED. */
 int ctd_cancel(ctd_ctx *ctx, ctd_req_id id);
+
+/* Autotuner: launch-shape search for the single-request transport kernel.
+ * It times probe launches of the phantom's current problem (its source,
+ * spectrum and physics; the first batch of 10 * n_probe histories with seed,
+ * that is n_probe histories over every 1 keV bin) for blocks per SM in {3, 4},
+ * claims of {64, 256, 1024} histories and flight caps of {1, 2, 4, 8}, and
+ * keeps the fastest shape in the context for later runs.  Results of a run do
+ * not depend on the launch shape (up to the order of binary64 additions). */
+typedef struct {
+    int blocks_per_sm;
+    int chunk;
+    int flight_cap;
+    int n_tried;
+    double histories_per_s;    /* of the chosen shape on the probe */
+    double baseline_per_s;     /* of the shape the context had before */
+} ctd_tune_result;
+
+int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, ctd_tune_result *out);
 
 /* Mean dose and its standard error (Gy per history, nvox doubles each; either
  * may be NULL) and the stats of the last ctd_run (stats may be NULL). */

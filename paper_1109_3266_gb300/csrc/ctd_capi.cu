@@ -2,6 +2,7 @@
 // source/spectrum/physics set-up, the batch loop of Sec. 2.2.1 and results.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -146,6 +147,11 @@ struct ctd_ctx {
     std::vector<int64_t> pending, active;
     int64_t next_req = 1;
     int max_active = 64;
+    double round_histories = 1e8;   // admission stops once a round would exceed this
+    // batched form: the captured batch loop and what it was captured for
+    cudaGraphExec_t batch_graph = nullptr;
+    std::vector<unsigned char> batch_graph_key;
+    cudaStream_t capture_stream = nullptr;
     double reserve_bytes = 1.0 * (1ull << 30);
 };
 
@@ -416,6 +422,8 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
         ctx->device = opt->device;
         if (opt->blocks_per_sm > 0) ctx->blocks_per_sm = opt->blocks_per_sm;
         if (opt->multi_blocks_per_sm > 0) ctx->multi_blocks_per_sm = opt->multi_blocks_per_sm;
+        if (opt->serve_max_active > 0) ctx->max_active = opt->serve_max_active;
+        if (opt->serve_round_histories > 0) ctx->round_histories = opt->serve_round_histories;
         if (opt->threads_per_block > 0) ctx->threads = opt->threads_per_block;
         if (opt->chunk > 0) ctx->chunk = opt->chunk;
         if (opt->flight_cap > 0) ctx->flight_cap = opt->flight_cap;
@@ -443,7 +451,9 @@ int ctd_destroy(ctd_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->phantoms.clear();
+    if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     for (auto e : ctx->events) cudaEventDestroy(e);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return CTD_OK;
@@ -717,8 +727,6 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
                        ctx->stream));
-    CK(cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long),
-                       ctx->stream));
     // batch b of every request in one launch, then one fold over every grid
     ctd::LaunchParams L;
     std::memset(&L, 0, sizeof(L));
@@ -728,16 +736,63 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
     L.chunk = ctx->chunk;
     L.flight_cap = ctx->flight_cap;
     const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
-    for (int b = 0; b < n_batches; ++b) {
-        L.reqs = ctx->u_reqs.p + static_cast<size_t>(b) * n_req;
-        cudaEvent_t e0 = event_at(ctx, 2 * b), e1 = event_at(ctx, 2 * b + 1);
-        if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
-        CK(cudaEventRecord(e0, ctx->stream));
-        CKS(ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, ctx->stream));
-        CK(cudaEventRecord(e1, ctx->stream));
-        CKS(ctd::launch_fold_multi(ctx->u_folds.p + static_cast<size_t>(b) * n_req, ctx->u_tiles.p, n_req, tiles[n_req],
-                                   ctx->stream));
+    for (int b = 0; b < n_batches; ++b)
+        if (!event_at(ctx, 2 * b) || !event_at(ctx, 2 * b + 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
+    // The batch loop (claim counters, n_batches shared launches with their timing
+    // events, the folds) is captured once into a CUDA graph and replayed while
+    // the descriptors, buffers and launch shape stay the same.
+    std::vector<unsigned char> key;
+    auto put = [&key](const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        key.insert(key.end(), c, c + n);
+    };
+    put(descs.data(), descs.size() * sizeof(ctd::RequestDesc));
+    put(folds.data(), folds.size() * sizeof(ctd::FoldDesc));
+    put(tiles.data(), tiles.size() * sizeof(uint64_t));
+    const void *bufs[4] = {ctx->u_reqs.p, ctx->u_folds.p, ctx->u_tiles.p, ctx->u_work.p};
+    put(bufs, sizeof(bufs));
+    const int shape[5] = {n_batches, mgrid, ctx->threads, ctx->multi_blocks_per_sm, static_cast<int>(L.sh.max_n_mat)};
+    put(shape, sizeof(shape));
+    put(&L, sizeof(L));
+    if (!ctx->batch_graph || key != ctx->batch_graph_key) {
+        if (ctx->batch_graph) {
+            cudaGraphExecDestroy(ctx->batch_graph);
+            ctx->batch_graph = nullptr;
+        }
+        if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = ctx->capture_stream;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int crc = CTD_OK;
+        if (cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long), cs) !=
+            cudaSuccess)
+            crc = CTD_ECUDA;
+        for (int b = 0; b < n_batches && crc == CTD_OK; ++b) {
+            L.reqs = ctx->u_reqs.p + static_cast<size_t>(b) * n_req;
+            if (cudaEventRecordWithFlags(ctx->events[2 * b], cs, cudaEventRecordExternal) != cudaSuccess) crc = CTD_ECUDA;
+            if (crc == CTD_OK)
+                crc = ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, cs);
+            if (crc == CTD_OK && cudaEventRecordWithFlags(ctx->events[2 * b + 1], cs, cudaEventRecordExternal) != cudaSuccess)
+                crc = CTD_ECUDA;
+            if (crc == CTD_OK)
+                crc = ctd::launch_fold_multi(ctx->u_folds.p + static_cast<size_t>(b) * n_req, ctx->u_tiles.p, n_req,
+                                             tiles[n_req], cs);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (crc != CTD_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(CTD_ECUDA, "capturing the batched launches failed");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->batch_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            ctx->batch_graph = nullptr;
+            return fail(CTD_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
+        }
+        ctx->batch_graph_key.swap(key);
     }
+    CK(cudaGraphLaunch(ctx->batch_graph, ctx->stream));
     for (int r = 0; r < n_req; ++r) {
         Phantom &P = *ps[r];
         CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, n_batches, P.dose.p, P.sd.p, P.nvox, ctx->stream));
@@ -898,8 +953,14 @@ double elapsed_since(double t) { return now_s() - t; }
 // Admit queued requests in order while memory and slots allow.
 int admit(ctd_ctx *ctx)
 {
+    double round = 0.0;
+    for (int64_t id : ctx->active) round += static_cast<double>(ctx->sreqs[id].req.batch_histories);
     while (!ctx->pending.empty() && static_cast<int>(ctx->active.size()) < ctx->max_active) {
         ServeReq &R = ctx->sreqs[ctx->pending.front()];
+        // first in, first out: a request joins the running set only while one round of
+        // every running request stays within the round budget (one request always may)
+        const double b = static_cast<double>(R.req.batch_histories);
+        if (!ctx->active.empty() && round + b > ctx->round_histories) break;
         Phantom *P = find(ctx, R.ph);
         if (!P) {
             R.state = CTD_REQ_FAILED;
@@ -927,6 +988,7 @@ int admit(ctd_ctx *ctx)
         P->have_result = false;
         R.state = CTD_REQ_RUNNING;
         R.t_start = now_s();
+        round += b;
         ctx->active.push_back(R.id);
         ctx->pending.erase(ctx->pending.begin());
     }
@@ -1152,6 +1214,77 @@ int ctd_cancel(ctd_ctx *ctx, ctd_req_id id)
         if (P) P->busy_req = 0;
     } else if (R.state == CTD_REQ_RUNNING) {
         R.cancel = true;
+    }
+    return CTD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+extern "C" {
+
+int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, ctd_tune_result *out)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if ((rc = busy(P))) return rc;
+    if (n_probe < 1000) return fail(CTD_EINVAL, "n_probe must be at least 1000");
+    const uint64_t n = 10 * n_probe;
+    if ((rc = prepare_run(ctx, *P, n, 10))) return rc;
+    P->have_result = false;
+    ctd::RequestDesc q;
+    fill_request(*P, seed, q);
+    const int old_bps = ctx->blocks_per_sm, old_chunk = ctx->chunk, old_cap = ctx->flight_cap;
+    struct Shape {
+        int bps, chunk, cap;
+    };
+    std::vector<Shape> shapes;
+    shapes.push_back({old_bps, old_chunk, old_cap});
+    for (int bps : {3, 4})
+        for (int chunk : {64, 256, 1024})
+            for (int cap : {1, 2, 4, 8})
+                if (!(bps == old_bps && chunk == old_chunk && cap == old_cap)) shapes.push_back({bps, chunk, cap});
+    double best = 1e300, base = 0.0;
+    Shape pick = shapes[0];
+    for (size_t k = 0; k < shapes.size(); ++k) {
+        ctx->blocks_per_sm = shapes[k].bps;
+        ctx->chunk = shapes[k].chunk;
+        ctx->flight_cap = shapes[k].cap;
+        double t_min = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+            if ((rc = transport(ctx, *P, q, 0, 0, 0, n_probe, P->tally.p, 0))) {
+                ctx->blocks_per_sm = old_bps;
+                ctx->chunk = old_chunk;
+                ctx->flight_cap = old_cap;
+                return rc;
+            }
+            CK(cudaStreamSynchronize(ctx->stream));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]));
+            t_min = std::min(t_min, static_cast<double>(ms) * 1e-3);
+        }
+        if (k == 0) base = t_min;
+        if (t_min < best) {
+            best = t_min;
+            pick = shapes[k];
+        }
+    }
+    CK(cudaMemsetAsync(P->tally.p, 0, P->nvox * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->blocks_per_sm = pick.bps;
+    ctx->chunk = pick.chunk;
+    ctx->flight_cap = pick.cap;
+    if (out) {
+        out->blocks_per_sm = pick.bps;
+        out->chunk = pick.chunk;
+        out->flight_cap = pick.cap;
+        out->n_tried = static_cast<int>(shapes.size());
+        out->histories_per_s = static_cast<double>(n_probe) / best;
+        out->baseline_per_s = static_cast<double>(n_probe) / base;
     }
     return CTD_OK;
 }

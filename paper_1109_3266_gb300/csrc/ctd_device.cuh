@@ -163,10 +163,14 @@ __device__ __forceinline__ unsigned long long kev_fixed(float e)
     return ex >= 0 ? (m << ex) : (m >> -ex);
 }
 
-// tally deposit of a non-negative binary32 energy into the binary64 grid
+// Tally deposit of a non-negative binary32 energy into the binary64 grid, as a
+// global reduction that returns nothing (a fire-and-forget L2 atomic), also
+// when the grid's address was read from shared memory.
 __device__ __forceinline__ void deposit(double *tally, size_t idx, float e)
 {
-    if (e > 0.0f) atomicAdd(tally + idx, widen(e));
+    if (e > 0.0f)
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(tally + idx)), "d"(widen(e))
+                     : "memory");
 }
 
 // New direction after a scatter of polar cosine mu and azimuth 2 pi tphi.

@@ -31,7 +31,8 @@ class CtdError(RuntimeError):
 class ctd_options(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("blocks_per_sm", C.c_int),
                 ("threads_per_block", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int),
-                ("multi_blocks_per_sm", C.c_int)]
+                ("multi_blocks_per_sm", C.c_int), ("serve_max_active", C.c_int),
+                ("serve_round_histories", C.c_double)]
 
 
 class ctd_material(C.Structure):
@@ -76,6 +77,14 @@ class ctd_req_status(C.Structure):
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(5)
 
+
+class ctd_tune_result(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int), ("n_tried", C.c_int),
+                ("histories_per_s", C.c_double), ("baseline_per_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 _lib = None
 
 
@@ -113,6 +122,7 @@ def lib():
         L.ctd_poll.argtypes = [P, C.c_int64, C.POINTER(ctd_req_status)]
         L.ctd_wait.argtypes = [P, C.c_int64, C.c_double, C.POINTER(ctd_req_status)]
         L.ctd_cancel.argtypes = [P, C.c_int64]
+        L.ctd_autotune.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.POINTER(ctd_tune_result)]
         _lib = L
     return _lib
 
@@ -128,9 +138,10 @@ def _dp(a):
 
 # --------------------------------------------------------------------------- C names
 def ctd_create(device=0, stream=None, blocks_per_sm=0, threads_per_block=0, chunk=0, flight_cap=0,
-               multi_blocks_per_sm=0):
+               multi_blocks_per_sm=0, serve_max_active=0, serve_round_histories=0.0):
     """Context handle.  stream: a CUDA stream handle (int), e.g. torch's current stream."""
-    opt = ctd_options(device, stream or None, blocks_per_sm, threads_per_block, chunk, flight_cap, multi_blocks_per_sm)
+    opt = ctd_options(device, stream or None, blocks_per_sm, threads_per_block, chunk, flight_cap, multi_blocks_per_sm,
+                      serve_max_active, float(serve_round_histories))
     h = C.c_void_p()
     _check(lib().ctd_create(C.byref(h), C.byref(opt)))
     return h
@@ -220,6 +231,13 @@ def ctd_wait(ctx, req_id, timeout_s):
 
 def ctd_cancel(ctx, req_id):
     _check(lib().ctd_cancel(ctx, int(req_id)))
+
+
+def ctd_autotune(ctx, ph, n_probe, seed=1):
+    """Pick the fastest launch shape for this phantom's problem; returns the choice."""
+    r = ctd_tune_result()
+    _check(lib().ctd_autotune(ctx, ph, int(n_probe), int(seed), C.byref(r)))
+    return r.as_dict()
 
 
 def ctd_run_range(ctx, ph, n_histories, seed, n_batches, h_begin, h_end, clear=True):

@@ -263,6 +263,15 @@ def head(n_hist: int = 2_000_000_000, n_batches: int = 10, seed: int = 3, phanto
                    n_hist, n_batches, seed)
 
 
+def head_request(phantom: Phantom, seed: int, kvp: int = 100, n_hist: int = 1) -> Problem:
+    """A served dose request on a given head phantom: 100 kVp half-fan CBCT,
+    transport seed `seed` (the phantom is shared data, the histories are not)."""
+    half_z = phantom.nz * phantom.dz / 2.0
+    src = arc_source(100.0, -1.0, 13.5, -half_z, half_z, n_proj=360)
+    return Problem(f"head_req{seed}", phantom, src, spectrum_kramers(kvp, 2.5), Physics(e_min=1, e_max=150),
+                   n_hist, 10, seed)
+
+
 def batched_requests(n_req: int = 64, seed: int = 4, hist_lo: float = 1e7, hist_hi: float = 1e9,
                      sides=tuple(range(64, 257, 32))) -> List[Problem]:
     """Uneven requests: cube side uniform on {64, 96, ..., 256} voxels of 0.1 cm,

@@ -143,3 +143,17 @@ def test_serve_loop_reports_latency(ctd, ctx):
     assert summ["done"] == 4 and summ["p50_s"] > 0 and summ["p99_s"] >= summ["p50_s"]
     for r in reqs:
         assert r.state == ctd.REQ_DONE and r.batches >= 10
+
+
+def test_autotune_picks_a_shape_and_results_do_not_depend_on_it(ctd, ctx):
+    p = problems()[0]
+    before = alone(ctd, ctx, p)
+    c2 = ctd.ctd_create(device=0)
+    h = ctd.load_problem(c2, p)
+    r = ctd.ctd_autotune(c2, h, 200_000, seed=5)
+    assert r["blocks_per_sm"] in (3, 4) and r["chunk"] in (64, 256, 1024) and r["flight_cap"] in (1, 2, 4, 8)
+    assert r["n_tried"] in (24, 25) and r["histories_per_s"] >= r["baseline_per_s"] * 0.999
+    ctd.ctd_run(c2, h, p.n_hist, p.seed, p.n_batches)
+    same(before, ctd.ctd_get_dose_and_stddev(c2, h, p.phantom.nvox))
+    ctd.ctd_destroy_phantom(c2, h)
+    ctd.ctd_destroy(c2)

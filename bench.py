@@ -377,15 +377,16 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     sides = tuple(range(64, args.max_side + 1, 32))
     reqs = I.batched_requests(args.n_requests, hist_lo=args.hist_lo, hist_hi=args.hist_hi, sides=sides)
-    ctx = ctd.ctd_create(device=0, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
-                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap,
-                         multi_blocks_per_sm=args.multi_blocks_per_sm)
-    hs = [ctd.load_problem(ctx, p) for p in reqs]
+    ctxs = [ctd.ctd_create(device=0, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
+                           threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap,
+                           multi_blocks_per_sm=args.multi_blocks_per_sm, shared_launch=k) for k in (0, 1)]
+    hss = [[ctd.load_problem(c, p) for p in reqs] for c in ctxs]
+    ctx, hs = ctxs[0], hss[0]
     n_total = sum(p.n_hist for p in reqs)
     nb = 10
 
-    def batched():
-        ctd.ctd_run_batch(ctx, hs, [p.n_hist for p in reqs], [p.seed for p in reqs], nb)
+    def batched(k=0):
+        ctd.ctd_run_batch(ctxs[k], hss[k], [p.n_hist for p in reqs], [p.seed for p in reqs], nb)
 
     def plain():
         for h, p in zip(hs, reqs):
@@ -404,24 +405,30 @@ def run_batched(args):
         return ts
 
     timed(batched, 1)
+    timed(lambda: batched(1), 1)
     with Clocks(0) as clk:
         tb = timed(batched, args.steps)
+        ts = timed(lambda: batched(1), max(1, args.steps // 2))
         tp = timed(plain, max(1, args.steps // 2))
     rsd = [ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)[2]["avg_rsd"] for h in hs]
     vb = n_total / float(np.mean(tb))
+    vs = n_total / float(np.mean(ts))
     vp = n_total / float(np.mean(tp))
     print(json.dumps({
         "metric": "photon histories/sec, batched form vs plain single-request form", "value": vb, "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * float(np.mean(tb)),
         "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "batched", "requests": len(reqs), "histories_per_step": n_total, "batches": nb,
-                   "sides": sorted({p.meta["side"] for p in reqs}), "hist_range": [args.hist_lo, args.hist_hi]},
+                   "sides": sorted({p.meta["side"] for p in reqs}), "hist_range": [args.hist_lo, args.hist_hi],
+                   "launches": "one chain of single-request launches per request, one CUDA graph"},
         "plain_value": vp, "plain_ms_per_step": 1e3 * float(np.mean(tp)), "speedup_vs_plain": vb / vp,
+        "shared_launch_value": vs, "shared_launch_speedup_vs_plain": vs / vp,
         "avg_rsd_range": [float(min(rsd)), float(max(rsd))], "clocks": clk.summary(),
     }), flush=True)
-    for h in hs:
-        ctd.ctd_destroy_phantom(ctx, h)
-    ctd.ctd_destroy(ctx)
+    for c, hl in zip(ctxs, hss):
+        for h in hl:
+            ctd.ctd_destroy_phantom(c, h)
+        ctd.ctd_destroy(c)
 
 
 # --------------------------------------------------------------------------- served form
@@ -443,7 +450,8 @@ def run_served(args):
 
     out = {}
     for label, max_active in (("continuous", 0), ("one_at_a_time", 1)):
-        ctx = ctd.ctd_create(device=0, multi_blocks_per_sm=args.multi_blocks_per_sm, serve_max_active=max_active)
+        ctx = ctd.ctd_create(device=0, multi_blocks_per_sm=args.multi_blocks_per_sm, serve_max_active=max_active,
+                             shared_launch=args.shared_launch)
         # warm-up: one request alone
         serve.serve(ctx, [(0.0, 4999)], make, args.batch_histories, 0.01, n_histories_max=40 * args.batch_histories)
         with Clocks(0) as clk:
@@ -463,7 +471,8 @@ def run_served(args):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "served", "phantom": [nx, ny, nz], "voxel_cm": d, "rate_per_s": args.rate,
                    "requests": args.n_requests, "batch_histories": args.batch_histories, "rsd_target": 0.01,
-                   "min_batches": 10, "phantom_pool": args.pool, "time_limit_s": args.time_limit},
+                   "min_batches": 10, "phantom_pool": args.pool, "time_limit_s": args.time_limit,
+                   "launches": "shared multi-request launch" if args.shared_launch else "one stream per request"},
         "continuous": c, "one_at_a_time": o,
         "throughput_vs_one_at_a_time": (c["histories_per_s"] / o["histories_per_s"]) if o["histories_per_s"] else None,
     }), flush=True)
@@ -493,6 +502,7 @@ def main():
     ap.add_argument("--batch-histories", type=int, default=int(9e9))
     ap.add_argument("--time-limit", type=float, default=None)
     ap.add_argument("--multi-blocks-per-sm", type=int, default=0)
+    ap.add_argument("--shared-launch", type=int, default=0, help="served form: one shared multi-request launch")
     ap.add_argument("--hist-lo", type=float, default=1e7)
     ap.add_argument("--hist-hi", type=float, default=1e9)
     ap.add_argument("--traffic-per-launch", type=float, default=None)

@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 1
+#define CTD_ABI_VERSION 2
 
 typedef enum {
     CTD_OK = 0,
@@ -54,6 +54,11 @@ typedef struct {
     double serve_round_histories; /* requests are admitted first in, first out while one
                                  batch of every running request stays within this many
                                  histories (default 1e8); one request always runs     */
+    int shared_launch;        /* batched and served forms: 0 (default) runs each request's
+                                 batches as its own chain of single-request launches on
+                                 its own stream, so that one request's tail overlaps the
+                                 next one's launch; 1 runs one multi-request launch per
+                                 batch shared by all requests                          */
 } ctd_options;
 
 /* Material: the numbers the closed-form cross sections use (Sec. 2.1).
@@ -160,16 +165,22 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
 int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches,
                   uint64_t h_begin, uint64_t h_end, int clear);
 
-/* Batched form: n_req dose calculations in shared persistent launches.
- * Request r transports n_histories[r] histories of phantoms[r] (distinct
- * phantoms, each with its source and spectrum set, all on the same node grid)
- * with random numbers keyed by seeds[r], in n_batches (>= 2) batches.  Batch b
- * of every request runs in one launch, in which each block works on one
- * request at a time and moves on to the next when it runs out of histories,
- * followed by one fold over every request's grids.  Each phantom's results are then read with
- * ctd_get_dose_and_stddev and equal those of a separate ctd_run with the same
- * arguments (up to the order of binary64 additions in the tallies); its
- * t_transport_s is the time of the shared launches.  Blocks until done. */
+/* Batched form: n_req dose calculations in one call.  Request r transports
+ * n_histories[r] histories of phantoms[r] (distinct phantoms, each with its
+ * source and spectrum set) with random numbers keyed by seeds[r], in n_batches
+ * (>= 2) batches.  The whole call is one CUDA graph, recorded once and replayed
+ * while the requests and the launch shape stay the same.  With shared_launch = 0
+ * each request is its own chain of single-request launches and folds on its own
+ * stream, and the device overlaps one chain's last blocks with the next chain's
+ * first ones; with shared_launch = 1 batch b of every request runs in one
+ * multi-request launch (each block works on one request at a time and moves on
+ * to the next when it runs out of histories; all requests on the same node
+ * grid, else CTD_EINVAL), followed by one fold over every request's grids.
+ * Each phantom's results are then read with ctd_get_dose_and_stddev and equal
+ * those of a separate ctd_run with the same arguments (up to the order of
+ * binary64 additions in the tallies); its t_transport_s is the device time of
+ * the whole graph (shared_launch = 0) or of its n_batches shared launches
+ * (shared_launch = 1).  Blocks until done. */
 int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const uint64_t *n_histories,
                   const uint64_t *seeds, int n_batches);
 
@@ -180,8 +191,10 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
  * Requests wait in a queue until admitted, first in, first out (free device
  * memory above the context's 1 GiB reserve, fewer than serve_max_active
  * running, one round within serve_round_histories); each call of ctd_serve_step
- * admits what fits, runs one batch of every running request in one shared
- * launch, folds them, updates the statistics and retires finished requests.
+ * admits what fits, runs one batch of every running request (each on its own
+ * stream, or with shared_launch = 1 in one shared launch, which needs every
+ * request on one node grid), folds them, updates the statistics and retires
+ * finished requests.
  * A finished request's result equals ctd_run(phantom, k * batch_histories,
  * seed, k) for its k batches (up to the order of binary64 additions), alone or
  * mixed with others, and is read with ctd_get_dose_and_stddev.  A phantom

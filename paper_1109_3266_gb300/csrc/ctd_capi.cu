@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -106,6 +107,11 @@ struct Phantom {
     int64_t busy_req = 0;      // served request using this phantom, 0 if none
 };
 
+struct Staged {
+    ctd::DeviceCounts c;
+    double res[4];    // avg RSD, sigma_bar, D_max, deposited energy
+};
+
 struct ServeReq {
     int64_t id = 0;
     int ph = 0;
@@ -153,6 +159,17 @@ struct ctd_ctx {
     std::vector<unsigned char> batch_graph_key;
     cudaStream_t capture_stream = nullptr;
     double reserve_bytes = 1.0 * (1ull << 30);
+    // batched and served forms: 0 runs each request as its own chain of
+    // single-request launches on its own stream (the device overlaps the chains),
+    // 1 shares one multi-request launch per batch among all requests
+    int shared_launch = 0;
+    Staged *staged = nullptr;      // pinned read-back of counts and results
+    size_t staged_n = 0;
+    // angular surfaces by (kind, q0, e_min, n_e, n_zeta): they do not depend on the phantom
+    std::map<std::array<double, 5>, std::vector<float>> surfaces;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_done;
+    cudaEvent_t fork_event = nullptr;
 };
 
 namespace {
@@ -180,6 +197,23 @@ int busy(Phantom *P)
                        : CTD_OK;
 }
 
+// C (kind 0) or R (kind 1, form-factor width q0) surface in binary32, built
+// once per context and node grid.
+const std::vector<float> &angular_surface(ctd_ctx *ctx, int kind, double q0, int e_min, int n_e, int n_zeta)
+{
+    const std::array<double, 5> key{static_cast<double>(kind), kind ? (q0 > 0.0 ? q0 : 0.0) : 0.0,
+                                    static_cast<double>(e_min), static_cast<double>(n_e), static_cast<double>(n_zeta)};
+    auto it = ctx->surfaces.find(key);
+    if (it != ctx->surfaces.end()) return it->second;
+    if (ctx->surfaces.size() >= 64) ctx->surfaces.clear();
+    const size_t row = static_cast<size_t>(n_e) * n_zeta;
+    std::vector<double> tmp(row);
+    ctd::build_surface(kind, q0, e_min, n_e, n_zeta, tmp.data());
+    std::vector<float> f(row);
+    for (size_t i = 0; i < row; ++i) f[i] = static_cast<float>(tmp[i]);
+    return ctx->surfaces.emplace(key, std::move(f)).first->second;
+}
+
 int build_tables(ctd_ctx *ctx, Phantom &P)
 {
     if (P.tables_ok) return CTD_OK;
@@ -194,14 +228,11 @@ int build_tables(ctd_ctx *ctx, Phantom &P)
     P.h_mm.resize(n_e);
     for (int j = 0; j < n_e; ++j) P.h_mm[j] = static_cast<float>(mmax[j]);
     const size_t row = static_cast<size_t>(n_e) * ph.n_zeta;
-    std::vector<double> tmp(row);
-    ctd::build_surface(0, 0.0, ph.e_min_kev, n_e, ph.n_zeta, tmp.data());
-    P.h_cs.resize(row);
-    for (size_t i = 0; i < row; ++i) P.h_cs[i] = static_cast<float>(tmp[i]);
+    P.h_cs = angular_surface(ctx, 0, 0.0, ph.e_min_kev, n_e, ph.n_zeta);
     P.h_rs.resize(row * nm);
     for (int m = 0; m < nm; ++m) {
-        ctd::build_surface(1, P.mats[m].q0, ph.e_min_kev, n_e, ph.n_zeta, tmp.data());
-        for (size_t i = 0; i < row; ++i) P.h_rs[m * row + i] = static_cast<float>(tmp[i]);
+        const std::vector<float> &r = angular_surface(ctx, 1, P.mats[m].q0, ph.e_min_kev, n_e, ph.n_zeta);
+        std::copy(r.begin(), r.end(), P.h_rs.begin() + m * row);
     }
     int rc;
     if ((rc = P.tab.ensure(P.h_tab.size())) || (rc = P.mm.ensure(n_e)) || (rc = P.cs.ensure(row)) ||
@@ -306,6 +337,13 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     q.awt = static_cast<float>((P.src.arc1_rad - P.src.arc0_rad) / (2.0 * ctd::kPi));
     q.mode = P.phys.mode;
     q.max_real = P.phys.max_real;
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        q.rk[2 * r] = k0;
+        q.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
 }
 
 void fill_shared(Phantom &P, ctd::SharedTables &sh)
@@ -325,6 +363,72 @@ cudaEvent_t event_at(ctd_ctx *ctx, size_t i)
         ctx->events.push_back(e);
     }
     return ctx->events[i];
+}
+
+// Streams for independent request chains; chain r runs on lane r % kMaxLanes.
+constexpr int kMaxLanes = 64;
+
+int ensure_lanes(ctd_ctx *ctx, int n)
+{
+    n = std::min(n, kMaxLanes);
+    while (static_cast<int>(ctx->lanes.size()) < n) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(s);
+            return fail(CTD_ECUDA, "cudaEventCreate failed");
+        }
+        ctx->lanes.push_back(s);
+        ctx->lane_done.push_back(e);
+    }
+    if (!ctx->fork_event) CK(cudaEventCreateWithFlags(&ctx->fork_event, cudaEventDisableTiming));
+    return CTD_OK;
+}
+
+// the first min(n, kMaxLanes) lanes start after everything issued so far on origin
+int fork_lanes(ctd_ctx *ctx, cudaStream_t origin, int n)
+{
+    CK(cudaEventRecord(ctx->fork_event, origin));
+    for (int i = 0; i < std::min(n, kMaxLanes); ++i) CK(cudaStreamWaitEvent(ctx->lanes[i], ctx->fork_event, 0));
+    return CTD_OK;
+}
+
+// origin continues after everything issued on those lanes
+int join_lanes(ctd_ctx *ctx, cudaStream_t origin, int n)
+{
+    for (int i = 0; i < std::min(n, kMaxLanes); ++i) {
+        CK(cudaEventRecord(ctx->lane_done[i], ctx->lanes[i]));
+        CK(cudaStreamWaitEvent(origin, ctx->lane_done[i], 0));
+    }
+    return CTD_OK;
+}
+
+cudaStream_t lane(ctd_ctx *ctx, int r) { return ctx->lanes[r % kMaxLanes]; }
+
+// One single-request launch of q (its tables from P) on stream s, at the
+// context's launch shape.
+int launch_one(ctd_ctx *ctx, Phantom &P, const ctd::RequestDesc &q, cudaStream_t s)
+{
+    ctd::LaunchParams L;
+    std::memset(&L, 0, sizeof(L));
+    fill_shared(P, L.sh);
+    L.one = q;
+    L.chunk = ctx->chunk;
+    L.flight_cap = ctx->flight_cap;
+    return ctd::launch_transport(L, ctx->num_sms * ctx->blocks_per_sm, ctx->threads,
+                                 ctx->threads * ctx->blocks_per_sm, s);
+}
+
+// Mean, standard error, avg RSD and deposited energy of a finished run of nb
+// batches, on stream s.
+int finish_stats(Phantom &P, int nb, cudaStream_t s)
+{
+    int e = ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, nb, P.dose.p, P.sd.p, P.nvox, s);
+    if (e == CTD_OK) e = ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, s);
+    if (e == CTD_OK)
+        e = ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, s);
+    return e;
 }
 
 // One transport launch over local histories [lb, le) of a batch starting at global h_base.
@@ -363,45 +467,80 @@ int prepare_run(ctd_ctx *ctx, Phantom &P, uint64_t n, int nb)
     return CTD_OK;
 }
 
-int collect(ctd_ctx *ctx, Phantom &P, size_t n_launch, double t0_wall)
-{
-    ctd::DeviceCounts c;
-    CK(cudaMemcpyAsync(&c, P.counts.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
-    double res[4];
-    CK(cudaMemcpyAsync(res, P.result.p, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    ctd_run_stats &s = P.stats;
-    s.pe = c.n[ctd::kCntPe];
-    s.compton = c.n[ctd::kCntCompton];
-    s.rayleigh = c.n[ctd::kCntRayleigh];
-    s.fictitious = c.n[ctd::kCntFict];
-    s.escaped = c.n[ctd::kCntEscaped];
-    s.missed = c.n[ctd::kCntMissed];
-    s.cutoff = c.n[ctd::kCntCutoff];
-    s.terminated = c.n[ctd::kCntTerminated];
-    s.aborted = c.n[ctd::kCntAborted];
-    s.steps = c.n[ctd::kCntSteps];
-    s.e_emitted_kev = ctd::fixed_kev(c.e_fix[0], c.e_fix[1]);
-    s.e_escaped_kev = ctd::fixed_kev(c.e_fix[2], c.e_fix[3]);
-    s.avg_rsd = res[0];
-    s.paper_sigma_bar = res[1];
-    s.d_max = res[2];
-    s.e_deposited_kev = res[3];
-    double tt = 0.0;
-    for (size_t i = 0; i < n_launch; ++i) {
-        float ms = 0.0f;
-        CK(cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]));
-        tt += ms * 1e-3;
-    }
-    s.t_transport_s = tt;
-    s.transport_launches = static_cast<int>(n_launch);
-    s.t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0_wall;
-    return CTD_OK;
-}
-
 double now_s()
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Device time of launches [0, n_launch) from their event pairs.
+int transport_time(ctd_ctx *ctx, size_t n_launch, double &t)
+{
+    t = 0.0;
+    for (size_t i = 0; i < n_launch; ++i) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]));
+        t += ms * 1e-3;
+    }
+    return CTD_OK;
+}
+
+// Counts, energies and precision figures of several phantoms read back in one
+// go (copies into pinned staging, one synchronisation).
+int collect_many(ctd_ctx *ctx, Phantom *const *ps, int n, size_t n_launch, double t0_wall,
+                 const double *t0_each = nullptr)
+{
+    if (static_cast<size_t>(n) > ctx->staged_n) {
+        if (ctx->staged) cudaFreeHost(ctx->staged);
+        ctx->staged = nullptr;
+        ctx->staged_n = 0;
+        if (cudaMallocHost(reinterpret_cast<void **>(&ctx->staged), n * sizeof(Staged)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CTD_ENOMEM, "cudaMallocHost failed");
+        }
+        ctx->staged_n = n;
+    }
+    for (int i = 0; i < n; ++i) {
+        CK(cudaMemcpyAsync(&ctx->staged[i].c, ps[i]->counts.p, sizeof(ctd::DeviceCounts), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->staged[i].res, ps[i]->result.p, sizeof(ctx->staged[i].res), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double t_now = now_s();
+    double t_transport;
+    int rc;
+    if ((rc = transport_time(ctx, n_launch, t_transport))) return rc;
+    for (int i = 0; i < n; ++i) {
+        const ctd::DeviceCounts &c = ctx->staged[i].c;
+        const double *res = ctx->staged[i].res;
+        ctd_run_stats &s = ps[i]->stats;
+        s.pe = c.n[ctd::kCntPe];
+        s.compton = c.n[ctd::kCntCompton];
+        s.rayleigh = c.n[ctd::kCntRayleigh];
+        s.fictitious = c.n[ctd::kCntFict];
+        s.escaped = c.n[ctd::kCntEscaped];
+        s.missed = c.n[ctd::kCntMissed];
+        s.cutoff = c.n[ctd::kCntCutoff];
+        s.terminated = c.n[ctd::kCntTerminated];
+        s.aborted = c.n[ctd::kCntAborted];
+        s.steps = c.n[ctd::kCntSteps];
+        s.e_emitted_kev = ctd::fixed_kev(c.e_fix[0], c.e_fix[1]);
+        s.e_escaped_kev = ctd::fixed_kev(c.e_fix[2], c.e_fix[3]);
+        s.avg_rsd = res[0];
+        s.paper_sigma_bar = res[1];
+        s.d_max = res[2];
+        s.e_deposited_kev = res[3];
+        s.t_transport_s = t_transport;
+        s.transport_launches = static_cast<int>(n_launch);
+        s.t_total_s = t_now - (t0_each ? t0_each[i] : t0_wall);
+    }
+    return CTD_OK;
+}
+
+int collect(ctd_ctx *ctx, Phantom &P, size_t n_launch, double t0_wall)
+{
+    Phantom *ps[1] = {&P};
+    return collect_many(ctx, ps, 1, n_launch, t0_wall);
 }
 
 }  // namespace
@@ -427,6 +566,7 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
         if (opt->threads_per_block > 0) ctx->threads = opt->threads_per_block;
         if (opt->chunk > 0) ctx->chunk = opt->chunk;
         if (opt->flight_cap > 0) ctx->flight_cap = opt->flight_cap;
+        ctx->shared_launch = opt->shared_launch != 0;
     }
     if (ctx->threads % 32 != 0 || ctx->threads > 256) return fail(CTD_EINVAL, "threads_per_block must be a multiple of 32 and at most 256");
     if (ctx->blocks_per_sm > 64 || ctx->multi_blocks_per_sm > 64) return fail(CTD_EINVAL, "blocks_per_sm at most 64");
@@ -454,6 +594,10 @@ int ctd_destroy(ctd_ctx *ctx)
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     for (auto e : ctx->events) cudaEventDestroy(e);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    for (auto l : ctx->lanes) cudaStreamDestroy(l);
+    for (auto e : ctx->lane_done) cudaEventDestroy(e);
+    if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
+    if (ctx->staged) cudaFreeHost(ctx->staged);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return CTD_OK;
@@ -671,8 +815,9 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
             return fail(CTD_EINVAL, "request %d has fewer histories than batches", r);
         if ((rc = busy(ps[r]))) return rc;
         if ((rc = prepare_run(ctx, *ps[r], n_histories[r], n_batches))) return rc;
+        // one shared launch holds one node grid and one angular surface size
         const ctd_physics &a = ps[0]->phys, &b = ps[r]->phys;
-        if (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta)
+        if (ctx->shared_launch && (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta))
             return fail(CTD_EINVAL, "request %d has another node grid than request 0", r);
     }
     int max_n_mat = 0;
@@ -718,29 +863,6 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
             h += nb;
         }
     }
-    if ((rc = ctx->u_reqs.ensure(descs.size())) ||
-        (rc = ctx->u_folds.ensure(folds.size())) || (rc = ctx->u_tiles.ensure(tiles.size())))
-        return rc;
-    CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), descs.size() * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), folds.size() * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    // batch b of every request in one launch, then one fold over every grid
-    ctd::LaunchParams L;
-    std::memset(&L, 0, sizeof(L));
-    fill_shared(*ps[0], L.sh);
-    L.sh.max_n_mat = max_n_mat;
-    L.n_req = n_req;
-    L.chunk = ctx->chunk;
-    L.flight_cap = ctx->flight_cap;
-    const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
-    for (int b = 0; b < n_batches; ++b)
-        if (!event_at(ctx, 2 * b) || !event_at(ctx, 2 * b + 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
-    // The batch loop (claim counters, n_batches shared launches with their timing
-    // events, the folds) is captured once into a CUDA graph and replayed while
-    // the descriptors, buffers and launch shape stay the same.
     std::vector<unsigned char> key;
     auto put = [&key](const void *p, size_t n) {
         const unsigned char *c = static_cast<const unsigned char *>(p);
@@ -748,12 +870,100 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
     };
     put(descs.data(), descs.size() * sizeof(ctd::RequestDesc));
     put(folds.data(), folds.size() * sizeof(ctd::FoldDesc));
-    put(tiles.data(), tiles.size() * sizeof(uint64_t));
-    const void *bufs[4] = {ctx->u_reqs.p, ctx->u_folds.p, ctx->u_tiles.p, ctx->u_work.p};
-    put(bufs, sizeof(bufs));
-    const int shape[5] = {n_batches, mgrid, ctx->threads, ctx->multi_blocks_per_sm, static_cast<int>(L.sh.max_n_mat)};
+    const int shape[8] = {n_batches, ctx->shared_launch, ctx->num_sms, ctx->blocks_per_sm, ctx->multi_blocks_per_sm,
+                          ctx->threads, ctx->chunk, ctx->flight_cap};
     put(shape, sizeof(shape));
-    put(&L, sizeof(L));
+    size_t n_launch = 1;
+    std::function<int(cudaStream_t)> body;
+    if (!ctx->shared_launch) {
+        // every request is its own chain (claim counters cleared, then transport
+        // and fold of each batch in turn) on its own stream; the chains overlap
+        for (int r = 0; r < n_req; ++r) {
+            ctd::SharedTables sh;
+            std::memset(&sh, 0, sizeof(sh));
+            fill_shared(*ps[r], sh);
+            put(&sh, sizeof(sh));
+        }
+        if ((rc = ensure_lanes(ctx, n_req))) return rc;
+        if (!event_at(ctx, 0) || !event_at(ctx, 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
+        body = [&](cudaStream_t cs) {
+            if (cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long),
+                                cs) != cudaSuccess ||
+                cudaEventRecordWithFlags(ctx->events[0], cs, cudaEventRecordExternal) != cudaSuccess)
+                return static_cast<int>(CTD_ECUDA);
+            int e = fork_lanes(ctx, cs, n_req);
+            for (int r = 0; r < n_req && e == CTD_OK; ++r) {
+                Phantom &P = *ps[r];
+                for (int b = 0; b < n_batches && e == CTD_OK; ++b) {
+                    const size_t k = static_cast<size_t>(b) * n_req + r;
+                    e = launch_one(ctx, P, descs[k], lane(ctx, r));
+                    if (e == CTD_OK)
+                        e = ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, folds[k].scale,
+                                             lane(ctx, r));
+                }
+                if (e == CTD_OK) e = finish_stats(P, n_batches, lane(ctx, r));
+            }
+            if (e == CTD_OK) e = join_lanes(ctx, cs, n_req);
+            if (e == CTD_OK && cudaEventRecordWithFlags(ctx->events[1], cs, cudaEventRecordExternal) != cudaSuccess)
+                e = CTD_ECUDA;
+            return e;
+        };
+    } else {
+        // batch b of every request in one launch, then one fold over every grid
+        if ((rc = ctx->u_reqs.ensure(descs.size())) || (rc = ctx->u_folds.ensure(folds.size())) ||
+            (rc = ctx->u_tiles.ensure(tiles.size())))
+            return rc;
+        CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), descs.size() * sizeof(ctd::RequestDesc),
+                           cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), folds.size() * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        put(tiles.data(), tiles.size() * sizeof(uint64_t));
+        const void *bufs[3] = {ctx->u_reqs.p, ctx->u_folds.p, ctx->u_tiles.p};
+        put(bufs, sizeof(bufs));
+        ctd::LaunchParams L;
+        std::memset(&L, 0, sizeof(L));
+        fill_shared(*ps[0], L.sh);
+        L.sh.max_n_mat = max_n_mat;
+        L.n_req = n_req;
+        L.chunk = ctx->chunk;
+        L.flight_cap = ctx->flight_cap;
+        put(&L, sizeof(L));
+        const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
+        for (int b = 0; b < n_batches; ++b)
+            if (!event_at(ctx, 2 * b) || !event_at(ctx, 2 * b + 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
+        n_launch = n_batches;
+        body = [&, L, mgrid](cudaStream_t cs) mutable {
+            int e = CTD_OK;
+            if (cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long),
+                                cs) != cudaSuccess)
+                e = CTD_ECUDA;
+            for (int b = 0; b < n_batches && e == CTD_OK; ++b) {
+                L.reqs = ctx->u_reqs.p + static_cast<size_t>(b) * n_req;
+                if (cudaEventRecordWithFlags(ctx->events[2 * b], cs, cudaEventRecordExternal) != cudaSuccess)
+                    e = CTD_ECUDA;
+                if (e == CTD_OK)
+                    e = ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, cs);
+                if (e == CTD_OK &&
+                    cudaEventRecordWithFlags(ctx->events[2 * b + 1], cs, cudaEventRecordExternal) != cudaSuccess)
+                    e = CTD_ECUDA;
+                if (e == CTD_OK)
+                    e = ctd::launch_fold_multi(ctx->u_folds.p + static_cast<size_t>(b) * n_req, ctx->u_tiles.p, n_req,
+                                               tiles[n_req], cs);
+            }
+            for (int r = 0; r < n_req && e == CTD_OK; ++r) e = finish_stats(*ps[r], n_batches, cs);
+            return e;
+        };
+    }
+    const void *work = ctx->u_work.p;
+    put(&work, sizeof(work));
+    for (int r = 0; r < n_req; ++r) {
+        const void *out[4] = {ps[r]->dose.p, ps[r]->sd.p, ps[r]->partials.p, ps[r]->result.p};
+        put(out, sizeof(out));
+    }
+    // The batch loop is captured once into a CUDA graph and replayed while the
+    // descriptors, buffers and launch shape stay the same.
     if (!ctx->batch_graph || key != ctx->batch_graph_key) {
         if (ctx->batch_graph) {
             cudaGraphExecDestroy(ctx->batch_graph);
@@ -762,21 +972,7 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
         if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         cudaStream_t cs = ctx->capture_stream;
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        int crc = CTD_OK;
-        if (cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long), cs) !=
-            cudaSuccess)
-            crc = CTD_ECUDA;
-        for (int b = 0; b < n_batches && crc == CTD_OK; ++b) {
-            L.reqs = ctx->u_reqs.p + static_cast<size_t>(b) * n_req;
-            if (cudaEventRecordWithFlags(ctx->events[2 * b], cs, cudaEventRecordExternal) != cudaSuccess) crc = CTD_ECUDA;
-            if (crc == CTD_OK)
-                crc = ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, cs);
-            if (crc == CTD_OK && cudaEventRecordWithFlags(ctx->events[2 * b + 1], cs, cudaEventRecordExternal) != cudaSuccess)
-                crc = CTD_ECUDA;
-            if (crc == CTD_OK)
-                crc = ctd::launch_fold_multi(ctx->u_folds.p + static_cast<size_t>(b) * n_req, ctx->u_tiles.p, n_req,
-                                             tiles[n_req], cs);
-        }
+        const int crc = body(cs);
         cudaGraph_t graph = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
         if (crc != CTD_OK || ce != cudaSuccess) {
@@ -793,14 +989,8 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
         ctx->batch_graph_key.swap(key);
     }
     CK(cudaGraphLaunch(ctx->batch_graph, ctx->stream));
+    if ((rc = collect_many(ctx, ps.data(), n_req, n_launch, t0))) return rc;
     for (int r = 0; r < n_req; ++r) {
-        Phantom &P = *ps[r];
-        CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, n_batches, P.dose.p, P.sd.p, P.nvox, ctx->stream));
-        CKS(ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, ctx->stream));
-        CKS(ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, ctx->stream));
-    }
-    for (int r = 0; r < n_req; ++r) {
-        if ((rc = collect(ctx, *ps[r], n_batches, t0))) return rc;
         ps[r]->stats.histories = n_histories[r];
         ps[r]->stats.n_batches = n_batches;
         ps[r]->have_result = true;
@@ -1056,7 +1246,7 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
     }
     std::vector<Phantom *> ps(n);
     for (int i = 0; i < n; ++i) ps[i] = find(ctx, ctx->sreqs[ctx->active[i]].ph);
-    for (int i = 1; i < n; ++i) {
+    for (int i = 1; i < n && ctx->shared_launch; ++i) {
         const ctd_physics &a = ps[0]->phys, &b = ps[i]->phys;
         if (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta) {
             retire(ctx, ctx->sreqs[ctx->active[i]], CTD_REQ_FAILED);
@@ -1092,35 +1282,61 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
         f.nvox = P.nvox;
         f.scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
     }
-    if ((rc = ctx->u_reqs.ensure(n)) || (rc = ctx->u_folds.ensure(n)) ||
-        (rc = ctx->u_tiles.ensure(n + 1)))
-        return rc;
-    CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), n * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), n * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemsetAsync(ctx->u_work.p, 0, n * sizeof(unsigned long long), ctx->stream));
-    ctd::LaunchParams L;
-    std::memset(&L, 0, sizeof(L));
-    fill_shared(*ps[0], L.sh);
-    L.sh.max_n_mat = max_n_mat;
-    L.reqs = ctx->u_reqs.p;
-    L.n_req = n;
-    L.chunk = ctx->chunk;
-    L.flight_cap = ctx->flight_cap;
-    const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
-    CKS(ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, ctx->stream));
-    CKS(ctd::launch_fold_multi(ctx->u_folds.p, ctx->u_tiles.p, n, tiles[n], ctx->stream));
+    // one batch of every running request; those past min_batches also get their
+    // statistics for the stopping test
     std::vector<int> checked;
     for (int i = 0; i < n; ++i) {
         ServeReq &R = ctx->sreqs[ctx->active[i]];
-        Phantom &P = *ps[i];
         R.batches += 1;
         R.histories += R.req.batch_histories;
-        if (R.batches >= R.req.min_batches) {
-            CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, R.batches, P.dose.p, P.sd.p, P.nvox, ctx->stream));
-            CKS(ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, ctx->stream));
-            checked.push_back(i);
+        if (R.batches >= R.req.min_batches) checked.push_back(i);
+    }
+    auto stats = [&](int i, cudaStream_t s) {
+        Phantom &P = *ps[i];
+        const int nb = ctx->sreqs[ctx->active[i]].batches;
+        int e = ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, nb, P.dose.p, P.sd.p, P.nvox, s);
+        if (e == CTD_OK) e = ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, s);
+        return e;
+    };
+    if (!ctx->shared_launch) {
+        // each request on its own stream: transport, fold, statistics
+        if ((rc = ensure_lanes(ctx, n))) return rc;
+        CK(cudaMemsetAsync(ctx->u_work.p, 0, n * sizeof(unsigned long long), ctx->stream));
+        if ((rc = fork_lanes(ctx, ctx->stream, n))) return rc;
+        size_t c = 0;
+        for (int i = 0; i < n; ++i) {
+            Phantom &P = *ps[i];
+            const cudaStream_t s = lane(ctx, i);
+            CKS(launch_one(ctx, P, descs[i], s));
+            CKS(ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, folds[i].scale, s));
+            if (c < checked.size() && checked[c] == i) {
+                CKS(stats(i, s));
+                ++c;
+            }
         }
+        if ((rc = join_lanes(ctx, ctx->stream, n))) return rc;
+    } else {
+        if ((rc = ctx->u_reqs.ensure(n)) || (rc = ctx->u_folds.ensure(n)) || (rc = ctx->u_tiles.ensure(n + 1)))
+            return rc;
+        CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), n * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), n * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaMemsetAsync(ctx->u_work.p, 0, n * sizeof(unsigned long long), ctx->stream));
+        ctd::LaunchParams L;
+        std::memset(&L, 0, sizeof(L));
+        fill_shared(*ps[0], L.sh);
+        L.sh.max_n_mat = max_n_mat;
+        L.reqs = ctx->u_reqs.p;
+        L.n_req = n;
+        L.chunk = ctx->chunk;
+        L.flight_cap = ctx->flight_cap;
+        const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
+        CKS(ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, ctx->stream));
+        CKS(ctd::launch_fold_multi(ctx->u_folds.p, ctx->u_tiles.p, n, tiles[n], ctx->stream));
+        for (int i : checked) CKS(stats(i, ctx->stream));
     }
     std::vector<std::array<double, 3>> res(checked.size());
     for (size_t c = 0; c < checked.size(); ++c)
@@ -1136,14 +1352,21 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
         const bool cap = R.req.n_histories_max && R.histories >= R.req.n_histories_max;
         if (hit || cap) finished.push_back(R.id);
     }
+    std::vector<Phantom *> fp;
+    std::vector<double> ft;
     for (int64_t id : finished) {
         ServeReq &R = ctx->sreqs[id];
         Phantom &P = *find(ctx, R.ph);
         CKS(ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, ctx->stream));
-        if ((rc = collect(ctx, P, 0, R.t_start))) return rc;
-        P.stats.histories = R.histories;
-        P.stats.n_batches = R.batches;
-        P.have_result = true;
+        fp.push_back(&P);
+        ft.push_back(R.t_start);
+    }
+    if (!fp.empty() && (rc = collect_many(ctx, fp.data(), static_cast<int>(fp.size()), 0, 0.0, ft.data()))) return rc;
+    for (size_t i = 0; i < finished.size(); ++i) {
+        ServeReq &R = ctx->sreqs[finished[i]];
+        fp[i]->stats.histories = R.histories;
+        fp[i]->stats.n_batches = R.batches;
+        fp[i]->have_result = true;
         retire(ctx, R, CTD_REQ_DONE);
     }
     if (n_active) *n_active = static_cast<int>(ctx->active.size() + ctx->pending.size());

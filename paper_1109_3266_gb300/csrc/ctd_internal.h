@@ -85,6 +85,7 @@ struct alignas(16) RequestDesc {
     int src_kind, n_proj, continuous;
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
     int mode, max_real;
+    uint32_t rk[20];             // Philox round keys of seed: (lo, hi) + r (Weyl constants), r = 0..9
 };
 
 // blocks copy a descriptor into shared memory in 16-byte words

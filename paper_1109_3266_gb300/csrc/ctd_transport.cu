@@ -25,7 +25,28 @@ struct Photon {
     uint64_t h;
     uint32_t step;
     int nreal;
+    int j;            // energy node of e, its fraction and the majorant there;
+    float te, mmax;   // they change only with e
 };
+
+// Philox block of (history, step, stream) of request q: the round keys are
+// taken from q when it sits in the kernel's parameter space (kKeys), else
+// derived from the seed.
+template <bool kKeys>
+__device__ __forceinline__ U4 draw(const RequestDesc &q, uint64_t h, uint32_t step, uint32_t stream)
+{
+    if (kKeys)
+        return philox_rk(static_cast<uint32_t>(h), static_cast<uint32_t>(h >> 32), step, stream, q.rk);
+    return block(q.seed, h, step, stream);
+}
+
+// energy node, fraction and majorant of the photon's energy
+__device__ __forceinline__ void set_energy(Photon &ph, const SharedTables &sh, const float *__restrict__ s_mm)
+{
+    ph.j = enode(ph.e, sh.e_min, sh.n_e, ph.te);
+    const float m0 = s_mm[ph.j], m1 = s_mm[ph.j + 1];
+    ph.mmax = m0 + ph.te * (m1 - m0);
+}
 
 // Event counts of a lane, in registers.
 struct LaneCounts {
@@ -84,11 +105,12 @@ __device__ __forceinline__ int bin_search(const RequestDesc &q, uint64_t local)
 // Source photon of local history `local` (global index h) of request q;
 // `bin` is a lower bound of its 1 keV interval.  Returns true if the photon
 // enters the phantom.
+template <bool kKeys>
 __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_t local, int bin, Photon &ph,
                                        LaneCounts &cnt)
 {
     while (bin < q.nbins - 1 && __ldg(&q.pref[bin + 1]) <= local) ++bin;
-    const U4 b0 = block(q.seed, h, 0, kStreamSource);
+    const U4 b0 = draw<kKeys>(q, h, 0, kStreamSource);
     const float elo = __ldg(&q.bin_lo[bin]), ehi = __ldg(&q.bin_hi[bin]);
     const float e = elo + (ehi - elo) * uni(b0.x);
     cnt.emitted(e);
@@ -108,7 +130,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     bool accepted = false;
     float uu = 0.0f, vv = 0.0f, qq = 0.0f;
     for (uint32_t t = 1; t <= kMaxTrials; ++t) {
-        const U4 b = block(q.seed, h, t, kStreamSource);
+        const U4 b = draw<kKeys>(q, h, t, kStreamSource);
         uu = q.ulo + q.uw * uni(b.x);
         vv = q.vlo + q.vw * uni(b.y);
         qq = (D2 + uu * uu) + vv * vv;
@@ -169,8 +191,6 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
 struct Hit {
     size_t idx;       // voxel
     int m;            // material
-    int j;            // energy node
-    float te;         // energy fraction
     int type;         // 0 photoelectric, 1 Compton, 2 Rayleigh
     uint32_t rz, rw;  // the step's random words for zeta and phi
 };
@@ -180,22 +200,21 @@ enum { kEnded = 0, kFictitious = 1, kReal = 2 };
 // One Woodcock flight (Sec. 2.1): free path against mu_max(E), the move, the
 // escape test, the voxel and the interaction type.  s_tab and s_mm are the
 // request's attenuation table and majorant in shared memory.
+template <bool kKeys>
 __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc &q, const float4 *__restrict__ s_tab,
-                                      const float *__restrict__ s_mm, Photon &ph, LaneCounts &cnt, Hit &hit)
+                                      Photon &ph, LaneCounts &cnt, Hit &hit)
 {
     if (ph.step >= kMaxSteps) {
         cnt.event(kCntAborted);
         cnt.escaped(ph.e);
         return kEnded;
     }
-    const U4 b = block(q.seed, ph.h, ph.step, kStreamTransport);
+    const U4 b = draw<kKeys>(q, ph.h, ph.step, kStreamTransport);
     ph.step++;
     cnt.n[kCntSteps]++;
-    float te;
     const int n_e = sh.n_e;
-    const int j = enode(ph.e, sh.e_min, n_e, te);
-    const float m0 = s_mm[j], m1 = s_mm[j + 1];
-    const float mmax = m0 + te * (m1 - m0);
+    const int j = ph.j;
+    const float te = ph.te, mmax = ph.mmax;
     const float path = (-log32(uni(b.x))) / mmax;
     ph.x = ph.x + path * ph.ux;
     ph.y = ph.y + path * ph.uy;
@@ -229,8 +248,6 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     }
     hit.idx = idx;
     hit.m = m;
-    hit.j = j;
-    hit.te = te;
     hit.type = type;
     hit.rz = b.z;
     hit.rw = b.w;
@@ -239,8 +256,8 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
 
 // A real interaction: local deposition, C/R-surface polar angle, rotation.
 // Returns false when the history has ended.
-__device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDesc &q, Photon &ph, const Hit &hit,
-                                         LaneCounts &cnt)
+__device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDesc &q, const float *__restrict__ s_mm,
+                                         Photon &ph, const Hit &hit, LaneCounts &cnt)
 {
     ph.nreal++;
     if (hit.type == 0) {
@@ -250,7 +267,7 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
         return false;
     }
     const float *S = hit.type == 1 ? sh.csurf : q.rsurf + static_cast<size_t>(hit.m) * sh.n_e * sh.n_zeta;
-    const float mu = surface(S, sh.n_zeta, hit.j, hit.te, uni(hit.rz));
+    const float mu = surface(S, sh.n_zeta, ph.j, ph.te, uni(hit.rz));
     if (hit.type == 1) {
         // Compton: E' = E / (1 + (E/mc^2)(1 - mu)), the electron gets E - E'
         cnt.n[kCntCompton]++;
@@ -263,6 +280,7 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
         }
         deposit(q.tally, hit.idx, ph.e - ep);
         ph.e = ep;
+        set_energy(ph, sh, s_mm);
     } else {
         cnt.event(kCntRayleigh);
     }
@@ -299,6 +317,7 @@ constexpr size_t kWarpBytes = kQueueBytes + sizeof(WarpPool);
 
 // All histories [q.local_begin, q.local_end) of one request, claimed by warps
 // from q.work in runs of `chunk`.  Returns when the warp has no photon left.
+template <bool kKeys>
 __device__ __forceinline__ void run_request(const LaunchParams &P, const RequestDesc &q, const float4 *s_tab,
                                             const float *s_mm, const Queue &Q, int lane, LaneCounts &cnt)
 {
@@ -338,7 +357,7 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
                 bool ok = false;
                 if (lane < take) {
                     const uint64_t local = pool_next + lane;
-                    ok = source(q, q.h_base + local, local, pool_bin, np, cnt);
+                    ok = source<kKeys>(q, q.h_base + local, local, pool_bin, np, cnt);
                 }
                 const unsigned okm = __ballot_sync(kFull, ok);
                 if (ok) {
@@ -380,6 +399,7 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
                 ph.e = Q.f[6 * kQueue + slot];
                 ph.step = 0;
                 ph.nreal = 0;
+                set_energy(ph, P.sh, s_mm);
                 alive = true;
             }
         }
@@ -394,10 +414,10 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
             Hit hit;
             int f, k = 0;
             do {
-                f = flight(P.sh, q, s_tab, s_mm, ph, cnt, hit);
+                f = flight<kKeys>(P.sh, q, s_tab, ph, cnt, hit);
             } while (f == kFictitious && ++k < P.flight_cap);
             if (f == kEnded) alive = false;
-            else if (f == kReal) alive = interact(P.sh, q, ph, hit, cnt);
+            else if (f == kReal) alive = interact(P.sh, q, s_mm, ph, hit, cnt);
         }
     }
 }
@@ -435,7 +455,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
     if (!kMulti) {
         load_tables(P.one, n_e, s_tab, s_mm);
         __syncthreads();
-        run_request(P, P.one, s_tab, s_mm, Q, lane, cnt);
+        run_request<true>(P, P.one, s_tab, s_mm, Q, lane, cnt);
         flush_warp(P.one.counts, cnt, lane);
         return;
     }
@@ -468,7 +488,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
         __syncthreads();
         load_tables(q, n_e, s_tab, s_mm);
         __syncthreads();
-        run_request(P, q, s_tab, s_mm, Q, lane, cnt);
+        run_request<false>(P, q, s_tab, s_mm, Q, lane, cnt);
         flush_warp(q.counts, cnt, lane);
         __syncthreads();
         // the same request is exhausted now; continue the walk from it
@@ -534,11 +554,18 @@ size_t transport_smem_bytes(const LaunchParams &p, int threads)
            static_cast<size_t>(threads / 32) * kWarpBytes;
 }
 
+// persistent grids: a few blocks per SM
+constexpr int kMaxGrid = 1 << 16;
+
 // Kernel variants by residency: 4 blocks of 256 threads per SM cap it at 64
 // registers, 7 blocks of 128 at 73, fewer at 85.
 int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid <= 0 || grid > kMaxGrid || block <= 0 || block > 256 || block % 32 != 0) {
+        set_error("transport launch shape out of range");
+        return CTD_EINVAL;
+    }
     const size_t smem = transport_smem_bytes(p, block);
     return p.n_req > 0 ? launch_m<true>(p, grid, block, threads_per_sm, smem, s)
                        : launch_m<false>(p, grid, block, threads_per_sm, smem, s);

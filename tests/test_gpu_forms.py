@@ -30,6 +30,19 @@ def ctx(ctd):
     ctd.ctd_destroy(c)
 
 
+@pytest.fixture(scope="module")
+def shared_ctx(ctd):
+    c = ctd.ctd_create(device=0, shared_launch=1)
+    yield c
+    ctd.ctd_destroy(c)
+
+
+@pytest.fixture(params=["chains", "shared"])
+def form_ctx(request, ctx, shared_ctx):
+    """The batched and served forms in both launch designs."""
+    return ctx if request.param == "chains" else shared_ctx
+
+
 def problems():
     return [I.head(120_000, seed=31, phantom_seed=7, shape=(64, 64, 40), d=0.4),
             I.cbct_water(90_000, seed=32, shape=(48, 48, 24), d=0.8),
@@ -55,33 +68,44 @@ def same(a, b):
     assert st2["avg_rsd"] == pytest.approx(st["avg_rsd"], rel=1e-6)
 
 
-def test_batched_equals_separate_runs(ctd, ctx):
+def test_batched_equals_separate_runs(ctd, ctx, form_ctx):
     ps = problems()
     ref = [alone(ctd, ctx, p) for p in ps]
-    hs = [ctd.load_problem(ctx, p) for p in ps]
-    ctd.ctd_run_batch(ctx, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
+    hs = [ctd.load_problem(form_ctx, p) for p in ps]
+    ctd.ctd_run_batch(form_ctx, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
     for p, h, r in zip(ps, hs, ref):
-        same(r, ctd.ctd_get_dose_and_stddev(ctx, h, p.phantom.nvox))
-    # a second batched call on the same phantoms gives the same again
-    ctd.ctd_run_batch(ctx, hs[::-1], [p.n_hist for p in ps[::-1]], [p.seed for p in ps[::-1]], 10)
+        same(r, ctd.ctd_get_dose_and_stddev(form_ctx, h, p.phantom.nvox))
+    # a second batched call on the same phantoms, in another order, gives the same again
+    ctd.ctd_run_batch(form_ctx, hs[::-1], [p.n_hist for p in ps[::-1]], [p.seed for p in ps[::-1]], 10)
     for p, h, r in zip(ps, hs, ref):
-        same(r, ctd.ctd_get_dose_and_stddev(ctx, h, p.phantom.nvox))
+        same(r, ctd.ctd_get_dose_and_stddev(form_ctx, h, p.phantom.nvox))
     for h in hs:
-        ctd.ctd_destroy_phantom(ctx, h)
+        ctd.ctd_destroy_phantom(form_ctx, h)
 
 
-def test_batched_rejects_mixed_node_grids_and_duplicates(ctd, ctx):
-    a = ctd.load_problem(ctx, I.tiny_water(1000))            # nodes 10-150 keV
-    b = ctd.load_problem(ctx, problems()[1])                  # nodes 1-150 keV
-    with pytest.raises(ctd.CtdError):
-        ctd.ctd_run_batch(ctx, [a, b], [1000, 1000], [1, 2], 10)
-    with pytest.raises(ctd.CtdError):
-        ctd.ctd_run_batch(ctx, [b, b], [1000, 1000], [1, 2], 10)
-    ctd.ctd_destroy_phantom(ctx, a)
-    ctd.ctd_destroy_phantom(ctx, b)
+def test_batched_node_grids_and_duplicates(ctd, ctx, shared_ctx):
+    tw, cw = I.tiny_water(1000), problems()[3]
+    for c in (ctx, shared_ctx):
+        a = ctd.load_problem(c, tw)                            # nodes 10-150 keV
+        b = ctd.load_problem(c, cw)                            # nodes 1-150 keV
+        with pytest.raises(ctd.CtdError):
+            ctd.ctd_run_batch(c, [b, b], [1000, 1000], [1, 2], 10)
+        if c is shared_ctx:
+            # one shared launch holds one node grid
+            with pytest.raises(ctd.CtdError):
+                ctd.ctd_run_batch(c, [a, b], [1000, 1000], [1, 2], 10)
+        else:
+            # separate chains do not
+            ctd.ctd_run_batch(c, [a, b], [tw.n_hist, cw.n_hist], [tw.seed, cw.seed], 10)
+            got = [ctd.ctd_get_dose_and_stddev(c, h, p.phantom.nvox) for h, p in ((a, tw), (b, cw))]
+            same(alone(ctd, c, tw, nb=10), got[0])
+            same(alone(ctd, c, cw, nb=10), got[1])
+        ctd.ctd_destroy_phantom(c, a)
+        ctd.ctd_destroy_phantom(c, b)
 
 
-def test_served_requests_equal_plain_runs(ctd, ctx):
+def test_served_requests_equal_plain_runs(ctd, form_ctx):
+    ctx = form_ctx
     ps = problems()[:3]
     B = [20_000, 15_000, 9_000]
     targets = [0.12, 0.2, 0.3]

@@ -42,8 +42,8 @@ LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes issue per SM clock
 # (smsp__inst_executed x thread-per-instruction ratio / histories) and DRAM
 # bytes per launch (dram__bytes_read + dram__bytes_write).
 KERNEL_PROFILE = {
-    "cbct_water": {"lane_inst_per_history": 3254.0, "dram_bytes_per_launch": 13.60e9, "histories_per_launch": 1e8},
-    "head": {"lane_inst_per_history": 5219.0, "dram_bytes_per_launch": 23.21e9, "histories_per_launch": 2e8},
+    "cbct_water": {"lane_inst_per_history": 3072.0, "dram_bytes_per_launch": 13.60e9, "histories_per_launch": 1e8},
+    "head": {"lane_inst_per_history": 4490.0, "dram_bytes_per_launch": 23.33e9, "histories_per_launch": 2e8},
 }
 
 
@@ -332,6 +332,22 @@ def run_ours(args):
                            "peak_gbs": peaks.get("hbm_gbs"),
                            "atomics_per_s": p.n_hist * args.steps * deposits_per_hist / t_transport,
                            "steps_per_history": steps_per_hist, "deposits_per_history": deposits_per_hist}
+    if not args.no_probe:
+        # memory ceilings measured on this GPU by the library's probes, over the same
+        # number of slots as the phantom: binary64 reductions into random tally slots
+        # and random voxel (material + density) gathers
+        n_ops = 1 << 31
+        red = ctd.ctd_probe_memory(ctx, ctd.PROBE_L2_RED, nvox, n_ops)
+        vox = ctd.ctd_probe_memory(ctx, ctd.PROBE_VOXEL, nvox, n_ops)
+        g4 = ctd.ctd_probe_memory(ctx, ctd.PROBE_GATHER4, nvox, n_ops)
+        ms = roof["memory_side"]
+        steps_per_s = p.n_hist * args.steps * steps_per_hist / t_transport
+        ms.update({"l2_red_peak_per_s": red, "atomic_frac": ms["atomics_per_s"] / red,
+                   "voxel_gather_peak_per_s": vox, "steps_per_s": steps_per_s, "gather_frac": steps_per_s / vox,
+                   "gather4_peak_per_s": g4,
+                   "probe": f"{n_ops} operations on uniform random slots of {nvox} voxels "
+                            f"({nvox * 8 / 1e6:.0f} MB binary64 tally, {nvox * 5 / 1e6:.0f} MB voxels), "
+                            f"mean of 3 launches after 1"})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -492,6 +508,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the memory-ceiling probes")
     ap.add_argument("--rsd-stop", type=int, default=1, help="measure sec-to-1%% with the RSD-stopped form")
     ap.add_argument("--inst-per-history", type=float, default=0.0)
     ap.add_argument("--n-requests", type=int, default=64)

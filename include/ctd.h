@@ -284,6 +284,26 @@ int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e
  * floats; out holds n (fn 0) or 2n (fn 1) host floats. */
 int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n);
 
+/* Memory-system probes for the roofline of the transport kernel.  The paper has
+ * no counterpart; they measure the two memory ceilings the transport meets:
+ *   kind CTD_PROBE_L2_RED (0): binary64 reductions (red.global.add.f64, the
+ *        deposit instruction) of 1.0 into uniformly random slots of a buffer of
+ *        n_slots doubles;
+ *   kind CTD_PROBE_GATHER4 (1): gathers of 4-byte records from uniformly random
+ *        slots of a buffer of n_slots floats;
+ *   kind CTD_PROBE_VOXEL (2): gathers of one voxel's material byte and 4-byte
+ *        density from uniformly random slots of n_slots voxels (the Woodcock
+ *        step's fetch).
+ * About n_ops operations (rounded up to whole rounds of 8 per thread over
+ * SMs x 8 blocks of 256 threads) run in one launch, timed with CUDA events on
+ * the context's stream after one untimed launch; *ops_per_s receives the mean
+ * rate of 3 timed launches.  Slots are drawn with the lowbias32 hash, so
+ * buffers that fit in L2 measure L2 and larger ones HBM.  The call allocates
+ * and frees its buffers (CTD_ENOMEM if they do not fit) and blocks until done.
+ * 1 <= n_slots < 2^32 and 1 <= n_ops <= 2^40, else CTD_EINVAL. */
+enum { CTD_PROBE_L2_RED = 0, CTD_PROBE_GATHER4 = 1, CTD_PROBE_VOXEL = 2 };
+int ctd_probe_memory(ctd_ctx *ctx, int kind, uint64_t n_slots, uint64_t n_ops, double *ops_per_s);
+
 /* Allocation-free avg RSD.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need the
  * precision measure, such as code running inside CUDA stream capture (where

@@ -1446,6 +1446,48 @@ int ctd_cancel(ctd_ctx *ctx, ctd_req_id id)
 // ---------------------------------------------------------------- autotuner
 extern "C" {
 
+int ctd_probe_memory(ctd_ctx *ctx, int kind, uint64_t n_slots, uint64_t n_ops, double *ops_per_s)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    if (kind < 0 || kind > 2 || n_slots < 1 || n_slots >= (1ull << 32) || n_ops < 1 || n_ops > (1ull << 40) ||
+        !ops_per_s)
+        return fail(CTD_EINVAL, "probe: kind 0-2, 1 <= n_slots < 2^32, 1 <= n_ops <= 2^40");
+    const int block = 256, grid = ctx->num_sms * 8;
+    const uint64_t per_round = static_cast<uint64_t>(grid) * block * 8;
+    const uint64_t rounds64 = (n_ops + per_round - 1) / per_round;
+    // operation indices are 32-bit
+    if (rounds64 * per_round >= (1ull << 32)) return fail(CTD_EINVAL, "probe: n_ops too large for one launch");
+    const uint32_t rounds = static_cast<uint32_t>(rounds64);
+    DevBuf<double> dbuf;
+    DevBuf<float> fbuf, out;
+    DevBuf<uint8_t> mbuf;
+    if (kind == 0) rc = dbuf.ensure(n_slots);
+    else rc = fbuf.ensure(n_slots);
+    if (!rc && kind == 2) rc = mbuf.ensure(n_slots);
+    if (!rc && kind != 0) rc = out.ensure(static_cast<size_t>(grid) * block);
+    if (rc) return rc;
+    if (kind == 0) CK(cudaMemsetAsync(dbuf.p, 0, n_slots * sizeof(double), ctx->stream));
+    if (kind != 0) CK(cudaMemsetAsync(fbuf.p, 0, n_slots * sizeof(float), ctx->stream));
+    if (kind == 2) CK(cudaMemsetAsync(mbuf.p, 0, n_slots, ctx->stream));
+    if (!event_at(ctx, 0) || !event_at(ctx, 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
+    const uint32_t n32 = static_cast<uint32_t>(n_slots);
+    CKS(ctd::launch_probe(kind, dbuf.p, fbuf.p, mbuf.p, out.p, n32, rounds, 0x9E3779B9u, grid, block, ctx->stream));
+    double t = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        CK(cudaEventRecord(ctx->events[0], ctx->stream));
+        CKS(ctd::launch_probe(kind, dbuf.p, fbuf.p, mbuf.p, out.p, n32, rounds, 0x85EBCA6Bu * (k + 1), grid, block,
+                              ctx->stream));
+        CK(cudaEventRecord(ctx->events[1], ctx->stream));
+        CK(cudaEventSynchronize(ctx->events[1]));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]));
+        t += ms * 1e-3;
+    }
+    *ops_per_s = 3.0 * static_cast<double>(rounds) * static_cast<double>(per_round) / t;
+    return CTD_OK;
+}
+
 int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, ctd_tune_result *out)
 {
     int rc;

@@ -134,5 +134,7 @@ struct FoldDesc {
 };
 constexpr int kFoldTile = 4096;
 int launch_fold_multi(const FoldDesc *descs, const uint64_t *tile_off, int n, uint64_t total_tiles, void *stream);
+int launch_probe(int kind, double *dbuf, float *fbuf, uint8_t *mbuf, float *out, uint32_t n_slots, uint32_t rounds,
+                 uint32_t salt, int grid, int block, void *stream);
 
 }  // namespace ctd

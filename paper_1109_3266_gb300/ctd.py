@@ -123,6 +123,7 @@ def lib():
         L.ctd_wait.argtypes = [P, C.c_int64, C.c_double, C.POINTER(ctd_req_status)]
         L.ctd_cancel.argtypes = [P, C.c_int64]
         L.ctd_autotune.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.POINTER(ctd_tune_result)]
+        L.ctd_probe_memory.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, dp]
         _lib = L
     return _lib
 
@@ -322,3 +323,14 @@ def run_problem(ctx, problem, handle=None):
     ctd_run(ctx, h, problem.n_hist, problem.seed, problem.n_batches)
     dose, sd, st = ctd_get_dose_and_stddev(ctx, h, problem.phantom.nvox)
     return dose, sd, st, h
+
+
+PROBE_L2_RED, PROBE_GATHER4, PROBE_VOXEL = 0, 1, 2
+
+
+def ctd_probe_memory(ctx, kind, n_slots, n_ops):
+    """Rate (operations/s) of random binary64 L2 reductions (kind 0), 4-byte
+    gathers (1) or voxel gathers (2) over n_slots slots."""
+    r = C.c_double()
+    _check(lib().ctd_probe_memory(ctx, int(kind), C.c_uint64(n_slots), C.c_uint64(n_ops), C.byref(r)))
+    return r.value

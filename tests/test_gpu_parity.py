@@ -234,3 +234,21 @@ def test_edge_cases(ctd, ctx, oracle):
     ctd.ctd_destroy_phantom(ctx, h)
     with pytest.raises(ctd.CtdError):
         ctd.ctd_destroy_phantom(ctx, h)
+
+
+@pytest.mark.gpu
+def test_memory_probes_report_rates(ctd):
+    """The memory-ceiling probes run on L2- and HBM-sized buffers and give
+    positive, finite rates; arguments out of range are refused."""
+    c = ctd.ctd_create(device=0)
+    try:
+        for kind in (ctd.PROBE_L2_RED, ctd.PROBE_GATHER4, ctd.PROBE_VOXEL):
+            for n_slots in (1, 1 << 20, 1 << 28):
+                r = ctd.ctd_probe_memory(c, kind, n_slots, 1 << 24)
+                assert np.isfinite(r) and r > 0
+        for bad in ((3, 1 << 20, 1 << 20), (0, 0, 1 << 20), (0, 1 << 32, 1 << 20), (1, 1 << 20, 0),
+                    (2, 1 << 20, 1 << 33)):
+            with pytest.raises(ctd.CtdError):
+                ctd.ctd_probe_memory(c, *bad)
+    finally:
+        ctd.ctd_destroy(c)

@@ -13,6 +13,9 @@
  *     Rayleigh per formula unit 1.565e-5 Z^2 / E_MeV^2 in barn, Compton
  *     = free-electron Klein-Nishina total per electron times electrons per gram;
  *   - Rayleigh form factor F^2(q^2) ~ exp(-q^2 / q0^2) (or 1, Thomson);
+ *   - Waller-Hartree Compton (Eq. 2 with S(q)): S(q)/Z = 1 - exp(-q^2 / sq0^2)
+ *     with q^2 = 2 k^2 (1 - cos theta), k = E / hc, the same momentum transfer as
+ *     the form factor; its total is the integral of Eq. 2 by composite Simpson;
  *   - random numbers: Philox4x32-10 keyed by the 64-bit seed, counter
  *     (history lo, history hi, step, stream).
  */
@@ -35,6 +38,7 @@
 #define OR_RAY_COEF 1.565e-5       /* Rayleigh coefficient (barn MeV^2)     */
 #define OR_CDF_POINTS 20000        /* mu intervals of the numeric cdf       */
 #define OR_MAX_TRIALS 1000         /* rejection loops give up after this    */
+#define OR_MAX_TRIALS_WH (1u << 20) /* Waller-Hartree keeps about a(1-mu) of KN draws at low E */
 #define OR_MAX_STEPS 100000000u    /* Woodcock steps per history            */
 
 enum { OR_STREAM_TRANSPORT = 0, OR_STREAM_SOURCE = 1, OR_STREAM_EXACT = 2, OR_STREAM_SAMPLER = 3 };
@@ -192,6 +196,45 @@ double or_mu_rayleigh(const or_material *m, double e_kev)
     return ((sigma * OR_BARN) * OR_NA) / m->a_mol;
 }
 
+/* Eq. 2 up to the factor r0^2/2: the Klein-Nishina density in mu = cos theta
+ * times S(q)/Z = 1 - exp(-a (1 - mu)), a = 2 k^2 / sq0^2 (a <= 0: S/Z = 1). */
+static double or_pdf_wh(double k, double a, double mu)
+{
+    double e = 1.0 / (1.0 + k * (1.0 - mu));
+    double kn = (e * e) * ((e + 1.0 / e) - (1.0 - mu * mu));
+    if (a <= 0.0) return kn;
+    return kn * (-expm1(-a * (1.0 - mu)));
+}
+
+static double or_wh_a(double e_kev, double sq0)
+{
+    double kr = e_kev / OR_HC;
+    return sq0 > 0.0 ? (2.0 * kr * kr) / (sq0 * sq0) : 0.0;
+}
+
+double or_sigma_wh(double e_kev, double sq0)
+{
+    const int M = OR_CDF_POINTS;
+    double k = e_kev / OR_MEC2;
+    double a = or_wh_a(e_kev, sq0);
+    /* Simpson weights 1, 4, 2, ..., 4, 1 on mu_n = (2n - M)/M, h = 2/M */
+    double odd = 0.0, even = 0.0;
+    for (int n = 1; n < M; ++n) {
+        double mu = (double)(2 * n - M) / (double)M;
+        if (n & 1) odd += or_pdf_wh(k, a, mu);
+        else even += or_pdf_wh(k, a, mu);
+    }
+    double ends = or_pdf_wh(k, a, -1.0) + or_pdf_wh(k, a, 1.0);
+    double integral = ((2.0 / (double)M) / 3.0) * (ends + (4.0 * odd + 2.0 * even));
+    /* dsigma/dOmega = (r0^2/2) pdf, dOmega = 2 pi dmu */
+    return (OR_PI * OR_R0 * OR_R0) * integral;
+}
+
+double or_mu_compton_wh(const or_material *m, double e_kev)
+{
+    return (OR_NA * m->z_over_a) * or_sigma_wh(e_kev, m->sq0);
+}
+
 /* ===================================================================== */
 /* Largest-remainder allocation of n histories to spectrum bins           */
 /* (Sec. 2.2.5: histories distributed to 1 keV intervals by the spectrum). */
@@ -278,6 +321,8 @@ static void or_invert_row(const double *cdf, int n_zeta, double *row)
     row[n_zeta - 1] = 1.0;
 }
 
+/* kind 0: Klein-Nishina C surface; 1: Rayleigh R surface of width q0;
+ * 2: Waller-Hartree C surface of scattering-function width q0 */
 static void or_build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out)
 {
     const int M = OR_CDF_POINTS;
@@ -290,7 +335,7 @@ static void or_build_surface(int kind, double q0, int e_min, int n_e, int n_zeta
         double a = q0 > 0.0 ? (2.0 * kr * kr) / (q0 * q0) : 0.0;
         for (int n = 0; n <= M; ++n) {
             double mu = (double)(2 * n - M) / (double)M;
-            pdf[n] = kind == 0 ? or_pdf_kn(k, mu) : or_pdf_rayleigh(a, mu);
+            pdf[n] = kind == 0 ? or_pdf_kn(k, mu) : kind == 1 ? or_pdf_rayleigh(a, mu) : or_pdf_wh(k, a, mu);
         }
         cdf[0] = 0.0;
         for (int n = 1; n <= M; ++n) cdf[n] = cdf[n - 1] + (pdf[n - 1] + pdf[n]);
@@ -310,6 +355,11 @@ void or_build_rayleigh_surface(double q0, int e_min, int n_e, int n_zeta, double
     or_build_surface(1, q0, e_min, n_e, n_zeta, out);
 }
 
+void or_build_wh_surface(double sq0, int e_min, int n_e, int n_zeta, double *out)
+{
+    or_build_surface(2, sq0, e_min, n_e, n_zeta, out);
+}
+
 /* ===================================================================== */
 /* Set-up: tables, majorant, surfaces, batch and bin offsets.            */
 /* ===================================================================== */
@@ -319,7 +369,8 @@ struct or_setup {
     int n_e;
     double *tab64; float *tab32;   /* [n_mat][n_e][3]: PE, PE+C, PE+C+R mass attenuation */
     double *mm64; float *mm32;     /* [n_e] majorant mu_max(E), 1/cm (Sec. 2.1)         */
-    double *cs64; float *cs32;     /* [n_e][n_zeta] C surface                            */
+    int n_cs;                      /* C surfaces: 1 (Klein-Nishina) or n_mat (Waller-Hartree) */
+    double *cs64; float *cs32;     /* [n_cs][n_e][n_zeta] C surfaces                     */
     double *rs64; float *rs32;     /* [n_mat][n_e][n_zeta] R surfaces                    */
     uint64_t n_lo, n_rem;          /* batch sizes: first n_rem batches hold n_lo + 1     */
     uint64_t *pref_big, *pref_small; /* [nbins + 1] bin start offsets inside a batch     */
@@ -346,6 +397,7 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
     if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || p->n_mat <= 0 || p->nbins <= 0) return NULL;
     if (p->e_max <= p->e_min || p->e_min <= 0 || p->n_zeta < 2 || p->n_batches <= 0) return NULL;
     if (!(p->majorant_scale >= 1.0)) return NULL;
+    if (p->compton != OR_COMPTON_KN && p->compton != OR_COMPTON_WH) return NULL;
     for (int j = 0; j < p->nbins; ++j)
         if (!(p->e_lo[j] >= p->e_min && p->e_hi[j] <= p->e_max && p->e_hi[j] >= p->e_lo[j])) return NULL;
     or_setup *s = (or_setup *)calloc(1, sizeof(or_setup));
@@ -360,8 +412,9 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
     s->tab32 = (float *)malloc(sizeof(float) * (size_t)nm * n_e * 3);
     s->mm64 = (double *)malloc(sizeof(double) * n_e);
     s->mm32 = (float *)malloc(sizeof(float) * n_e);
-    s->cs64 = (double *)malloc(sizeof(double) * (size_t)n_e * nz);
-    s->cs32 = (float *)malloc(sizeof(float) * (size_t)n_e * nz);
+    s->n_cs = p->compton == OR_COMPTON_WH ? nm : 1;
+    s->cs64 = (double *)malloc(sizeof(double) * (size_t)s->n_cs * n_e * nz);
+    s->cs32 = (float *)malloc(sizeof(float) * (size_t)s->n_cs * n_e * nz);
     s->rs64 = (double *)malloc(sizeof(double) * (size_t)nm * n_e * nz);
     s->rs32 = (float *)malloc(sizeof(float) * (size_t)nm * n_e * nz);
     double *rho_max = (double *)calloc((size_t)nm, sizeof(double));
@@ -379,7 +432,7 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
         for (int j = 0; j < n_e; ++j) {
             double e = (double)(p->e_min + j);
             double pe = or_mu_pe(&p->mats[m], e);
-            double c = or_mu_compton(&p->mats[m], e);
+            double c = p->compton == OR_COMPTON_WH ? or_mu_compton_wh(&p->mats[m], e) : or_mu_compton(&p->mats[m], e);
             double r = or_mu_rayleigh(&p->mats[m], e);
             size_t o = ((size_t)m * n_e + j) * 3;
             s->tab64[o + 0] = pe;
@@ -402,8 +455,13 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
     free(rho_max);
     free(present);
     /* surfaces */
-    or_build_kn_surface(p->e_min, n_e, nz, s->cs64);
-    for (size_t i = 0; i < (size_t)n_e * nz; ++i) s->cs32[i] = (float)s->cs64[i];
+    if (p->compton == OR_COMPTON_WH) {
+        for (int m = 0; m < nm; ++m)
+            or_build_wh_surface(p->mats[m].sq0, p->e_min, n_e, nz, s->cs64 + (size_t)m * n_e * nz);
+    } else {
+        or_build_kn_surface(p->e_min, n_e, nz, s->cs64);
+    }
+    for (size_t i = 0; i < (size_t)s->n_cs * n_e * nz; ++i) s->cs32[i] = (float)s->cs64[i];
     for (int m = 0; m < nm; ++m) {
         double *dst = s->rs64 + (size_t)m * n_e * nz;
         or_build_rayleigh_surface(p->mats[m].q0, p->e_min, n_e, nz, dst);
@@ -458,7 +516,7 @@ void or_setup_tables(const or_setup *s, double *mu_cum, double *mu_max)
 void or_setup_surfaces(const or_setup *s, double *c_surf, double *r_surf)
 {
     size_t nc = (size_t)s->n_e * s->p.n_zeta;
-    for (size_t i = 0; i < nc; ++i) c_surf[i] = s->prec == 32 ? (double)s->cs32[i] : s->cs64[i];
+    for (size_t i = 0; i < (size_t)s->n_cs * nc; ++i) c_surf[i] = s->prec == 32 ? (double)s->cs32[i] : s->cs64[i];
     size_t nr = (size_t)s->p.n_mat * nc;
     for (size_t i = 0; i < nr; ++i) r_surf[i] = s->prec == 32 ? (double)s->rs32[i] : s->rs64[i];
 }
@@ -504,6 +562,34 @@ static double or_exact_kn(double e_kev, uint64_t seed, uint64_t h, uint32_t step
             double mu = 1.0 - (x - 1.0) / k;
             if (r3 <= 0.5 * (mu * mu + 1.0 / x)) { *ok = 1; return mu; }
         }
+    }
+    *ok = 0;
+    return 1.0;
+}
+
+/* Waller-Hartree: a Klein-Nishina draw by Kahn's method, kept with probability
+ * S(q)/Z <= 1 (the fourth word of the same block), else a new trial. */
+static double or_exact_wh(double sq0, double e_kev, uint64_t seed, uint64_t h, uint32_t step, int *ok)
+{
+    double k = e_kev / OR_MEC2;
+    double a = or_wh_a(e_kev, sq0);
+    double p1 = (1.0 + 2.0 * k) / (9.0 + 2.0 * k);
+    for (uint32_t t = 0; t < OR_MAX_TRIALS_WH; ++t) {
+        uint32_t b[4];
+        or_block(seed, h, step, OR_STREAM_EXACT | (t << 8), b);
+        double r1 = or_uniform(b[0]), r2 = or_uniform(b[1]), r3 = or_uniform(b[2]), r4 = or_uniform(b[3]);
+        double mu;
+        if (r1 <= p1) {
+            double x = 1.0 + 2.0 * k * r2;
+            if (!(r3 <= 4.0 * (1.0 / x - 1.0 / (x * x)))) continue;
+            mu = 1.0 - (x - 1.0) / k;
+        } else {
+            double x = (1.0 + 2.0 * k) / (1.0 + 2.0 * k * r2);
+            mu = 1.0 - (x - 1.0) / k;
+            if (!(r3 <= 0.5 * (mu * mu + 1.0 / x))) continue;
+        }
+        double sz = a > 0.0 ? -expm1(-a * (1.0 - mu)) : 1.0;
+        if (r4 <= sz) { *ok = 1; return mu; }
     }
     *ok = 0;
     return 1.0;

@@ -30,17 +30,23 @@
 extern "C" {
 #endif
 
-/* Material record: the closed-form cross sections need these four numbers. */
+/* Material record: the closed-form cross sections need these numbers. */
 typedef struct {
-    double z_over_a;  /* electrons per gram / N_A (Compton, Eq. 2 with S = 1)      */
+    double z_over_a;  /* electrons per gram / N_A (Compton, Eq. 2)                 */
     double a_mol;     /* molar mass of one formula unit, g/mol (PE and Rayleigh)   */
     double z_eff;     /* effective atomic number (PE ~ Z^4, Rayleigh ~ Z^2)         */
     double q0;        /* analytic form-factor width, 1/Angstrom; <= 0 means F^2 = 1 */
+    double sq0;       /* analytic scattering-function width for the Waller-Hartree
+                         Compton model, S(q)/Z = 1 - exp(-q^2/sq0^2), 1/Angstrom;
+                         <= 0 means S/Z = 1 (free electrons)                      */
 } or_material;
 
 enum { OR_SRC_STATIC = 0, OR_SRC_ARC = 1 };
 enum { OR_MODE_FULL = 0, OR_MODE_MAX_REAL = 1 };
 enum { OR_SAMPLE_SURFACE = 0, OR_SAMPLE_EXACT = 1 };
+/* Compton model (Sec. 2.2.3): free-electron Klein-Nishina (Eq. 2 with S = 1) or
+ * Waller-Hartree (Eq. 2 with the material's scattering function S(q)). */
+enum { OR_COMPTON_KN = 0, OR_COMPTON_WH = 1 };
 
 typedef struct {
     /* phantom: x fastest, then y, then z; centred at the origin */
@@ -67,6 +73,7 @@ typedef struct {
     int mode;                     /* OR_MODE_* */
     int max_real;                 /* real interactions before termination (OR_MODE_MAX_REAL) */
     int sampling;                 /* OR_SAMPLE_* (EXACT only in f64) */
+    int compton;                  /* OR_COMPTON_* */
     /* run */
     uint64_t n_hist;
     int n_batches;
@@ -90,6 +97,11 @@ double or_sigma_kn(double e_kev);                  /* cm^2 per electron */
 double or_mu_pe(const or_material *m, double e_kev);
 double or_mu_compton(const or_material *m, double e_kev);
 double or_mu_rayleigh(const or_material *m, double e_kev);
+/* Waller-Hartree: pi r0^2 times the composite Simpson integral over mu in
+ * [-1, 1] (20000 intervals) of (E'/E)^2 (E'/E + E/E' - sin^2 theta) S(q)/Z,
+ * cm^2 per electron; sq0 <= 0 integrates Klein-Nishina alone */
+double or_sigma_wh(double e_kev, double sq0);
+double or_mu_compton_wh(const or_material *m, double e_kev);
 
 /* integer allocation of n histories to bins by largest remainder */
 int or_allocate(uint64_t n, int nbins, const double *w, uint64_t *out);
@@ -111,15 +123,17 @@ int or_transport_f32(const or_setup *s, uint64_t h0, uint64_t h1, double *edep, 
 /* inspection of the set-up (node values as stored; f32 values widened) */
 int or_setup_sizes(const or_setup *s, int *n_e, int *n_zeta, int *n_mat);
 void or_setup_tables(const or_setup *s, double *mu_cum /* n_mat*n_e*3 */, double *mu_max /* n_e */);
-void or_setup_surfaces(const or_setup *s, double *c_surf /* n_e*n_zeta */,
+void or_setup_surfaces(const or_setup *s, double *c_surf /* n_c*n_e*n_zeta, n_c = 1 (KN) or n_mat (WH) */,
                        double *r_surf /* n_mat*n_e*n_zeta */);
 
 /* the surfaces on their own (Sec. 2.2.2 and 2.2.3), binary64 */
 void or_build_kn_surface(int e_min, int n_e, int n_zeta, double *out);
 void or_build_rayleigh_surface(double q0, int e_min, int n_e, int n_zeta, double *out);
+void or_build_wh_surface(double sq0, int e_min, int n_e, int n_zeta, double *out);
 
 /* angular samplers for the sampler validation of Figs. 3-4:
- * kind 0 = Compton (free-electron Klein-Nishina), 1 = Rayleigh;
+ * kind 0 = Compton (the set-up's model; Waller-Hartree reads the material's
+ * scattering function), 1 = Rayleigh;
  * surface samplers read the set-up's surfaces at E; exact samplers use rejection. */
 int or_sample_mu_f64(const or_setup *s, int kind, int material, double e_kev, int exact,
                      uint64_t seed, uint64_t n, double *out);

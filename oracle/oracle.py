@@ -31,7 +31,8 @@ def lib():
 
 
 class OrMaterial(C.Structure):
-    _fields_ = [("z_over_a", C.c_double), ("a_mol", C.c_double), ("z_eff", C.c_double), ("q0", C.c_double)]
+    _fields_ = [("z_over_a", C.c_double), ("a_mol", C.c_double), ("z_eff", C.c_double), ("q0", C.c_double),
+                ("sq0", C.c_double)]
 
 
 class OrProblem(C.Structure):
@@ -46,7 +47,7 @@ class OrProblem(C.Structure):
         ("nbins", C.c_int), ("e_lo", C.POINTER(C.c_double)), ("e_hi", C.POINTER(C.c_double)),
         ("w", C.POINTER(C.c_double)),
         ("e_min", C.c_int), ("e_max", C.c_int), ("n_zeta", C.c_int), ("majorant_scale", C.c_double),
-        ("mode", C.c_int), ("max_real", C.c_int), ("sampling", C.c_int),
+        ("mode", C.c_int), ("max_real", C.c_int), ("sampling", C.c_int), ("compton", C.c_int),
         ("n_hist", C.c_uint64), ("n_batches", C.c_int), ("seed", C.c_uint64),
     ]
 
@@ -67,11 +68,14 @@ def _declare(L):
     L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
     L.or_uniform.restype = C.c_double
     L.or_uniform.argtypes = [C.c_uint32]
-    for n in ("or_mu_pe", "or_mu_compton", "or_mu_rayleigh"):
+    for n in ("or_mu_pe", "or_mu_compton", "or_mu_rayleigh", "or_mu_compton_wh"):
         getattr(L, n).restype = C.c_double
         getattr(L, n).argtypes = [C.POINTER(OrMaterial), C.c_double]
     L.or_sigma_kn.restype = C.c_double
     L.or_sigma_kn.argtypes = [C.c_double]
+    L.or_sigma_wh.restype = C.c_double
+    L.or_sigma_wh.argtypes = [C.c_double, C.c_double]
+    L.or_build_wh_surface.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int, dp]
     L.or_allocate.argtypes = [C.c_uint64, C.c_int, dp, C.POINTER(C.c_uint64)]
     L.or_log_f32.restype = C.c_float
     L.or_log_f32.argtypes = [C.c_float]
@@ -114,7 +118,7 @@ def uniform(x: int) -> float:
 
 
 def material_struct(m) -> OrMaterial:
-    return OrMaterial(m.z_over_a, m.a_mol, m.z_eff, m.q0)
+    return OrMaterial(m.z_over_a, m.a_mol, m.z_eff, m.q0, m.sq0)
 
 
 def mu_pe(m, e):
@@ -131,6 +135,15 @@ def mu_rayleigh(m, e):
 
 def sigma_kn(e):
     return lib().or_sigma_kn(e)
+
+
+def sigma_wh(e, sq0):
+    """Waller-Hartree total per electron (cm^2), Simpson over mu."""
+    return lib().or_sigma_wh(e, sq0)
+
+
+def mu_compton_wh(m, e):
+    return lib().or_mu_compton_wh(C.byref(material_struct(m)), e)
 
 
 def allocate(n: int, w) -> np.ndarray:
@@ -179,10 +192,17 @@ def rayleigh_surface(q0, e_min, n_e, n_zeta):
     return out
 
 
+def wh_surface(sq0, e_min, n_e, n_zeta):
+    out = np.empty((n_e, n_zeta), dtype=np.float64)
+    lib().or_build_wh_surface(sq0, e_min, n_e, n_zeta, _ptr(out, C.c_double))
+    return out
+
+
 # --------------------------------------------------------------------------
 # problem set-up and transport
 # --------------------------------------------------------------------------
 _MODES = {"full": 0, "max_real": 1}
+_COMPTON = {"kn": 0, "wh": 1}
 
 
 class Setup:
@@ -215,6 +235,8 @@ class Setup:
         p.e_min, p.e_max, p.n_zeta = phy.e_min, phy.e_max, phy.n_zeta
         p.majorant_scale, p.mode, p.max_real = phy.majorant_scale, mode, phy.max_real
         p.sampling = 0 if sampling == "surface" else 1
+        self.compton = getattr(phy, "compton", "kn")
+        p.compton = _COMPTON[self.compton]
         p.n_hist, p.n_batches, p.seed = problem.n_hist, problem.n_batches, problem.seed
         self._p = p
         fn = lib().or_setup_create_f64 if precision == 64 else lib().or_setup_create_f32
@@ -238,7 +260,9 @@ class Setup:
         return cum, mm
 
     def surfaces(self):
-        cs = np.empty((self.n_e, self.n_zeta), dtype=np.float64)
+        """C surfaces ([n_e][n_zeta], or [n_mat][n_e][n_zeta] for Waller-Hartree) and R surfaces."""
+        shape = (self.n_mat, self.n_e, self.n_zeta) if self.compton == "wh" else (self.n_e, self.n_zeta)
+        cs = np.empty(shape, dtype=np.float64)
         rs = np.empty((self.n_mat, self.n_e, self.n_zeta), dtype=np.float64)
         lib().or_setup_surfaces(self.handle, _ptr(cs, C.c_double), _ptr(rs, C.c_double))
         return cs, rs

@@ -35,6 +35,8 @@ class Material:
     z_eff    : effective atomic number
     q0       : form-factor width in 1/Angstrom; 0 selects F^2 = 1 (Thomson)
     density  : nominal density (g/cm^3), used by the phantom generators only
+    sq0      : scattering-function width in 1/Angstrom for the Waller-Hartree
+               Compton model, S(q)/Z = 1 - exp(-q^2/sq0^2); 0 selects S/Z = 1
     """
     name: str
     z_over_a: float
@@ -42,10 +44,16 @@ class Material:
     z_eff: float
     q0: float
     density: float
+    sq0: float = 0.55
 
 
-def _mat(name, z_over_a, z_eff, density, a_mol=None, q0=1.0):
-    return Material(name, z_over_a, a_mol if a_mol is not None else 10.0 / z_over_a, z_eff, q0, density)
+# proposed scattering-function width (the paper's PENELOPE tables are not
+# available): S/Z of water's electrons is about 0.4 at sin(theta/2)/lambda = 0.2/A
+SQ0 = 0.55
+
+
+def _mat(name, z_over_a, z_eff, density, a_mol=None, q0=1.0, sq0=SQ0):
+    return Material(name, z_over_a, a_mol if a_mol is not None else 10.0 / z_over_a, z_eff, q0, density, sq0)
 
 
 WATER = _mat("water", 0.5551, 7.42, 1.0, a_mol=18.015)
@@ -114,6 +122,7 @@ class Physics:
     majorant_scale: float = 1.0
     mode: str = "full"          # "full" | "max_real" ("primary" is max_real with 1)
     max_real: int = 0
+    compton: str = "kn"         # "kn" free-electron Klein-Nishina | "wh" Waller-Hartree (Eq. 2 with S)
 
 
 @dataclass

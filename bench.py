@@ -55,15 +55,18 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload(name):
+def workload(name, compton="kn"):
+    """The named workload; compton "wh" switches it to the Waller-Hartree model."""
+    import dataclasses
+
     from paper_1109_3266_gb300 import inputs as I
-    if name == "cbct_water":
-        return I.cbct_water()
-    if name == "head":
-        return I.head()
-    if name == "tiny_water":
-        return I.tiny_water()
-    raise SystemExit(f"unknown workload {name}")
+    makers = {"cbct_water": I.cbct_water, "head": I.head, "tiny_water": I.tiny_water}
+    if name not in makers:
+        raise SystemExit(f"unknown workload {name}")
+    p = makers[name]()
+    if compton != "kn":
+        p = I.scaled(p, physics=dataclasses.replace(p.physics, compton=compton))
+    return p
 
 
 class Clocks:
@@ -194,7 +197,7 @@ def run_reference(args):
     rank, world = dist_init(args.gpus)
     if rank != 0:
         return
-    p = workload(args.workload)
+    p = workload(args.workload, args.compton)
     threads = cpu_cores()
     for _ in range(args.warmup):
         oracle_rate(p, 0.5, threads)
@@ -210,7 +213,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ns[0] / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": p.name, "histories_per_step": ns[0]},
+        "config": {"workload": p.name, "histories_per_step": ns[0], "compton": args.compton},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -227,7 +230,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    p = workload(args.workload)
+    p = workload(args.workload, args.compton)
     seed = p.seed + 7919 * rank
     nvox = p.phantom.nvox
     ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
@@ -313,7 +316,8 @@ def run_ours(args):
     ck = clk.summary()
     mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = SM_COUNT * LANES_PER_SM_CLK * mhz * 1e6 / 1e12        # tera lane-instructions / s
-    prof = KERNEL_PROFILE.get(p.name, {})
+    # the lane-instruction count was measured for the Klein-Nishina model
+    prof = KERNEL_PROFILE.get(p.name, {}) if args.compton == "kn" else {}
     inst_per_hist = args.inst_per_history or prof.get("lane_inst_per_history")
     achieved = p.n_hist * args.steps * inst_per_hist / t_transport / 1e12 if inst_per_hist else None
     traffic = args.traffic_per_launch or prof.get("dram_bytes_per_launch")
@@ -367,7 +371,7 @@ def run_ours(args):
                        "kvp": 120 if p.name == "cbct_water" else None, "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (256 MB write outside timed events)",
                        "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk,
-                       "flight_cap": args.flight_cap},
+                       "flight_cap": args.flight_cap, "compton": args.compton},
             "sec_to_1pct_avg_rsd": measured_1["seconds"] if measured_1 else sec_to_1,
             "sec_to_1pct_avg_rsd_extrapolated": sec_to_1, "rsd_stopped_run": measured_1,
             "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
@@ -520,6 +524,8 @@ def main():
     ap.add_argument("--time-limit", type=float, default=None)
     ap.add_argument("--multi-blocks-per-sm", type=int, default=0)
     ap.add_argument("--shared-launch", type=int, default=0, help="served form: one shared multi-request launch")
+    ap.add_argument("--compton", default="kn", choices=["kn", "wh"],
+                    help="Compton model: free-electron Klein-Nishina or Waller-Hartree")
     ap.add_argument("--hist-lo", type=float, default=1e7)
     ap.add_argument("--hist-hi", type=float, default=1e9)
     ap.add_argument("--traffic-per-launch", type=float, default=None)

@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 2
+#define CTD_ABI_VERSION 3
 
 typedef enum {
     CTD_OK = 0,
@@ -66,12 +66,16 @@ typedef struct {
  *   a_mol    : g/mol of one formula unit (photoelectric 1e-2 Z^4/E_MeV^3 microbarn,
  *              Rayleigh 1.565e-5 Z^2/E_MeV^2 barn, both per formula unit)
  *   z_eff    : effective atomic number
- *   q0       : Rayleigh form-factor width F^2 ~ exp(-q^2/q0^2), 1/Angstrom; <= 0: F^2 = 1 */
+ *   q0       : Rayleigh form-factor width F^2 ~ exp(-q^2/q0^2), 1/Angstrom; <= 0: F^2 = 1
+ *   sq0      : scattering-function width of the Waller-Hartree Compton model,
+ *              S(q)/Z = 1 - exp(-q^2/sq0^2), 1/Angstrom; <= 0: S/Z = 1 (free electrons).
+ * q^2 = 2 k^2 (1 - cos theta) with k = E/hc, for both. */
 typedef struct {
     double z_over_a;
     double a_mol;
     double z_eff;
     double q0;
+    double sq0;
 } ctd_material;
 
 typedef enum { CTD_SRC_STATIC = 0, CTD_SRC_ARC = 1 } ctd_source_kind;
@@ -98,7 +102,13 @@ typedef enum { CTD_MODE_FULL = 0, CTD_MODE_MAX_REAL = 1 } ctd_mode;
  * also the absorption energy (Sec. 3.1).  n_zeta columns per R/C surface row
  * (Sec. 2.2.2-2.2.3).  majorant_scale >= 1 multiplies mu_max(E) (Sec. 2.1).
  * CTD_MODE_MAX_REAL stops a photon after max_real real interactions (1 =
- * primary only), counting its remaining energy as escaped. */
+ * primary only), counting its remaining energy as escaped.
+ * compton_model (Sec. 2.2.3): CTD_COMPTON_KN, free-electron Klein-Nishina
+ * (Eq. 2 with S = 1; total in closed form, one C surface for all materials);
+ * CTD_COMPTON_WH, Waller-Hartree (Eq. 2 with each material's S(q); total by
+ * composite Simpson integration of Eq. 2 over 20000 intervals in cos theta,
+ * one C surface per material). */
+typedef enum { CTD_COMPTON_KN = 0, CTD_COMPTON_WH = 1 } ctd_compton_model;
 typedef struct {
     int e_min_kev;
     int e_max_kev;
@@ -106,6 +116,7 @@ typedef struct {
     double majorant_scale;
     int mode;
     int max_real;
+    int compton_model;
 } ctd_physics;
 
 /* Results of the last run of a phantom. */
@@ -268,13 +279,15 @@ int ctd_get_edep(ctd_ctx *ctx, ctd_phantom ph, double *edep_kev, size_t nvox);
 
 /* The binary32 tables the device uses, widened to double: mu_cum[n_mat][n_e][3]
  * (photoelectric, +Compton, +Rayleigh, cm^2/g), mu_max[n_e] (1/cm),
- * c_surf[n_e][n_zeta], r_surf[n_mat][n_e][n_zeta].  Sizes via the out-params
+ * c_surf[n_c][n_e][n_zeta] (n_c = 1 under Klein-Nishina, n_mat under
+ * Waller-Hartree), r_surf[n_mat][n_e][n_zeta].  Sizes via the out-params
  * (any pointer may be NULL).  Builds the tables if needed. */
 int ctd_get_tables(ctd_ctx *ctx, ctd_phantom ph, int *n_e, int *n_zeta, int *n_mat, double *mu_cum,
                    double *mu_max, double *c_surf, double *r_surf);
 
 /* Sampler validation (Figs. 3-4): n polar cosines at energy e_kev drawn on the
- * device from the C surface (kind 0) or the R surface of material (kind 1),
+ * device from the C surface (kind 0; under Waller-Hartree that of material)
+ * or the R surface of material (kind 1),
  * the i-th from Philox counter (i, 0, 0, 3) under seed.  out: host doubles. */
 int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e_kev, uint64_t seed,
                   uint64_t n, double *out);

@@ -197,8 +197,9 @@ int busy(Phantom *P)
                        : CTD_OK;
 }
 
-// C (kind 0) or R (kind 1, form-factor width q0) surface in binary32, built
-// once per context and node grid.
+// Klein-Nishina C (kind 0), Rayleigh R (kind 1, form-factor width q0) or
+// Waller-Hartree C (kind 2, scattering-function width q0) surface in binary32,
+// built once per context and node grid.
 const std::vector<float> &angular_surface(ctd_ctx *ctx, int kind, double q0, int e_min, int n_e, int n_zeta)
 {
     const std::array<double, 5> key{static_cast<double>(kind), kind ? (q0 > 0.0 ? q0 : 0.0) : 0.0,
@@ -221,26 +222,36 @@ int build_tables(ctd_ctx *ctx, Phantom &P)
     const int n_e = ph.e_max_kev - ph.e_min_kev + 1;
     const int nm = static_cast<int>(P.mats.size());
     std::vector<double> cum, mmax;
-    ctd::build_tables(P.mats, P.rho_max, P.present, ph.e_min_kev, n_e, ph.majorant_scale, cum, mmax);
+    ctd::build_tables(P.mats, P.rho_max, P.present, ph.e_min_kev, n_e, ph.majorant_scale, ph.compton_model, cum,
+                      mmax);
     P.h_tab.assign(static_cast<size_t>(nm) * n_e * 4, 0.0f);
     for (size_t i = 0; i < static_cast<size_t>(nm) * n_e; ++i)
         for (int c = 0; c < 3; ++c) P.h_tab[i * 4 + c] = static_cast<float>(cum[i * 3 + c]);
     P.h_mm.resize(n_e);
     for (int j = 0; j < n_e; ++j) P.h_mm[j] = static_cast<float>(mmax[j]);
     const size_t row = static_cast<size_t>(n_e) * ph.n_zeta;
-    P.h_cs = angular_surface(ctx, 0, 0.0, ph.e_min_kev, n_e, ph.n_zeta);
+    if (ph.compton_model == CTD_COMPTON_WH) {
+        // one Waller-Hartree C surface per material
+        P.h_cs.resize(row * nm);
+        for (int m = 0; m < nm; ++m) {
+            const std::vector<float> &c = angular_surface(ctx, 2, P.mats[m].sq0, ph.e_min_kev, n_e, ph.n_zeta);
+            std::copy(c.begin(), c.end(), P.h_cs.begin() + m * row);
+        }
+    } else {
+        P.h_cs = angular_surface(ctx, 0, 0.0, ph.e_min_kev, n_e, ph.n_zeta);
+    }
     P.h_rs.resize(row * nm);
     for (int m = 0; m < nm; ++m) {
         const std::vector<float> &r = angular_surface(ctx, 1, P.mats[m].q0, ph.e_min_kev, n_e, ph.n_zeta);
         std::copy(r.begin(), r.end(), P.h_rs.begin() + m * row);
     }
     int rc;
-    if ((rc = P.tab.ensure(P.h_tab.size())) || (rc = P.mm.ensure(n_e)) || (rc = P.cs.ensure(row)) ||
+    if ((rc = P.tab.ensure(P.h_tab.size())) || (rc = P.mm.ensure(n_e)) || (rc = P.cs.ensure(P.h_cs.size())) ||
         (rc = P.rs.ensure(row * nm)))
         return rc;
     CK(cudaMemcpyAsync(P.tab.p, P.h_tab.data(), P.h_tab.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(P.mm.p, P.h_mm.data(), n_e * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(P.cs.p, P.h_cs.data(), row * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P.cs.p, P.h_cs.data(), P.h_cs.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(P.rs.p, P.h_rs.data(), row * nm * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     P.n_e = n_e;
@@ -301,6 +312,8 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     q.tab = P.tab.p;
     q.mmax = P.mm.p;
     q.rsurf = P.rs.p;
+    q.csurf = P.cs.p;
+    q.cs_stride = P.phys.compton_model == CTD_COMPTON_WH ? P.n_e * P.phys.n_zeta : 0;
     q.n_mat = static_cast<int>(P.mats.size());
     q.work = P.work.p;
     q.nbins = static_cast<int>(P.w.size());
@@ -348,7 +361,6 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
 
 void fill_shared(Phantom &P, ctd::SharedTables &sh)
 {
-    sh.csurf = P.cs.p;
     sh.n_e = P.n_e;
     sh.n_zeta = P.phys.n_zeta;
     sh.e_min = P.phys.e_min_kev;
@@ -613,8 +625,9 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     if (!(dx > 0 && dy > 0 && dz > 0)) return fail(CTD_EINVAL, "voxel sizes must be positive");
     if (n_mat <= 0 || n_mat > ctd::kMaxPhantomMaterials) return fail(CTD_EINVAL, "n_mat must be 1..16");
     for (int m = 0; m < n_mat; ++m)
-        if (!(mats[m].z_over_a > 0 && mats[m].a_mol > 0 && mats[m].z_eff > 0))
-            return fail(CTD_EINVAL, "material %d has non-positive parameters", m);
+        if (!(mats[m].z_over_a > 0 && mats[m].a_mol > 0 && mats[m].z_eff > 0) || !std::isfinite(mats[m].q0) ||
+            !std::isfinite(mats[m].sq0))
+            return fail(CTD_EINVAL, "material %d has non-positive or non-finite parameters", m);
     const size_t nvox = static_cast<size_t>(nx) * ny * nz;
     if (nvox > (static_cast<size_t>(1) << 40)) return fail(CTD_EINVAL, "phantom too large");
     std::unique_ptr<Phantom> P(new Phantom());
@@ -638,6 +651,7 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     P->phys.majorant_scale = 1.0;
     P->phys.mode = CTD_MODE_FULL;
     P->phys.max_real = 0;
+    P->phys.compton_model = CTD_COMPTON_KN;
     if ((rc = P->mat.ensure(nvox)) || (rc = P->rho.ensure(nvox))) return rc;
     CK(cudaMemcpyAsync(P->mat.p, mat, nvox, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(P->rho.p, density, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
@@ -675,6 +689,8 @@ int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys)
         return fail(CTD_EINVAL, "majorant_scale must be >= 1");
     if (phys->mode != CTD_MODE_FULL && phys->mode != CTD_MODE_MAX_REAL) return fail(CTD_EINVAL, "unknown mode");
     if (phys->mode == CTD_MODE_MAX_REAL && phys->max_real < 1) return fail(CTD_EINVAL, "max_real must be >= 1");
+    if (phys->compton_model != CTD_COMPTON_KN && phys->compton_model != CTD_COMPTON_WH)
+        return fail(CTD_EINVAL, "unknown Compton model");
     P->phys = *phys;
     P->tables_ok = false;
     return CTD_OK;
@@ -1108,7 +1124,9 @@ int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e
     if (n == 0) return CTD_OK;
     DevBuf<double> buf;
     if ((rc = buf.ensure(n))) return rc;
-    const float *surf = kind == 0 ? P->cs.p : P->rs.p + static_cast<size_t>(material) * P->n_e * P->phys.n_zeta;
+    const size_t row = static_cast<size_t>(P->n_e) * P->phys.n_zeta;
+    const float *surf = kind == 1 ? P->rs.p + material * row
+                                  : P->cs.p + (P->phys.compton_model == CTD_COMPTON_WH ? material * row : 0);
     CKS(ctd::launch_sample_mu(surf, P->phys.n_zeta, P->n_e, P->phys.e_min_kev, static_cast<float>(e_kev), seed, n,
                               buf.p, ctx->stream));
     CK(cudaMemcpyAsync(out, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

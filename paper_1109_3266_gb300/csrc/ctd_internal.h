@@ -31,12 +31,15 @@ double sigma_kn(double e_kev);
 double mu_pe(const ctd_material &m, double e_kev);
 double mu_compton(const ctd_material &m, double e_kev);
 double mu_rayleigh(const ctd_material &m, double e_kev);
+double sigma_wh(double e_kev, double sq0);
+double mu_compton_wh(const ctd_material &m, double e_kev);
 
 // Node tables: cum[(m*n_e + j)*3 + c] cumulative mass attenuation; mmax[j] majorant.
 void build_tables(const std::vector<ctd_material> &mats, const std::vector<double> &rho_max,
-                  const std::vector<int> &present, int e_min, int n_e, double scale,
+                  const std::vector<int> &present, int e_min, int n_e, double scale, int compton_model,
                   std::vector<double> &cum, std::vector<double> &mmax);
-// Inverse-cdf surface rows for node energies e_min..e_min+n_e-1: kind 0 Klein-Nishina, 1 Rayleigh.
+// Inverse-cdf surface rows for node energies e_min..e_min+n_e-1: kind 0 Klein-Nishina,
+// 1 Rayleigh of form-factor width q0, 2 Waller-Hartree of scattering-function width q0.
 void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out);
 // Largest-remainder allocation; false if the weights are unusable.
 bool allocate(uint64_t n, const std::vector<double> &w, std::vector<uint64_t> &out);
@@ -66,6 +69,7 @@ struct alignas(16) RequestDesc {
     const float *tab;            // [n_mat][n_e][4]: c1, c2, c3, 0 (cm^2/g)
     const float *mmax;           // [n_e] majorant mu_max(E), 1/cm
     const float *rsurf;          // [n_mat][n_e][n_zeta] R surfaces
+    const float *csurf;          // [n_c][n_e][n_zeta] C surfaces, material m at m * cs_stride
     const uint64_t *pref;        // [nbins+1] bin starts inside the batch
     const float *bin_lo;         // [nbins]
     const float *bin_hi;         // [nbins]
@@ -85,6 +89,7 @@ struct alignas(16) RequestDesc {
     int src_kind, n_proj, continuous;
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
     int mode, max_real;
+    int cs_stride;               // 0 (one Klein-Nishina surface) or n_e * n_zeta (Waller-Hartree)
     uint32_t rk[20];             // Philox round keys of seed: (lo, hi) + r (Weyl constants), r = 0..9
 };
 
@@ -95,7 +100,6 @@ constexpr int kMaxPhantomMaterials = 16;
 
 // What every request of a launch shares: the node grid and the C surface.
 struct SharedTables {
-    const float *csurf;          // [n_e][n_zeta]
     int n_e, n_zeta, e_min;
     int max_n_mat;               // largest n_mat of the launch's requests (shared-memory size)
 };

@@ -28,6 +28,49 @@ double mu_compton(const ctd_material &m, double e_kev)
     return (kNA * m.z_over_a) * sigma_kn(e_kev);
 }
 
+namespace {
+
+// Eq. 2 up to r0^2/2: the Klein-Nishina density in mu = cos theta times the
+// scattering function S/Z = 1 - exp(-a (1 - mu)), a = 2 k^2 / sq0^2 (a <= 0: 1).
+inline double density_wh(double k, double a, double mu)
+{
+    const double e = 1.0 / (1.0 + k * (1.0 - mu));
+    const double kn = (e * e) * ((e + 1.0 / e) - (1.0 - mu * mu));
+    if (a <= 0.0) return kn;
+    return kn * (-std::expm1(-a * (1.0 - mu)));
+}
+
+inline double wh_a(double e_kev, double sq0)
+{
+    const double kr = e_kev / kHc;
+    return sq0 > 0.0 ? (2.0 * kr * kr) / (sq0 * sq0) : 0.0;
+}
+
+}  // namespace
+
+// Waller-Hartree total per electron in cm^2: pi r0^2 times the composite
+// Simpson integral of Eq. 2 over mu in [-1, 1] on kCdfIntervals intervals.
+double sigma_wh(double e_kev, double sq0)
+{
+    const int M = kCdfIntervals;
+    const double k = e_kev / kMec2;
+    const double a = wh_a(e_kev, sq0);
+    double odd = 0.0, even = 0.0;
+    for (int n = 1; n < M; ++n) {
+        const double mu = static_cast<double>(2 * n - M) / static_cast<double>(M);
+        if (n & 1) odd += density_wh(k, a, mu);
+        else even += density_wh(k, a, mu);
+    }
+    const double ends = density_wh(k, a, -1.0) + density_wh(k, a, 1.0);
+    const double integral = ((2.0 / static_cast<double>(M)) / 3.0) * (ends + (4.0 * odd + 2.0 * even));
+    return (kPi * kR0 * kR0) * integral;
+}
+
+double mu_compton_wh(const ctd_material &m, double e_kev)
+{
+    return (kNA * m.z_over_a) * sigma_wh(e_kev, m.sq0);
+}
+
 // Photoelectric absorption, 1e-2 Z^4 / E_MeV^3 microbarn per formula unit (cm^2/g).
 double mu_pe(const ctd_material &m, double e_kev)
 {
@@ -47,7 +90,7 @@ double mu_rayleigh(const ctd_material &m, double e_kev)
 }
 
 void build_tables(const std::vector<ctd_material> &mats, const std::vector<double> &rho_max,
-                  const std::vector<int> &present, int e_min, int n_e, double scale,
+                  const std::vector<int> &present, int e_min, int n_e, double scale, int compton_model,
                   std::vector<double> &cum, std::vector<double> &mmax)
 {
     const size_t nm = mats.size();
@@ -57,7 +100,7 @@ void build_tables(const std::vector<ctd_material> &mats, const std::vector<doubl
         for (int j = 0; j < n_e; ++j) {
             const double e = static_cast<double>(e_min + j);
             const double pe = mu_pe(mats[m], e);
-            const double c = mu_compton(mats[m], e);
+            const double c = compton_model == CTD_COMPTON_WH ? mu_compton_wh(mats[m], e) : mu_compton(mats[m], e);
             const double r = mu_rayleigh(mats[m], e);
             double *dst = &cum[(m * n_e + j) * 3];
             dst[0] = pe;
@@ -108,7 +151,10 @@ void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *
         const double k = e / kMec2;
         const double kr = e / kHc;
         const double a = q0 > 0.0 ? (2.0 * kr * kr) / (q0 * q0) : 0.0;
-        for (int n = 0; n <= M; ++n) pdf[n] = kind == 0 ? density_kn(k, grid_mu(n)) : density_rayleigh(a, grid_mu(n));
+        for (int n = 0; n <= M; ++n)
+            pdf[n] = kind == 0 ? density_kn(k, grid_mu(n))
+                     : kind == 1 ? density_rayleigh(a, grid_mu(n))
+                                 : density_wh(k, a, grid_mu(n));
         // cumulative trapezoid without the common factor h/2
         cdf[0] = 0.0;
         for (int n = 1; n <= M; ++n) cdf[n] = cdf[n - 1] + (pdf[n - 1] + pdf[n]);

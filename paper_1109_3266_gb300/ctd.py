@@ -36,7 +36,8 @@ class ctd_options(C.Structure):
 
 
 class ctd_material(C.Structure):
-    _fields_ = [("z_over_a", C.c_double), ("a_mol", C.c_double), ("z_eff", C.c_double), ("q0", C.c_double)]
+    _fields_ = [("z_over_a", C.c_double), ("a_mol", C.c_double), ("z_eff", C.c_double), ("q0", C.c_double),
+                ("sq0", C.c_double)]
 
 
 class ctd_source(C.Structure):
@@ -47,7 +48,7 @@ class ctd_source(C.Structure):
 
 class ctd_physics(C.Structure):
     _fields_ = [("e_min_kev", C.c_int), ("e_max_kev", C.c_int), ("n_zeta", C.c_int), ("majorant_scale", C.c_double),
-                ("mode", C.c_int), ("max_real", C.c_int)]
+                ("mode", C.c_int), ("max_real", C.c_int), ("compton_model", C.c_int)]
 
 
 class ctd_run_stats(C.Structure):
@@ -161,7 +162,8 @@ def ctd_create_phantom(ctx, nx, ny, nz, dx, dy, dz, mat, density, materials):
     n = nx * ny * nz
     if mat.size != n or density.size != n:
         raise CtdError(1, "voxel arrays must hold nx*ny*nz values")
-    ms = (ctd_material * len(materials))(*[ctd_material(m.z_over_a, m.a_mol, m.z_eff, m.q0) for m in materials])
+    ms = (ctd_material * len(materials))(*[ctd_material(m.z_over_a, m.a_mol, m.z_eff, m.q0, m.sq0)
+                                            for m in materials])
     out = C.c_int32()
     _check(lib().ctd_create_phantom(ctx, nx, ny, nz, dx, dy, dz, mat.ctypes.data_as(C.POINTER(C.c_uint8)),
                                     density.ctypes.data_as(C.POINTER(C.c_float)), len(materials), ms, C.byref(out)))
@@ -172,9 +174,15 @@ def ctd_destroy_phantom(ctx, ph):
     _check(lib().ctd_destroy_phantom(ctx, ph))
 
 
-def ctd_set_physics(ctx, ph, e_min_kev=1, e_max_kev=150, n_zeta=1024, majorant_scale=1.0, mode="full", max_real=0):
+CTD_COMPTON_KN, CTD_COMPTON_WH = 0, 1
+
+
+def ctd_set_physics(ctx, ph, e_min_kev=1, e_max_kev=150, n_zeta=1024, majorant_scale=1.0, mode="full", max_real=0,
+                    compton="kn"):
+    """compton: "kn" (free-electron Klein-Nishina) or "wh" (Waller-Hartree)."""
     m = {"full": CTD_MODE_FULL, "max_real": CTD_MODE_MAX_REAL}[mode] if isinstance(mode, str) else int(mode)
-    p = ctd_physics(e_min_kev, e_max_kev, n_zeta, majorant_scale, m, max_real)
+    c = {"kn": CTD_COMPTON_KN, "wh": CTD_COMPTON_WH}[compton] if isinstance(compton, str) else int(compton)
+    p = ctd_physics(e_min_kev, e_max_kev, n_zeta, majorant_scale, m, max_real, c)
     _check(lib().ctd_set_physics(ctx, ph, C.byref(p)))
 
 
@@ -266,13 +274,15 @@ def ctd_get_edep(ctx, ph, nvox):
     return out
 
 
-def ctd_get_tables(ctx, ph):
+def ctd_get_tables(ctx, ph, compton="kn"):
+    """Tables as the device holds them; C surfaces [n_e][n_zeta], or
+    [n_mat][n_e][n_zeta] for a phantom set to the Waller-Hartree model."""
     ne, nz, nm = C.c_int(), C.c_int(), C.c_int()
     _check(lib().ctd_get_tables(ctx, ph, C.byref(ne), C.byref(nz), C.byref(nm), None, None, None, None))
     ne, nz, nm = ne.value, nz.value, nm.value
     cum = np.empty((nm, ne, 3))
     mm = np.empty(ne)
-    cs = np.empty((ne, nz))
+    cs = np.empty((nm, ne, nz) if compton == "wh" else (ne, nz))
     rs = np.empty((nm, ne, nz))
     _check(lib().ctd_get_tables(ctx, ph, None, None, None, _dp(cum), _dp(mm), _dp(cs), _dp(rs)))
     return cum, mm, cs, rs
@@ -313,7 +323,8 @@ def load_problem(ctx, problem, physics=True):
     ctd_set_spectrum(ctx, h, sp.e_lo, sp.e_hi, sp.w)
     if physics:
         p = problem.physics
-        ctd_set_physics(ctx, h, p.e_min, p.e_max, p.n_zeta, p.majorant_scale, p.mode, p.max_real)
+        ctd_set_physics(ctx, h, p.e_min, p.e_max, p.n_zeta, p.majorant_scale, p.mode, p.max_real,
+                        getattr(p, "compton", "kn"))
     return h
 
 

@@ -1,0 +1,107 @@
+"""Parity of the Waller-Hartree Compton model (Sec. 2.2.3, Eq. 2 with S(q)) on
+the GPU: tables and per-material C surfaces equal to the oracle's bit for
+bit, device sampling equal to the oracle's binary32 sampler and to Eq. 2,
+bit-exact counts against the binary32 oracle, dose within 3 sigma of the
+binary64 oracle, and the batched form equal to separate runs."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1109_3266_gb300 import inputs as I
+from test_gpu_parity import COUNT_KEYS, assert_counts_equal, dose_parity, small_cbct, small_head
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctd():
+    from paper_1109_3266_gb300 import build, ctd as binding
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(ctd):
+    c = ctd.ctd_create(device=0)
+    yield c
+    ctd.ctd_destroy(c)
+
+
+def wh(p):
+    return I.scaled(p, physics=dataclasses.replace(p.physics, compton="wh"))
+
+
+def test_wh_tables_and_surfaces_equal_oracle_bitwise(ctd, ctx, oracle):
+    p = wh(small_head(1000))
+    h = ctd.load_problem(ctx, p)
+    cum, mm, cs, rs = ctd.ctd_get_tables(ctx, h, compton="wh")
+    s = oracle.Setup(p, 32)
+    ocum, omm = s.tables()
+    ocs, ors = s.surfaces()
+    assert cs.shape == (len(p.phantom.materials), s.n_e, s.n_zeta)
+    assert np.array_equal(cum, ocum) and np.array_equal(mm, omm)
+    assert np.array_equal(cs, ocs) and np.array_equal(rs, ors)
+    # binding lowers the Compton column against Klein-Nishina
+    hk = ctd.load_problem(ctx, small_head(1000))
+    kn_cum = ctd.ctd_get_tables(ctx, hk)[0]
+    assert np.all((cum[:, :, 1] - cum[:, :, 0]) < (kn_cum[:, :, 1] - kn_cum[:, :, 0]))
+    ctd.ctd_destroy_phantom(ctx, hk)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+@pytest.mark.parametrize("mat,e", [(0, 10.0), (2, 60.0), (1, 30.5)])
+def test_wh_device_sampler_matches_oracle_and_eq2(ctd, ctx, oracle, mat, e):
+    from test_oracle_wh import _chi2_equal_prob, wh_cdf
+    p = wh(small_head(1000))
+    h = ctd.load_problem(ctx, p)
+    dev = ctd.ctd_sample_mu(ctx, h, "compton", mat, e, 91, 2_000_000)
+    ref = oracle.Setup(p, 32).sample_mu("compton", mat, e, 200_000, seed=91)
+    assert np.array_equal(dev[:200_000], ref)
+    assert _chi2_equal_prob(dev, wh_cdf(e, p.phantom.materials[mat].sq0)) > 1e-4
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+@pytest.mark.parametrize("make", [lambda: I.tiny_water(100_000), lambda: small_head(300_000),
+                                  lambda: small_cbct(300_000)])
+def test_wh_full_transport_matches_oracles(ctd, ctx, oracle, make):
+    p = wh(make())
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r32 = oracle.run(p, precision=32)
+    assert_counts_equal(st, r32.counts)
+    assert np.allclose(dose, r32.dose, rtol=1e-9, atol=1e-30)
+    r64 = oracle.run(p, precision=64)
+    frac, nmask = dose_parity(dose, sd, r64.dose, r64.std)
+    assert nmask > 50 and frac >= 0.99, (frac, nmask)
+    e64 = r64.counts["e_deposited"]
+    assert abs(st["e_deposited_kev"] - e64) <= 0.005 * e64
+    assert abs(st["e_deposited_kev"] + st["e_escaped_kev"] - st["e_emitted_kev"]) <= 1e-9 * st["e_emitted_kev"]
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_wh_primary_only_counts_bit_exact(ctd, ctx, oracle):
+    p = small_head(100_000)
+    p = I.scaled(p, physics=I.Physics(1, 150, mode="max_real", max_real=1, compton="wh"))
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r = oracle.run(p, precision=32)
+    assert_counts_equal(st, r.counts)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_wh_and_kn_requests_batched_together(ctd, ctx):
+    # request chains carry their own C surfaces: a mix of models equals separate runs
+    ps = [wh(small_head(80_000)), small_head(60_000, seed=5), wh(small_cbct(50_000))]
+    ref = []
+    for p in ps:
+        dose, sd, st, h = ctd.run_problem(ctx, p)
+        ref.append((dose, st))
+        ctd.ctd_destroy_phantom(ctx, h)
+    for shared in (0, 1):
+        c = ctd.ctd_create(device=0, shared_launch=shared)
+        hs = [ctd.load_problem(c, p) for p in ps]
+        ctd.ctd_run_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
+        for p, h, (dose, st) in zip(ps, hs, ref):
+            d2, _, st2 = ctd.ctd_get_dose_and_stddev(c, h, p.phantom.nvox)
+            assert all(st[k] == st2[k] for k in COUNT_KEYS)
+            assert np.allclose(d2, dose, rtol=1e-9, atol=0)
+        ctd.ctd_destroy(c)

@@ -41,7 +41,7 @@
 #define OR_MAX_TRIALS_WH (1u << 20) /* Waller-Hartree keeps about a(1-mu) of KN draws at low E */
 #define OR_MAX_STEPS 100000000u    /* Woodcock steps per history            */
 
-enum { OR_STREAM_TRANSPORT = 0, OR_STREAM_SOURCE = 1, OR_STREAM_EXACT = 2, OR_STREAM_SAMPLER = 3 };
+enum { OR_STREAM_TRANSPORT = 0, OR_STREAM_SOURCE = 1, OR_STREAM_EXACT = 2, OR_STREAM_SAMPLER = 3, OR_STREAM_MH = 4 };
 
 /* ===================================================================== */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.2): ten rounds */
@@ -361,6 +361,77 @@ void or_build_wh_surface(double sq0, int e_min, int n_e, int n_zeta, double *out
 }
 
 /* ===================================================================== */
+/* Fluence map (Sec. 2.2.4): the beamlet index I with probability f_I.    */
+/* Alias table: Walker's method built with Vose's two work lists.         */
+/* ===================================================================== */
+int or_alias_build(int n, const double *f, uint32_t *thr, int32_t *alias)
+{
+    if (n <= 0) return -1;
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(f[i] >= 0.0) || !isfinite(f[i])) return -1;
+        total += f[i];
+    }
+    if (!(total > 0.0) || !isfinite(total)) return -1;
+    double *p = (double *)malloc(sizeof(double) * (size_t)n);
+    int *small = (int *)malloc(sizeof(int) * (size_t)n);
+    int *large = (int *)malloc(sizeof(int) * (size_t)n);
+    int ns = 0, nl = 0;
+    /* scaled probabilities n f_i / total; columns below 1 borrow from columns above */
+    for (int i = 0; i < n; ++i) {
+        p[i] = (f[i] * (double)n) / total;
+        if (p[i] < 1.0) small[ns++] = i;
+        else large[nl++] = i;
+    }
+    while (ns > 0 && nl > 0) {
+        int l = small[--ns], g = large[--nl];
+        thr[l] = (uint32_t)(p[l] * 4294967296.0);
+        alias[l] = g;
+        p[g] = (p[g] + p[l]) - 1.0;
+        if (p[g] < 1.0) small[ns++] = g;
+        else large[nl++] = g;
+    }
+    /* what is left is 1 up to rounding */
+    while (nl > 0) { int g = large[--nl]; thr[g] = 0xffffffffu; alias[g] = g; }
+    while (ns > 0) { int l = small[--ns]; thr[l] = 0xffffffffu; alias[l] = l; }
+    free(p); free(small); free(large);
+    return 0;
+}
+
+static uint32_t or_alias_draw(int n_f, const uint32_t *thr, const int32_t *alias, uint32_t x, uint32_t y)
+{
+    uint32_t k = (uint32_t)(((uint64_t)x * (uint64_t)(uint32_t)n_f) >> 32);
+    return y < thr[k] ? k : (uint32_t)alias[k];
+}
+
+void or_alias_counts(int n_f, const uint32_t *thr, const int32_t *alias, uint64_t n, uint64_t seed,
+                     uint64_t *counts)
+{
+    for (int i = 0; i < n_f; ++i) counts[i] = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t b[4];
+        or_block(seed, i, 1, OR_STREAM_SOURCE, b);
+        counts[or_alias_draw(n_f, thr, alias, b[0], b[1])]++;
+    }
+}
+
+void or_mh_counts(int n_f, const double *f, int i0, uint64_t n, uint64_t seed, uint64_t *counts)
+{
+    for (int i = 0; i < n_f; ++i) counts[i] = 0;
+    int last = i0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t b[4];
+        or_block(seed, i, 0, OR_STREAM_MH, b);
+        /* 1. trial beamlet J uniform; 2. zeta uniform; 3. keep J if zeta < f_J / f_last */
+        int j = (int)(((uint64_t)b[0] * (uint64_t)(uint32_t)n_f) >> 32);
+        double zeta = or_uniform(b[1]);
+        int cur = zeta < f[j] / f[last] ? j : last;
+        counts[cur]++;
+        last = cur;
+    }
+}
+
+/* ===================================================================== */
 /* Set-up: tables, majorant, surfaces, batch and bin offsets.            */
 /* ===================================================================== */
 struct or_setup {
@@ -378,6 +449,9 @@ struct or_setup {
     double bx0, by0, bz0, bx1, by1, bz1, ix, iy, iz;
     float fbx0, fby0, fbz0, fbx1, fby1, fbz1, fix, fiy, fiz;
     double *cb64, *sb64; float *cb32, *sb32; /* projection angle cos/sin */
+    int fl_n;                      /* beamlets (0: no fluence map)                       */
+    uint32_t *fl_thr; int32_t *fl_alias;
+    double fl_du, fl_dv; float fl_fdu, fl_fdv;   /* beamlet size at the centre plane  */
 };
 
 static void or_setup_free(or_setup *s)
@@ -387,6 +461,7 @@ static void or_setup_free(or_setup *s)
     free(s->cs64); free(s->cs32); free(s->rs64); free(s->rs32);
     free(s->pref_big); free(s->pref_small);
     free(s->cb64); free(s->sb64); free(s->cb32); free(s->sb32);
+    free(s->fl_thr); free(s->fl_alias);
     free(s);
 }
 
@@ -485,6 +560,18 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
     s->fbx0 = (float)s->bx0; s->fby0 = (float)s->by0; s->fbz0 = (float)s->bz0;
     s->fbx1 = (float)s->bx1; s->fby1 = (float)s->by1; s->fbz1 = (float)s->bz1;
     s->fix = (float)s->ix; s->fiy = (float)s->iy; s->fiz = (float)s->iz;
+    /* fluence map: alias table over the beamlets */
+    if (p->fl_nu > 0) {
+        if (p->fl_nv <= 0 || !p->fl_f || (int64_t)p->fl_nu * p->fl_nv > (1 << 24)) { or_setup_free(s); return NULL; }
+        s->fl_n = p->fl_nu * p->fl_nv;
+        s->fl_thr = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)s->fl_n);
+        s->fl_alias = (int32_t *)malloc(sizeof(int32_t) * (size_t)s->fl_n);
+        if (or_alias_build(s->fl_n, p->fl_f, s->fl_thr, s->fl_alias) != 0) { or_setup_free(s); return NULL; }
+        s->fl_du = (p->u_hi - p->u_lo) / (double)p->fl_nu;
+        s->fl_dv = (p->v_hi - p->v_lo) / (double)p->fl_nv;
+        s->fl_fdu = (float)s->fl_du;
+        s->fl_fdv = (float)s->fl_dv;
+    }
     /* projection angles beta_k = arc0 + (arc1 - arc0) k / n_proj */
     int np = p->n_proj > 0 ? p->n_proj : 1;
     s->cb64 = (double *)malloc(sizeof(double) * np); s->sb64 = (double *)malloc(sizeof(double) * np);

@@ -63,6 +63,10 @@ typedef struct {
     int n_proj;                   /* discrete projections on the arc */
     double arc0, arc1;            /* arc start/end, radians */
     int continuous;               /* 1: angle uniform on [arc0, arc1) (Sec. 2.2.6) */
+    /* fluence map (Sec. 2.2.4): fl_nu x fl_nv beamlets tiling the field, u fastest,
+     * relative intensities fl_f (>= 0, sum > 0); fl_nu = 0: no map (uniform in solid angle) */
+    int fl_nu, fl_nv;
+    const double *fl_f;
     /* spectrum: bins [e_lo, e_hi] keV with relative weight w (Sec. 2.2.5) */
     int nbins;
     const double *e_lo, *e_hi, *w;
@@ -139,6 +143,20 @@ int or_sample_mu_f64(const or_setup *s, int kind, int material, double e_kev, in
                      uint64_t seed, uint64_t n, double *out);
 int or_sample_mu_f32(const or_setup *s, int kind, int material, double e_kev,
                      uint64_t seed, uint64_t n, double *out);
+
+/* Fluence map (Sec. 2.2.4).  Alias table of n intensities f (Walker's method in
+ * Vose's construction): beamlet I is drawn from a 32-bit word x and a second
+ * word y as k = floor(x n / 2^32), I = k if y < thr[k] else alias[k].
+ * Returns 0, or -1 if the intensities are unusable. */
+int or_alias_build(int n, const double *f, uint32_t *thr, int32_t *alias);
+/* Beamlet counts of n particles drawn from the alias table with the source's
+ * random numbers (particle i: Philox block (i, 1, stream 1) under seed). */
+void or_alias_counts(int n_f, const uint32_t *thr, const int32_t *alias, uint64_t n, uint64_t seed,
+                     uint64_t *counts);
+/* Beamlet counts of n particles from the paper's Metropolis-Hastings chain
+ * (Algorithm A1) started at beamlet i0: trial J uniform, kept if zeta < f_J /
+ * f_last (particle i: Philox block (i, 0, stream 4) under seed). */
+void or_mh_counts(int n_f, const double *f, int i0, uint64_t n, uint64_t seed, uint64_t *counts);
 
 /* the direction rotation on its own, for invariant checks */
 void or_rotate_f64(double *u, double mu, double t_phi);

@@ -44,6 +44,7 @@ class OrProblem(C.Structure):
         ("src_kind", C.c_int), ("sad", C.c_double),
         ("u_lo", C.c_double), ("u_hi", C.c_double), ("v_lo", C.c_double), ("v_hi", C.c_double),
         ("n_proj", C.c_int), ("arc0", C.c_double), ("arc1", C.c_double), ("continuous", C.c_int),
+        ("fl_nu", C.c_int), ("fl_nv", C.c_int), ("fl_f", C.POINTER(C.c_double)),
         ("nbins", C.c_int), ("e_lo", C.POINTER(C.c_double)), ("e_hi", C.POINTER(C.c_double)),
         ("w", C.POINTER(C.c_double)),
         ("e_min", C.c_int), ("e_max", C.c_int), ("n_zeta", C.c_int), ("majorant_scale", C.c_double),
@@ -94,6 +95,10 @@ def _declare(L):
     L.or_build_rayleigh_surface.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int, dp]
     L.or_sample_mu_f64.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64, dp]
     L.or_sample_mu_f32.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint64, dp]
+    L.or_alias_build.argtypes = [C.c_int, dp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]
+    L.or_alias_counts.argtypes = [C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_int32), C.c_uint64, C.c_uint64,
+                                  C.POINTER(C.c_uint64)]
+    L.or_mh_counts.argtypes = [C.c_int, dp, C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_uint64)]
     L.or_rotate_f64.argtypes = [dp, C.c_double, C.c_double]
     L.or_rotate_f32.argtypes = [C.POINTER(C.c_float), C.c_float, C.c_float]
 
@@ -180,6 +185,31 @@ def rotate(u, mu, t_phi, precision=64):
     return a
 
 
+def alias_table(f):
+    """Walker/Vose alias table of intensities f: (thresholds uint32, aliases int32)."""
+    f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+    thr = np.empty(f.size, dtype=np.uint32)
+    al = np.empty(f.size, dtype=np.int32)
+    if lib().or_alias_build(f.size, _ptr(f, C.c_double), _ptr(thr, C.c_uint32), _ptr(al, C.c_int32)) != 0:
+        raise ValueError("unusable intensities")
+    return thr, al
+
+
+def alias_counts(thr, al, n, seed):
+    out = np.zeros(thr.size, dtype=np.uint64)
+    lib().or_alias_counts(thr.size, _ptr(np.ascontiguousarray(thr), C.c_uint32),
+                          _ptr(np.ascontiguousarray(al), C.c_int32), n, seed, _ptr(out, C.c_uint64))
+    return out
+
+
+def mh_counts(f, n, seed, i0=0):
+    """Beamlet counts of the paper's Metropolis-Hastings chain (Algorithm A1)."""
+    f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+    out = np.zeros(f.size, dtype=np.uint64)
+    lib().or_mh_counts(f.size, _ptr(f, C.c_double), i0, n, seed, _ptr(out, C.c_uint64))
+    return out
+
+
 def kn_surface(e_min, n_e, n_zeta):
     out = np.empty((n_e, n_zeta), dtype=np.float64)
     lib().or_build_kn_surface(e_min, n_e, n_zeta, _ptr(out, C.c_double))
@@ -230,6 +260,11 @@ class Setup:
         p.sad = src.sad
         p.u_lo, p.u_hi, p.v_lo, p.v_hi = src.u_lo, src.u_hi, src.v_lo, src.v_hi
         p.n_proj, p.arc0, p.arc1, p.continuous = src.n_proj, src.arc0, src.arc1, int(src.continuous)
+        fl = getattr(src, "fluence", None)
+        if fl is not None:
+            self._fl = np.ascontiguousarray(fl, dtype=np.float64)
+            p.fl_nv, p.fl_nu = self._fl.shape
+            p.fl_f = _ptr(self._fl, C.c_double)
         p.nbins = len(self._w)
         p.e_lo, p.e_hi, p.w = _ptr(self._elo, C.c_double), _ptr(self._ehi, C.c_double), _ptr(self._w, C.c_double)
         p.e_min, p.e_max, p.n_zeta = phy.e_min, phy.e_max, phy.n_zeta

@@ -93,7 +93,9 @@ class Source:
     kind 'arc': source at sad*(sin b, cos b, 0) aimed at the origin, b on
     [arc0, arc1) at n_proj discrete angles (or uniform if continuous).
     The field [u_lo, u_hi] x [v_lo, v_hi] is given at the centre plane (cm);
-    u is lateral, v is along z for 'arc' and along y for 'static'."""
+    u is lateral, v is along z for 'arc' and along y for 'static'.
+    fluence: optional [n_v][n_u] relative beamlet intensities tiling the field
+    (Sec. 2.2.4); without it directions are uniform in solid angle."""
     kind: str
     sad: float
     u_lo: float
@@ -104,6 +106,7 @@ class Source:
     arc0: float = 0.0
     arc1: float = 2.0 * math.pi
     continuous: bool = False
+    fluence: Optional[np.ndarray] = None
 
 
 @dataclass
@@ -237,6 +240,21 @@ def pencil_source(sad: float = 100.0) -> Source:
 
 def arc_source(sad, u_lo, u_hi, v_lo, v_hi, n_proj=360, arc0=0.0, arc1=2.0 * math.pi, continuous=False):
     return Source("arc", sad, u_lo, u_hi, v_lo, v_hi, n_proj, arc0, arc1, continuous)
+
+
+def bowtie_fluence(n_u: int = 128, n_v: int = 32, seed: int = 0, t_centre: float = 0.1, t_edge: float = 2.5,
+                   mu_al: float = 0.75, noise: float = 0.02) -> np.ndarray:
+    """Synthetic air-scan fluence of a full-fan bowtie (stand-in for Fig. 5(a)):
+    aluminium thickness growing as the square of the lateral offset, from
+    t_centre at the centre to t_edge at the field edge (cm), attenuation
+    exp(-mu_al t) with mu_al about aluminium's at 60 keV, times seeded
+    multiplicative Gaussian noise of relative size `noise`.  [n_v][n_u], > 0."""
+    u = (np.arange(n_u) + 0.5) / n_u * 2.0 - 1.0
+    t = t_centre + (t_edge - t_centre) * u * u
+    f = np.tile(np.exp(-mu_al * t), (n_v, 1))
+    rng = np.random.default_rng(seed)
+    f = f * np.clip(1.0 + noise * rng.standard_normal(f.shape), 0.5, 1.5)
+    return np.ascontiguousarray(f, dtype=np.float64)
 
 
 # --------------------------------------------------------------------------

@@ -60,7 +60,8 @@ def workload(name, compton="kn"):
     import dataclasses
 
     from paper_1109_3266_gb300 import inputs as I
-    makers = {"cbct_water": I.cbct_water, "head": I.head, "tiny_water": I.tiny_water}
+    makers = {"cbct_water": I.cbct_water, "head": I.head, "tiny_water": I.tiny_water,
+              "cbct_water_bowtie": lambda: dataclasses.replace(I.cbct_water(bowtie=True), name="cbct_water_bowtie")}
     if name not in makers:
         raise SystemExit(f"unknown workload {name}")
     p = makers[name]()
@@ -368,7 +369,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": p.name, "voxels": [p.phantom.nx, p.phantom.ny, p.phantom.nz],
                        "voxel_cm": p.phantom.dx, "histories_per_step": p.n_hist, "batches": p.n_batches,
-                       "kvp": 120 if p.name == "cbct_water" else None, "parallelism": f"replicas{world}",
+                       "kvp": 120 if p.name.startswith("cbct_water") else 100 if p.name == "head" else None,
+                       "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (256 MB write outside timed events)",
                        "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk,
                        "flight_cap": args.flight_cap, "compton": args.compton},

@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 3
+#define CTD_ABI_VERSION 4
 
 typedef enum {
     CTD_OK = 0,
@@ -155,6 +155,22 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
 int ctd_destroy_phantom(ctd_ctx *ctx, ctd_phantom ph);
 int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys);
 int ctd_set_source(ctd_ctx *ctx, ctd_phantom ph, const ctd_source *src);
+
+/* Fluence map (Sec. 2.2.4): n_u x n_v beamlets tiling the source's field
+ * rectangle at the centre plane (u fastest; f[iv * n_u + iu]) with relative
+ * intensities f >= 0 of positive sum.  A source photon then comes from beamlet I
+ * with probability f_I / sum f, at a point uniform inside it, instead of
+ * uniformly in solid angle over the field.  The beamlet is drawn from a Walker
+ * alias table built on the host in binary64 (Vose's construction; thresholds
+ * floor(p 2^32) as 32-bit integers): Philox block (h, 1, stream 1) gives the
+ * column k = floor(x n / 2^32), the beamlet k if y < thr[k] else alias[k], and
+ * the offsets z, w inside it.  n_u = 0 removes the map.  At most 2^24 beamlets
+ * and 65535 per row.
+ * The host array is copied. */
+int ctd_set_fluence(ctd_ctx *ctx, ctd_phantom ph, int n_u, int n_v, const double *f);
+/* The alias table of the phantom's fluence map: *n beamlets, thr[n], alias[n]
+ * (either pointer may be NULL; *n = 0 without a map). */
+int ctd_get_fluence_table(ctd_ctx *ctx, ctd_phantom ph, int *n, uint32_t *thr, int32_t *alias);
 
 /* Spectrum (Sec. 2.2.5): nbins intervals [e_lo[j], e_hi[j]] keV (e_lo == e_hi
  * is a line) with weights w[j] >= 0, sum > 0, inside [e_min, e_max] of the

@@ -105,6 +105,12 @@ struct Phantom {
     ctd_run_stats stats{};
     bool have_result = false;
     int64_t busy_req = 0;      // served request using this phantom, 0 if none
+    // fluence map (Sec. 2.2.4): alias table over fl_nu x fl_nv beamlets (fl_nu = 0: none)
+    int fl_nu = 0, fl_nv = 0;
+    std::vector<uint32_t> h_thr;
+    std::vector<int32_t> h_alias;
+    DevBuf<uint32_t> fl_thr;
+    DevBuf<int32_t> fl_alias;
 };
 
 struct Staged {
@@ -314,6 +320,15 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     q.rsurf = P.rs.p;
     q.csurf = P.cs.p;
     q.cs_stride = P.phys.compton_model == CTD_COMPTON_WH ? P.n_e * P.phys.n_zeta : 0;
+    if (P.fl_nu > 0) {
+        q.fl_thr = P.fl_thr.p;
+        q.fl_alias = P.fl_alias.p;
+        q.fl_n = P.fl_nu * P.fl_nv;
+        q.fl_nu = P.fl_nu;
+        q.fl_magic = ((1ull << 40) / static_cast<uint64_t>(P.fl_nu)) + 1;
+        q.fl_du = static_cast<float>((P.src.u_hi_cm - P.src.u_lo_cm) / static_cast<double>(P.fl_nu));
+        q.fl_dv = static_cast<float>((P.src.v_hi_cm - P.src.v_lo_cm) / static_cast<double>(P.fl_nv));
+    }
     q.n_mat = static_cast<int>(P.mats.size());
     q.work = P.work.p;
     q.nbins = static_cast<int>(P.w.size());
@@ -728,6 +743,48 @@ int ctd_set_source(ctd_ctx *ctx, ctd_phantom ph, const ctd_source *src)
     P->src = *src;
     P->src.n_proj = np;
     P->has_src = true;
+    return CTD_OK;
+}
+
+int ctd_set_fluence(ctd_ctx *ctx, ctd_phantom ph, int n_u, int n_v, const double *f)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if ((rc = busy(P))) return rc;
+    if (n_u == 0) {
+        P->fl_nu = P->fl_nv = 0;
+        return CTD_OK;
+    }
+    if (n_u < 0 || n_u > 65535 || n_v <= 0 || static_cast<int64_t>(n_u) * n_v > (1 << 24) || !f)
+        return fail(CTD_EINVAL, "fluence map: n_u <= 65535, 1 <= n_u * n_v <= 2^24 beamlets and a host array");
+    const int n = n_u * n_v;
+    std::vector<uint32_t> thr(n);
+    std::vector<int32_t> al(n);
+    if (!ctd::alias_build(n, f, thr.data(), al.data()))
+        return fail(CTD_EINVAL, "fluence map needs finite intensities >= 0 with a positive sum");
+    if ((rc = P->fl_thr.ensure(n)) || (rc = P->fl_alias.ensure(n))) return rc;
+    CK(cudaMemcpyAsync(P->fl_thr.p, thr.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P->fl_alias.p, al.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    P->h_thr.swap(thr);
+    P->h_alias.swap(al);
+    P->fl_nu = n_u;
+    P->fl_nv = n_v;
+    return CTD_OK;
+}
+
+int ctd_get_fluence_table(ctd_ctx *ctx, ctd_phantom ph, int *n, uint32_t *thr, int32_t *alias)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    const int m = P->fl_nu * P->fl_nv;
+    if (n) *n = m;
+    if (thr) std::copy(P->h_thr.begin(), P->h_thr.begin() + m, thr);
+    if (alias) std::copy(P->h_alias.begin(), P->h_alias.begin() + m, alias);
     return CTD_OK;
 }
 

@@ -41,6 +41,10 @@ void build_tables(const std::vector<ctd_material> &mats, const std::vector<doubl
 // Inverse-cdf surface rows for node energies e_min..e_min+n_e-1: kind 0 Klein-Nishina,
 // 1 Rayleigh of form-factor width q0, 2 Waller-Hartree of scattering-function width q0.
 void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out);
+// Walker alias table of n intensities (Vose's construction): thr[k] = floor(p 2^32)
+// of the kept share of column k, alias[k] the beamlet it borrows from; false if
+// the intensities are unusable.
+bool alias_build(int n, const double *f, uint32_t *thr, int32_t *alias);
 // Largest-remainder allocation; false if the weights are unusable.
 bool allocate(uint64_t n, const std::vector<double> &w, std::vector<uint64_t> &out);
 
@@ -90,6 +94,11 @@ struct alignas(16) RequestDesc {
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
     int mode, max_real;
     int cs_stride;               // 0 (one Klein-Nishina surface) or n_e * n_zeta (Waller-Hartree)
+    const uint32_t *fl_thr;      // [fl_n] fluence-map alias thresholds (fl_n = 0: no map)
+    const int32_t *fl_alias;     // [fl_n]
+    int fl_n, fl_nu;
+    float fl_du, fl_dv;          // beamlet size at the centre plane, cm
+    uint64_t fl_magic;           // floor(2^40 / fl_nu) + 1: I / fl_nu = (I fl_magic) >> 40 for I < 2^24, fl_nu < 2^16
     uint32_t rk[20];             // Philox round keys of seed: (lo, hi) + r (Weyl constants), r = 0..9
 };
 

@@ -172,6 +172,52 @@ void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *
     }
 }
 
+bool alias_build(int n, const double *f, uint32_t *thr, int32_t *alias)
+{
+    if (n <= 0) return false;
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(f[i] >= 0.0) || !std::isfinite(f[i])) return false;
+        total += f[i];
+    }
+    if (!(total > 0.0) || !std::isfinite(total)) return false;
+    // n f_i / total: columns under 1 are filled up from columns over 1, taken
+    // last in, first out from two work lists
+    std::vector<double> p(n);
+    std::vector<int> under, over;
+    under.reserve(n);
+    over.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        p[i] = (f[i] * static_cast<double>(n)) / total;
+        if (p[i] < 1.0) under.push_back(i);
+        else over.push_back(i);
+    }
+    while (!under.empty() && !over.empty()) {
+        const int l = under.back(), g = over.back();
+        under.pop_back();
+        over.pop_back();
+        thr[l] = static_cast<uint32_t>(p[l] * 4294967296.0);
+        alias[l] = g;
+        p[g] = (p[g] + p[l]) - 1.0;
+        if (p[g] < 1.0) under.push_back(g);
+        else over.push_back(g);
+    }
+    // columns left over hold 1 up to rounding
+    while (!over.empty()) {
+        const int g = over.back();
+        over.pop_back();
+        thr[g] = 0xffffffffu;
+        alias[g] = g;
+    }
+    while (!under.empty()) {
+        const int l = under.back();
+        under.pop_back();
+        thr[l] = 0xffffffffu;
+        alias[l] = l;
+    }
+    return true;
+}
+
 bool allocate(uint64_t n, const std::vector<double> &w, std::vector<uint64_t> &out)
 {
     const int nb = static_cast<int>(w.size());

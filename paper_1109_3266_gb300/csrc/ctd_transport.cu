@@ -105,7 +105,7 @@ __device__ __forceinline__ int bin_search(const RequestDesc &q, uint64_t local)
 // Source photon of local history `local` (global index h) of request q;
 // `bin` is a lower bound of its 1 keV interval.  Returns true if the photon
 // enters the phantom.
-template <bool kKeys>
+template <bool kKeys, bool kFluence>
 __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_t local, int bin, Photon &ph,
                                        LaneCounts &cnt)
 {
@@ -125,11 +125,24 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
             sb = __ldg(&q.sb[k]);
         }
     }
-    // uniform in solid angle over the field: uniform point, accepted with cos^3
+    // uniform in solid angle over the field: uniform point, accepted with cos^3;
+    // with a fluence map (Sec. 2.2.4): beamlet from the alias table, point uniform in it
     const float D = q.D, D2 = q.D2;
     bool accepted = false;
     float uu = 0.0f, vv = 0.0f, qq = 0.0f;
-    for (uint32_t t = 1; t <= kMaxTrials; ++t) {
+    if (kFluence && q.fl_n > 0) {
+        const U4 b = draw<kKeys>(q, h, 1, kStreamSource);
+        const uint32_t k =
+            static_cast<uint32_t>((static_cast<uint64_t>(b.x) * static_cast<uint64_t>(static_cast<uint32_t>(q.fl_n))) >> 32);
+        const uint32_t beam = b.y < __ldg(&q.fl_thr[k]) ? k : static_cast<uint32_t>(__ldg(&q.fl_alias[k]));
+        const uint32_t iv = static_cast<uint32_t>((static_cast<uint64_t>(beam) * q.fl_magic) >> 40);
+        const uint32_t iu = beam - iv * static_cast<uint32_t>(q.fl_nu);
+        uu = q.ulo + q.fl_du * (static_cast<float>(iu) + uni(b.z));
+        vv = q.vlo + q.fl_dv * (static_cast<float>(iv) + uni(b.w));
+        qq = (D2 + uu * uu) + vv * vv;
+        accepted = true;
+    }
+    for (uint32_t t = 1; t <= kMaxTrials && !accepted; ++t) {
         const U4 b = draw<kKeys>(q, h, t, kStreamSource);
         uu = q.ulo + q.uw * uni(b.x);
         vv = q.vlo + q.vw * uni(b.y);
@@ -318,7 +331,7 @@ constexpr size_t kWarpBytes = kQueueBytes + sizeof(WarpPool);
 
 // All histories [q.local_begin, q.local_end) of one request, claimed by warps
 // from q.work in runs of `chunk`.  Returns when the warp has no photon left.
-template <bool kKeys>
+template <bool kKeys, bool kFluence>
 __device__ __forceinline__ void run_request(const LaunchParams &P, const RequestDesc &q, const float4 *s_tab,
                                             const float *s_mm, const Queue &Q, int lane, LaneCounts &cnt)
 {
@@ -358,7 +371,7 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
                 bool ok = false;
                 if (lane < take) {
                     const uint64_t local = pool_next + lane;
-                    ok = source<kKeys>(q, q.h_base + local, local, pool_bin, np, cnt);
+                    ok = source<kKeys, kFluence>(q, q.h_base + local, local, pool_bin, np, cnt);
                 }
                 const unsigned okm = __ballot_sync(kFull, ok);
                 if (ok) {
@@ -435,7 +448,10 @@ __device__ __forceinline__ void load_tables(const RequestDesc &q, int n_e, float
 // of its descriptor, attenuation table and majorant in shared memory, and when
 // that request has no history left to claim the block moves on to the next
 // one, so that one request's tail overlaps the next one's start.
-template <int kMaxThreads, int kMinBlocks, bool kMulti>
+// kForm: 0 one request without a fluence map, 1 one request with a fluence map
+// (the map's source path is compiled only into this form, so that it does not
+// cost the open-field form registers), 2 several requests (maps checked per request)
+template <int kMaxThreads, int kMinBlocks, int kForm>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(const LaunchParams P)
 {
     extern __shared__ float4 smem[];
@@ -453,10 +469,11 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
     LaneCounts cnt;
     cnt.clear();
 
+    constexpr bool kMulti = kForm == 2;
     if (!kMulti) {
         load_tables(P.one, n_e, s_tab, s_mm);
         __syncthreads();
-        run_request<true>(P, P.one, s_tab, s_mm, Q, lane, cnt);
+        run_request<true, kForm == 1>(P, P.one, s_tab, s_mm, Q, lane, cnt);
         flush_warp(P.one.counts, cnt, lane);
         return;
     }
@@ -489,7 +506,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
         __syncthreads();
         load_tables(q, n_e, s_tab, s_mm);
         __syncthreads();
-        run_request<false>(P, q, s_tab, s_mm, Q, lane, cnt);
+        run_request<false, true>(P, q, s_tab, s_mm, Q, lane, cnt);
         flush_warp(q.counts, cnt, lane);
         __syncthreads();
         // the same request is exhausted now; continue the walk from it
@@ -525,10 +542,10 @@ __global__ void eval_math_kernel(int fn, const float *x, float *out, size_t n)
     }
 }
 
-template <int kMaxThreads, int kMinBlocks, bool kMulti>
+template <int kMaxThreads, int kMinBlocks, int kForm>
 int launch_t(const LaunchParams &p, int grid, int block, size_t smem, cudaStream_t stream)
 {
-    auto *k = transport_kernel<kMaxThreads, kMinBlocks, kMulti>;
+    auto *k = transport_kernel<kMaxThreads, kMinBlocks, kForm>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
             return CTD_ECUDA;
@@ -537,13 +554,13 @@ int launch_t(const LaunchParams &p, int grid, int block, size_t smem, cudaStream
     return cudaGetLastError() == cudaSuccess ? CTD_OK : CTD_ECUDA;
 }
 
-template <bool kMulti>
+template <int kForm>
 int launch_m(const LaunchParams &p, int grid, int block, int threads_per_sm, size_t smem, cudaStream_t s)
 {
     // the register budget follows the residency asked for (65536 registers per SM)
-    if (block <= 128 && threads_per_sm >= 896) return launch_t<128, 7, kMulti>(p, grid, block, smem, s);
-    if (threads_per_sm >= 1024) return launch_t<256, 4, kMulti>(p, grid, block, smem, s);
-    return launch_t<256, 3, kMulti>(p, grid, block, smem, s);
+    if (block <= 128 && threads_per_sm >= 896) return launch_t<128, 7, kForm>(p, grid, block, smem, s);
+    if (threads_per_sm >= 1024) return launch_t<256, 4, kForm>(p, grid, block, smem, s);
+    return launch_t<256, 3, kForm>(p, grid, block, smem, s);
 }
 
 }  // namespace
@@ -568,8 +585,9 @@ int launch_transport(const LaunchParams &p, int grid, int block, int threads_per
         return CTD_EINVAL;
     }
     const size_t smem = transport_smem_bytes(p, block);
-    return p.n_req > 0 ? launch_m<true>(p, grid, block, threads_per_sm, smem, s)
-                       : launch_m<false>(p, grid, block, threads_per_sm, smem, s);
+    if (p.n_req > 0) return launch_m<2>(p, grid, block, threads_per_sm, smem, s);
+    return p.one.fl_n > 0 ? launch_m<1>(p, grid, block, threads_per_sm, smem, s)
+                          : launch_m<0>(p, grid, block, threads_per_sm, smem, s);
 }
 
 int launch_sample_mu(const float *surf, int n_zeta, int n_e, int e_min, float e, uint64_t seed, uint64_t n,

@@ -125,6 +125,9 @@ def lib():
         L.ctd_cancel.argtypes = [P, C.c_int64]
         L.ctd_autotune.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.POINTER(ctd_tune_result)]
         L.ctd_probe_memory.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, dp]
+        L.ctd_set_fluence.argtypes = [P, C.c_int32, C.c_int, C.c_int, dp]
+        L.ctd_get_fluence_table.argtypes = [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_uint32),
+                                            C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -321,11 +324,35 @@ def load_problem(ctx, problem, physics=True):
     ctd_set_source(ctx, h, s.kind, s.sad, s.u_lo, s.u_hi, s.v_lo, s.v_hi, s.n_proj, s.arc0, s.arc1, s.continuous)
     sp = problem.spectrum
     ctd_set_spectrum(ctx, h, sp.e_lo, sp.e_hi, sp.w)
+    if getattr(s, "fluence", None) is not None:
+        ctd_set_fluence(ctx, h, s.fluence)
     if physics:
         p = problem.physics
         ctd_set_physics(ctx, h, p.e_min, p.e_max, p.n_zeta, p.majorant_scale, p.mode, p.max_real,
                         getattr(p, "compton", "kn"))
     return h
+
+
+def ctd_set_fluence(ctx, ph, f):
+    """Fluence map f[n_v][n_u] over the source's field (None removes it)."""
+    if f is None:
+        _check(lib().ctd_set_fluence(ctx, ph, 0, 0, None))
+        return
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    if f.ndim != 2:
+        raise CtdError(1, "fluence map must be [n_v][n_u]")
+    _check(lib().ctd_set_fluence(ctx, ph, f.shape[1], f.shape[0], _dp(f)))
+
+
+def ctd_get_fluence_table(ctx, ph):
+    """The fluence map's alias table: (thresholds uint32, aliases int32)."""
+    n = C.c_int()
+    _check(lib().ctd_get_fluence_table(ctx, ph, C.byref(n), None, None))
+    thr = np.empty(n.value, dtype=np.uint32)
+    al = np.empty(n.value, dtype=np.int32)
+    _check(lib().ctd_get_fluence_table(ctx, ph, None, thr.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                       al.ctypes.data_as(C.POINTER(C.c_int32))))
+    return thr, al
 
 
 def run_problem(ctx, problem, handle=None):

@@ -269,12 +269,15 @@ def tiny_water(n_hist: int = 100_000, n_batches: int = 10, seed: int = 1) -> Pro
 
 
 def cbct_water(n_hist: int = 1_000_000_000, n_batches: int = 10, seed: int = 2,
-               shape=(256, 256, 128), d: float = 0.2) -> Problem:
+               shape=(256, 256, 128), d: float = 0.2, bowtie: bool = False) -> Problem:
     """Water box 256x256x128 x 0.2 cm, 120 kVp Kramers + 2.5 mm Al, full rotation of
-    360 projections at SAD 100 cm, 20 x 20 cm field at the centre."""
+    360 projections at SAD 100 cm, 20 x 20 cm field at the centre; with bowtie, the
+    field carries a 128 x 32 full-fan bowtie fluence map (Sec. 2.2.4)."""
     nx, ny, nz = shape
     ph = uniform_box(nx, ny, nz, d, WATER)
     src = arc_source(100.0, -10.0, 10.0, -10.0, 10.0, n_proj=360)
+    if bowtie:
+        src = replace(src, fluence=bowtie_fluence(128, 32, seed=seed))
     return Problem("cbct_water", ph, src, spectrum_kramers(120, 2.5), Physics(e_min=1, e_max=150),
                    n_hist, n_batches, seed)
 

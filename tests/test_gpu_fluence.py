@@ -1,0 +1,96 @@
+"""Parity of the fluence-map source (Sec. 2.2.4) on the GPU: the alias table
+equals the oracle's bit for bit, histories through a bowtie-modulated field
+give the binary32 oracle's counts exactly and the binary64 oracle's dose
+within 3 sigma, the thin-absorber picture of the map is reproduced, and a
+request with a map batches with others."""
+import numpy as np
+import pytest
+
+from paper_1109_3266_gb300 import inputs as I
+from test_gpu_parity import COUNT_KEYS, assert_counts_equal, dose_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctd():
+    from paper_1109_3266_gb300 import build, ctd as binding
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(ctd):
+    c = ctd.ctd_create(device=0)
+    yield c
+    ctd.ctd_destroy(c)
+
+
+def bowtie_cbct(n_hist, seed=2):
+    return I.cbct_water(n_hist=n_hist, seed=seed, shape=(64, 64, 32), d=0.8, bowtie=True)
+
+
+def test_alias_table_equals_oracle_bitwise(ctd, ctx, oracle):
+    p = bowtie_cbct(1000)
+    h = ctd.load_problem(ctx, p)
+    thr, al = ctd.ctd_get_fluence_table(ctx, h)
+    othr, oal = oracle.alias_table(p.source.fluence)
+    assert np.array_equal(thr, othr) and np.array_equal(al, oal)
+    ctd.ctd_set_fluence(ctx, h, None)
+    assert ctd.ctd_get_fluence_table(ctx, h)[0].size == 0
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_set_fluence(ctx, h, np.zeros((2, 3)))
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_set_fluence(ctx, h, np.array([[1.0, -1.0]]))
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+@pytest.mark.parametrize("mode", ["full", "primary"])
+def test_bowtie_transport_matches_oracles(ctd, ctx, oracle, mode):
+    p = bowtie_cbct(300_000)
+    if mode == "primary":
+        p = I.scaled(p, physics=I.Physics(1, 150, mode="max_real", max_real=1))
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r32 = oracle.run(p, precision=32)
+    assert_counts_equal(st, r32.counts)
+    assert np.allclose(dose, r32.dose, rtol=1e-9, atol=1e-30)
+    if mode == "full":
+        r64 = oracle.run(p, precision=64)
+        frac, nmask = dose_parity(dose, sd, r64.dose, r64.std)
+        assert nmask > 50 and frac >= 0.99, (frac, nmask)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_thin_absorber_picture_bit_exact(ctd, ctx, oracle):
+    nu, nv, sub = 12, 6, 4
+    f = I.bowtie_fluence(nu, nv, seed=6)
+    absorber = I.Material("absorber", 0.4, 150.0, 60.0, 1.0, 5000.0)
+    ph = I.uniform_box(nu * sub, nv * sub, 1, 1.0, absorber, density=5000.0)
+    ph = I.Phantom(ph.nx, ph.ny, ph.nz, 12.0 / (nu * sub), 4.8 / (nv * sub), 1e-4, ph.mat, ph.rho, ph.materials)
+    src = I.Source("static", 50.0, -6.0, 6.0, -2.4, 2.4, fluence=f)
+    p = I.Problem("absorber", ph, src, I.spectrum_line(20.0),
+                  I.Physics(e_min=10, e_max=150, mode="max_real", max_real=1), 200_000, 10, 8)
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r32 = oracle.run(p, precision=32)
+    assert_counts_equal(st, r32.counts)
+    assert np.allclose(ctd.ctd_get_edep(ctx, h, ph.nvox), r32.edep, rtol=1e-12, atol=1e-9)
+    ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_bowtie_request_batches_with_others(ctd, ctx):
+    ps = [bowtie_cbct(60_000), I.cbct_water(40_000, seed=5, shape=(48, 48, 24), d=0.8),
+          I.head(50_000, seed=6, shape=(40, 40, 24), d=0.6)]
+    ref = []
+    for p in ps:
+        dose, sd, st, h = ctd.run_problem(ctx, p)
+        ref.append((dose, st))
+        ctd.ctd_destroy_phantom(ctx, h)
+    for shared in (0, 1):
+        c = ctd.ctd_create(device=0, shared_launch=shared)
+        hs = [ctd.load_problem(c, p) for p in ps]
+        ctd.ctd_run_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
+        for p, h, (dose, st) in zip(ps, hs, ref):
+            d2, _, st2 = ctd.ctd_get_dose_and_stddev(c, h, p.phantom.nvox)
+            assert all(st[k] == st2[k] for k in COUNT_KEYS)
+            assert np.allclose(d2, dose, rtol=1e-9, atol=0)
+        ctd.ctd_destroy(c)

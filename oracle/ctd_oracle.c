@@ -449,6 +449,8 @@ struct or_setup {
     double bx0, by0, bz0, bx1, by1, bz1, ix, iy, iz;
     float fbx0, fby0, fbz0, fbx1, fby1, fbz1, fix, fiy, fiz;
     double *cb64, *sb64; float *cb32, *sb32; /* projection angle cos/sin */
+    double *zb64; float *zb32;     /* projection source height (helical trajectory)       */
+    float fz0, fdz;                /* z0 and z1 - z0 in binary32                         */
     int fl_n;                      /* beamlets (0: no fluence map)                       */
     uint32_t *fl_thr; int32_t *fl_alias;
     double fl_du, fl_dv; float fl_fdu, fl_fdv;   /* beamlet size at the centre plane  */
@@ -460,7 +462,7 @@ static void or_setup_free(or_setup *s)
     free(s->tab64); free(s->tab32); free(s->mm64); free(s->mm32);
     free(s->cs64); free(s->cs32); free(s->rs64); free(s->rs32);
     free(s->pref_big); free(s->pref_small);
-    free(s->cb64); free(s->sb64); free(s->cb32); free(s->sb32);
+    free(s->cb64); free(s->sb64); free(s->cb32); free(s->sb32); free(s->zb64); free(s->zb32);
     free(s->fl_thr); free(s->fl_alias);
     free(s);
 }
@@ -576,11 +578,17 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
     int np = p->n_proj > 0 ? p->n_proj : 1;
     s->cb64 = (double *)malloc(sizeof(double) * np); s->sb64 = (double *)malloc(sizeof(double) * np);
     s->cb32 = (float *)malloc(sizeof(float) * np); s->sb32 = (float *)malloc(sizeof(float) * np);
+    s->zb64 = (double *)malloc(sizeof(double) * np); s->zb32 = (float *)malloc(sizeof(float) * np);
     for (int k = 0; k < np; ++k) {
         double b = p->arc0 + (p->arc1 - p->arc0) * (double)k / (double)np;
         s->cb64[k] = cos(b); s->sb64[k] = sin(b);
         s->cb32[k] = (float)s->cb64[k]; s->sb32[k] = (float)s->sb64[k];
+        /* helical: the height moves with the angle, z_k = z0 + (z1 - z0) k / n_proj */
+        s->zb64[k] = p->z0 + (p->z1 - p->z0) * (double)k / (double)np;
+        s->zb32[k] = (float)s->zb64[k];
     }
+    s->fz0 = (float)p->z0;
+    s->fdz = (float)(p->z1 - p->z0);
     return s;
 }
 

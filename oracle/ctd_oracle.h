@@ -63,6 +63,8 @@ typedef struct {
     int n_proj;                   /* discrete projections on the arc */
     double arc0, arc1;            /* arc start/end, radians */
     int continuous;               /* 1: angle uniform on [arc0, arc1) (Sec. 2.2.6) */
+    double z0, z1;                /* arc source height at arc0 and at arc1, linear in the
+                                     angle (helical trajectory; 0, 0: circular), cm      */
     /* fluence map (Sec. 2.2.4): fl_nu x fl_nv beamlets tiling the field, u fastest,
      * relative intensities fl_f (>= 0, sum > 0); fl_nu = 0: no map (uniform in solid angle) */
     int fl_nu, fl_nv;

@@ -44,6 +44,7 @@ class OrProblem(C.Structure):
         ("src_kind", C.c_int), ("sad", C.c_double),
         ("u_lo", C.c_double), ("u_hi", C.c_double), ("v_lo", C.c_double), ("v_hi", C.c_double),
         ("n_proj", C.c_int), ("arc0", C.c_double), ("arc1", C.c_double), ("continuous", C.c_int),
+        ("z0", C.c_double), ("z1", C.c_double),
         ("fl_nu", C.c_int), ("fl_nv", C.c_int), ("fl_f", C.POINTER(C.c_double)),
         ("nbins", C.c_int), ("e_lo", C.POINTER(C.c_double)), ("e_hi", C.POINTER(C.c_double)),
         ("w", C.POINTER(C.c_double)),
@@ -260,6 +261,7 @@ class Setup:
         p.sad = src.sad
         p.u_lo, p.u_hi, p.v_lo, p.v_hi = src.u_lo, src.u_hi, src.v_lo, src.v_hi
         p.n_proj, p.arc0, p.arc1, p.continuous = src.n_proj, src.arc0, src.arc1, int(src.continuous)
+        p.z0, p.z1 = getattr(src, "z0", 0.0), getattr(src, "z1", 0.0)
         fl = getattr(src, "fluence", None)
         if fl is not None:
             self._fl = np.ascontiguousarray(fl, dtype=np.float64)

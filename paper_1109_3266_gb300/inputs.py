@@ -107,6 +107,8 @@ class Source:
     arc1: float = 2.0 * math.pi
     continuous: bool = False
     fluence: Optional[np.ndarray] = None
+    z0: float = 0.0             # 'arc' source height at arc0 and arc1, linear in the angle
+    z1: float = 0.0             # (helical trajectory; both 0 for a circle)
 
 
 @dataclass
@@ -238,8 +240,15 @@ def pencil_source(sad: float = 100.0) -> Source:
     return Source("static", sad, 0.0, 0.0, 0.0, 0.0)
 
 
-def arc_source(sad, u_lo, u_hi, v_lo, v_hi, n_proj=360, arc0=0.0, arc1=2.0 * math.pi, continuous=False):
-    return Source("arc", sad, u_lo, u_hi, v_lo, v_hi, n_proj, arc0, arc1, continuous)
+def arc_source(sad, u_lo, u_hi, v_lo, v_hi, n_proj=360, arc0=0.0, arc1=2.0 * math.pi, continuous=False, z0=0.0,
+               z1=0.0):
+    return Source("arc", sad, u_lo, u_hi, v_lo, v_hi, n_proj, arc0, arc1, continuous, z0=z0, z1=z1)
+
+
+def helical_source(sad, u_lo, u_hi, v_lo, v_hi, turns, z0, z1, n_proj_per_turn=360, continuous=False):
+    """Helical CT: `turns` rotations while the source height goes from z0 to z1."""
+    return arc_source(sad, u_lo, u_hi, v_lo, v_hi, int(round(turns * n_proj_per_turn)), 0.0, 2.0 * math.pi * turns,
+                      continuous, z0, z1)
 
 
 def bowtie_fluence(n_u: int = 128, n_v: int = 32, seed: int = 0, t_centre: float = 0.1, t_edge: float = 2.5,

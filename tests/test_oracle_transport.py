@@ -329,3 +329,39 @@ def test_arc_projections_aim_at_the_centre(oracle, precision):
     on = ref > 0
     assert np.all(r.edep[~on] == 0)
     assert np.all(np.abs(mc[on] - ref[on]) < 4.5 * se[on]), (mc[on], ref[on], se[on])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("continuous", [False, True])
+def test_helical_trajectory_heights(oracle, precision, continuous):
+    # pencil beams on a helix from z = -3 to z = +3 cm into a 3 x 3 cm water rod, seen
+    # from multiples of 90 degrees only (equal chords): the energy of first interactions
+    # per 1 cm slice follows the heights the trajectory visits, and is zero outside [-3, 3)
+    ph = I.uniform_box(3, 3, 10, 1.0, I.WATER)
+    n = 300_000
+    if continuous:
+        # 1.5 turns: each slice is a 90-degree stretch of the helix, so all get a sixth
+        src = I.helical_source(100.0, 0.0, 0.0, 0.0, 0.0, turns=1.5, z0=-3.0, z1=3.0, n_proj_per_turn=4,
+                               continuous=True)
+        share = np.full(6, 1.0 / 6.0)
+    else:
+        # 2 turns of 4 projections: z_k = -3 + 0.75 k, k < 8, falls 2, 1, 1, 2, 1, 1 per slice
+        src = I.helical_source(100.0, 0.0, 0.0, 0.0, 0.0, turns=2.0, z0=-3.0, z1=3.0, n_proj_per_turn=4)
+        share = np.array([2, 1, 1, 2, 1, 1]) / 8.0
+    p = I.Problem("helix", ph, src, I.spectrum_line(60.0),
+                  I.Physics(e_min=10, e_max=150, mode="max_real", max_real=1), n, 10, 14)
+    r = oracle.run(p, precision=precision, threads=4)
+    per_z = r.edep.reshape(10, 9).sum(axis=1)
+    assert np.all(per_z[:2] == 0) and np.all(per_z[8:] == 0)
+    inside = per_z[2:8]
+    ex = inside.sum() * share
+    assert np.all(np.abs(inside - ex) < 5 * np.sqrt(ex * _mean_deposit(oracle, I.WATER, 1.0, 60.0))), inside / ex
+    if continuous:
+        # height and angle move together: slice i is lit from angles [90 i, 90 (i + 1)) degrees,
+        # the source at 100 (sin b, cos b, z), so the entry side of the rod takes more energy
+        e = r.edep.reshape(10, 3, 3)                  # [z, y, x]
+        for i, (sx, sy) in enumerate([(1, 1), (1, -1), (-1, -1), (-1, 1), (1, 1), (1, -1)]):
+            sl = e[2 + i]
+            near_x, far_x = (sl[:, 2].sum(), sl[:, 0].sum()) if sx > 0 else (sl[:, 0].sum(), sl[:, 2].sum())
+            near_y, far_y = (sl[2, :].sum(), sl[0, :].sum()) if sy > 0 else (sl[0, :].sum(), sl[2, :].sum())
+            assert near_x > 1.2 * far_x and near_y > 1.2 * far_y, (i, near_x / far_x, near_y / far_y)

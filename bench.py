@@ -301,8 +301,10 @@ def run_ours(args):
         h2 = ctd.ctd_create_phantom(ctx, ph.nx, ph.ny, ph.nz, ph.dx, ph.dy, ph.dz, mat_h, rho_h, ph.materials)
         s = p.source
         ctd.ctd_set_source(ctx, h2, s.kind, s.sad, s.u_lo, s.u_hi, s.v_lo, s.v_hi, s.n_proj, s.arc0, s.arc1,
-                           s.continuous)
+                           s.continuous, s.z0, s.z1)
         ctd.ctd_set_spectrum(ctx, h2, p.spectrum.e_lo, p.spectrum.e_hi, p.spectrum.w)
+        if s.fluence is not None:
+            ctd.ctd_set_fluence(ctx, h2, s.fluence)
         ctd.ctd_run(ctx, h2, p.n_hist, seed, p.n_batches)
         ctd._check(L.ctd_get_dose_and_stddev(ctx, h2, ctd._dp(dose_h), ctd._dp(sd_h), nvox, ctd.C.byref(st)))
         ctd.ctd_destroy_phantom(ctx, h2)

@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 4
+#define CTD_ABI_VERSION 5
 
 typedef enum {
     CTD_OK = 0,
@@ -93,6 +93,8 @@ typedef struct {
     int n_proj;
     double arc0_rad, arc1_rad;
     int continuous;
+    double z0_cm, z1_cm;  /* ARC: source height at arc0 and at arc1, linear in the angle,
+                             the field plane moving with it (helical CT); 0, 0: circle */
 } ctd_source;
 
 typedef enum { CTD_MODE_FULL = 0, CTD_MODE_MAX_REAL = 1 } ctd_mode;

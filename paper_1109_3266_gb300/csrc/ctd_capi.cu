@@ -336,6 +336,9 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     q.bin_hi = P.bins.p + q.nbins;
     q.cb = P.proj.p;
     q.sb = P.proj.p + (P.src.n_proj > 0 ? P.src.n_proj : 1);
+    q.zb = P.proj.p + 2 * (P.src.n_proj > 0 ? P.src.n_proj : 1);
+    q.hz0 = static_cast<float>(P.src.z0_cm);
+    q.hdz = static_cast<float>(P.src.z1_cm - P.src.z0_cm);
     q.counts = P.counts.p;
     q.seed = seed;
     q.nx = P.nx;
@@ -730,12 +733,15 @@ int ctd_set_source(ctd_ctx *ctx, ctd_phantom ph, const ctd_source *src)
     const int np = src->kind == CTD_SRC_ARC && !src->continuous ? src->n_proj : 1;
     if (src->kind == CTD_SRC_ARC && !src->continuous && (src->n_proj < 1 || src->n_proj > (1 << 24)))
         return fail(CTD_EINVAL, "n_proj must be 1..2^24");
-    std::vector<float> tab(2 * np);
+    if (!std::isfinite(src->z0_cm) || !std::isfinite(src->z1_cm)) return fail(CTD_EINVAL, "source heights must be finite");
+    std::vector<float> tab(3 * np);
     for (int k = 0; k < np; ++k) {
-        // projection angles b_k = arc0 + (arc1 - arc0) k / n_proj
+        // projection angles b_k = arc0 + (arc1 - arc0) k / n_proj, heights z0 + (z1 - z0) k / n_proj
         const double b = src->arc0_rad + (src->arc1_rad - src->arc0_rad) * static_cast<double>(k) / static_cast<double>(np);
         tab[k] = static_cast<float>(std::cos(b));
         tab[np + k] = static_cast<float>(std::sin(b));
+        tab[2 * np + k] =
+            static_cast<float>(src->z0_cm + (src->z1_cm - src->z0_cm) * static_cast<double>(k) / static_cast<double>(np));
     }
     if ((rc = P->proj.ensure(tab.size()))) return rc;
     CK(cudaMemcpyAsync(P->proj.p, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));

@@ -79,6 +79,7 @@ struct alignas(16) RequestDesc {
     const float *bin_hi;         // [nbins]
     const float *cb;             // [n_proj]
     const float *sb;             // [n_proj]
+    const float *zb;             // [n_proj] source height of each projection (helical)
     double *tally;               // [nvox] keV
     DeviceCounts *counts;
     unsigned long long *work;    // claim counter over [local_begin, local_end)
@@ -92,6 +93,7 @@ struct alignas(16) RequestDesc {
     float ix, iy, iz;
     int src_kind, n_proj, continuous;
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
+    float hz0, hdz;              // z0 and z1 - z0 of a continuous helical trajectory
     int mode, max_real;
     int cs_stride;               // 0 (one Klein-Nishina surface) or n_e * n_zeta (Waller-Hartree)
     const uint32_t *fl_thr;      // [fl_n] fluence-map alias thresholds (fl_n = 0: no map)

@@ -114,15 +114,17 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     const float elo = __ldg(&q.bin_lo[bin]), ehi = __ldg(&q.bin_hi[bin]);
     const float e = elo + (ehi - elo) * uni(b0.x);
     cnt.emitted(e);
-    float cb = 1.0f, sb = 0.0f;
+    float cb = 1.0f, sb = 0.0f, zs = 0.0f;
     if (q.src_kind == CTD_SRC_ARC) {
         if (q.continuous) {
             sincos_turns(q.a0t + q.awt * uni(b0.y), cb, sb);
+            zs = q.hz0 + q.hdz * uni(b0.y);
         } else {
             const uint32_t k =
                 static_cast<uint32_t>((static_cast<uint64_t>(b0.y) * static_cast<uint64_t>(q.n_proj)) >> 32);
             cb = __ldg(&q.cb[k]);
             sb = __ldg(&q.sb[k]);
+            zs = __ldg(&q.zb[k]);
         }
     }
     // uniform in solid angle over the field: uniform point, accepted with cos^3;
@@ -167,7 +169,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
         uz = vv * inv;
         rx = D * sb;
         ry = D * cb;
-        rz = 0.0f;
+        rz = zs;
     } else {
         ux = uu * inv;
         uy = vv * inv;

@@ -43,7 +43,7 @@ class ctd_material(C.Structure):
 class ctd_source(C.Structure):
     _fields_ = [("kind", C.c_int), ("sad_cm", C.c_double), ("u_lo_cm", C.c_double), ("u_hi_cm", C.c_double),
                 ("v_lo_cm", C.c_double), ("v_hi_cm", C.c_double), ("n_proj", C.c_int), ("arc0_rad", C.c_double),
-                ("arc1_rad", C.c_double), ("continuous", C.c_int)]
+                ("arc1_rad", C.c_double), ("continuous", C.c_int), ("z0_cm", C.c_double), ("z1_cm", C.c_double)]
 
 
 class ctd_physics(C.Structure):
@@ -190,9 +190,11 @@ def ctd_set_physics(ctx, ph, e_min_kev=1, e_max_kev=150, n_zeta=1024, majorant_s
 
 
 def ctd_set_source(ctx, ph, kind, sad_cm, u_lo_cm, u_hi_cm, v_lo_cm, v_hi_cm, n_proj=1, arc0_rad=0.0,
-                   arc1_rad=2 * np.pi, continuous=False):
+                   arc1_rad=2 * np.pi, continuous=False, z0_cm=0.0, z1_cm=0.0):
+    """z0_cm, z1_cm: arc source height at arc0 and arc1 (helical trajectory)."""
     k = {"static": CTD_SRC_STATIC, "arc": CTD_SRC_ARC}[kind] if isinstance(kind, str) else int(kind)
-    s = ctd_source(k, sad_cm, u_lo_cm, u_hi_cm, v_lo_cm, v_hi_cm, n_proj, arc0_rad, arc1_rad, int(continuous))
+    s = ctd_source(k, sad_cm, u_lo_cm, u_hi_cm, v_lo_cm, v_hi_cm, n_proj, arc0_rad, arc1_rad, int(continuous),
+                   float(z0_cm), float(z1_cm))
     _check(lib().ctd_set_source(ctx, ph, C.byref(s)))
 
 
@@ -321,7 +323,8 @@ def load_problem(ctx, problem, physics=True):
     ph_ = problem.phantom
     h = ctd_create_phantom(ctx, ph_.nx, ph_.ny, ph_.nz, ph_.dx, ph_.dy, ph_.dz, ph_.mat, ph_.rho, ph_.materials)
     s = problem.source
-    ctd_set_source(ctx, h, s.kind, s.sad, s.u_lo, s.u_hi, s.v_lo, s.v_hi, s.n_proj, s.arc0, s.arc1, s.continuous)
+    ctd_set_source(ctx, h, s.kind, s.sad, s.u_lo, s.u_hi, s.v_lo, s.v_hi, s.n_proj, s.arc0, s.arc1, s.continuous,
+                   getattr(s, "z0", 0.0), getattr(s, "z1", 0.0))
     sp = problem.spectrum
     ctd_set_spectrum(ctx, h, sp.e_lo, sp.e_hi, sp.w)
     if getattr(s, "fluence", None) is not None:

@@ -24,7 +24,6 @@ struct Photon {
     float x, y, z, ux, uy, uz, e;
     uint64_t h;
     uint32_t step;
-    int nreal;
     int j;            // energy node of e, its fraction and the majorant there;
     float te, mmax;   // they change only with e
 };
@@ -48,34 +47,75 @@ __device__ __forceinline__ void set_energy(Photon &ph, const SharedTables &sh, c
     ph.mmax = m0 + ph.te * (m1 - m0);
 }
 
-// Event counts of a lane, in registers.
-struct LaneCounts {
-    uint32_t n[10];
+// A lane's once-per-history event counts, energy totals and the real
+// interactions of its current photon, in shared memory: they change at most a
+// few times per history, and registers are what bounds the kernel's residency.
+struct LaneSlot {
     unsigned long long e_emitted, e_escaped;   // keV * 2^23
+    uint32_t ev[6];                            // PE, escaped, missed, cutoff, terminated, aborted
+    uint32_t nreal;                            // real interactions of the current photon
+    uint32_t pad;
+};
+static_assert(sizeof(LaneSlot) == 48, "LaneSlot layout");
+
+// Event counts of a lane: the per-step events (fictitious, Compton, Rayleigh)
+// in registers, the rest in the lane's slot.  Woodcock steps are not counted:
+// each ends in exactly one of escape, fictitious, PE, Compton or Rayleigh.
+struct LaneCounts {
+    uint32_t fict, compton, rayleigh;
+    LaneSlot *me;
     __device__ __forceinline__ void clear()
     {
+        fict = compton = rayleigh = 0;
+        me->e_emitted = 0;
+        me->e_escaped = 0;
 #pragma unroll
-        for (int i = 0; i < 10; ++i) n[i] = 0;
-        e_emitted = 0;
-        e_escaped = 0;
+        for (int i = 0; i < 6; ++i) me->ev[i] = 0;
     }
-    __device__ __forceinline__ void event(int k) { n[k]++; }
-    __device__ __forceinline__ void emitted(float e) { e_emitted += kev_fixed(e); }
-    __device__ __forceinline__ void escaped(float e) { e_escaped += kev_fixed(e); }
+    // k is a constant at every call site, so the switch folds away
+    __device__ __forceinline__ void event(int k)
+    {
+        switch (k) {
+        case kCntFict: ++fict; break;
+        case kCntCompton: ++compton; break;
+        case kCntRayleigh: ++rayleigh; break;
+        case kCntPe: ++me->ev[0]; break;
+        case kCntEscaped: ++me->ev[1]; break;
+        case kCntMissed: ++me->ev[2]; break;
+        case kCntCutoff: ++me->ev[3]; break;
+        case kCntTerminated: ++me->ev[4]; break;
+        default: ++me->ev[5]; break;   // kCntAborted
+        }
+    }
+    __device__ __forceinline__ void emitted(float e) { me->e_emitted += kev_fixed(e); }
+    __device__ __forceinline__ void escaped(float e) { me->e_escaped += kev_fixed(e); }
 };
 
 // A warp's counts added to a request's totals: warp sums, one atomic per
 // counter (energies as 128-bit fixed-point totals).  Leaves the counts cleared.
 __device__ __forceinline__ void flush_warp(DeviceCounts *dst, LaneCounts &c, int lane)
 {
+    __syncwarp();
+    const LaneSlot &m = *c.me;
+    uint32_t v[10];
+    v[kCntPe] = m.ev[0];
+    v[kCntCompton] = c.compton;
+    v[kCntRayleigh] = c.rayleigh;
+    v[kCntFict] = c.fict;
+    v[kCntEscaped] = m.ev[1];
+    v[kCntMissed] = m.ev[2];
+    v[kCntCutoff] = m.ev[3];
+    v[kCntTerminated] = m.ev[4];
+    v[kCntAborted] = m.ev[5];
+    v[kCntSteps] = m.ev[1] + c.fict + m.ev[0] + c.compton + c.rayleigh;
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        unsigned long long v = c.n[i];
+        unsigned long long x = v[i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-        if (lane == 0 && v) atomicAdd(&dst->n[i], v);
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        if (lane == 0 && x) atomicAdd(&dst->n[i], x);
     }
-    unsigned long long em = c.e_emitted, es = c.e_escaped;
+    unsigned long long em = m.e_emitted, es = m.e_escaped;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         em += __shfl_down_sync(kFull, em, o);
@@ -88,6 +128,7 @@ __device__ __forceinline__ void flush_warp(DeviceCounts *dst, LaneCounts &c, int
         if (o2 + es < o2) atomicAdd(&dst->e_fix[3], 1ull);
     }
     c.clear();
+    __syncwarp();
 }
 
 __device__ __forceinline__ int bin_search(const RequestDesc &q, uint64_t local)
@@ -226,7 +267,6 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     }
     const U4 b = draw<kKeys>(q, ph.h, ph.step, kStreamTransport);
     ph.step++;
-    cnt.n[kCntSteps]++;
     const int n_e = sh.n_e;
     const int j = ph.j;
     const float te = ph.te, mmax = ph.mmax;
@@ -258,7 +298,7 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     else if (y < rho * c3) type = 2;
     else type = 3;
     if (type == 3) {
-        cnt.n[kCntFict]++;
+        cnt.event(kCntFict);
         return kFictitious;
     }
     hit.idx = idx;
@@ -274,7 +314,6 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
 __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDesc &q, const float *__restrict__ s_mm,
                                          Photon &ph, const Hit &hit, LaneCounts &cnt)
 {
-    ph.nreal++;
     if (hit.type == 0) {
         // photoelectric absorption: the electron deposits E here
         cnt.event(kCntPe);
@@ -286,7 +325,7 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
     const float mu = surface(S, sh.n_zeta, ph.j, ph.te, uni(hit.rz));
     if (hit.type == 1) {
         // Compton: E' = E / (1 + (E/mc^2)(1 - mu)), the electron gets E - E'
-        cnt.n[kCntCompton]++;
+        cnt.event(kCntCompton);
         const float k = ph.e / static_cast<float>(kMec2);
         const float ep = ph.e / (1.0f + k * (1.0f - mu));
         if (ep < static_cast<float>(sh.e_min)) {
@@ -300,7 +339,7 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
     } else {
         cnt.event(kCntRayleigh);
     }
-    if (q.mode == CTD_MODE_MAX_REAL && ph.nreal >= q.max_real) {
+    if (q.mode == CTD_MODE_MAX_REAL && ++cnt.me->nreal >= static_cast<uint32_t>(q.max_real)) {
         cnt.event(kCntTerminated);
         cnt.escaped(ph.e);
         return false;
@@ -329,7 +368,7 @@ struct Queue {
     WarpPool *pool;
 };
 
-constexpr size_t kWarpBytes = kQueueBytes + sizeof(WarpPool);
+constexpr size_t kWarpBytes = kQueueBytes + sizeof(WarpPool) + 32 * sizeof(LaneSlot);
 
 // All histories [q.local_begin, q.local_end) of one request, claimed by warps
 // from q.work in runs of `chunk`.  Returns when the warp has no photon left.
@@ -414,7 +453,7 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
                 ph.uz = Q.f[5 * kQueue + slot];
                 ph.e = Q.f[6 * kQueue + slot];
                 ph.step = 0;
-                ph.nreal = 0;
+                cnt.me->nreal = 0;
                 set_energy(ph, P.sh, s_mm);
                 alive = true;
             }
@@ -469,6 +508,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
     Q.f = reinterpret_cast<float *>(Q.h + kQueue);
     Q.pool = reinterpret_cast<WarpPool *>(wbase + kQueueBytes);
     LaneCounts cnt;
+    cnt.me = reinterpret_cast<LaneSlot *>(wbase + kQueueBytes + sizeof(WarpPool)) + lane;
     cnt.clear();
 
     constexpr bool kMulti = kForm == 2;

@@ -179,6 +179,8 @@ def test_energy_conservation(oracle, precision):
         ends = c["pe"] + c["cutoff"] + c["escaped"] + c["missed"] + c["terminated"] + c["aborted"]
         assert ends == p.n_hist
         assert c["aborted"] == 0
+        # every Woodcock step ends in exactly one of: escape, fictitious, PE, Compton, Rayleigh
+        assert c["steps"] == c["escaped"] + c["fictitious"] + c["pe"] + c["compton"] + c["rayleigh"]
 
 
 def test_line_spectrum_emitted_energy_is_exact(oracle):

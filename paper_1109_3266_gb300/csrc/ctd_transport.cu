@@ -24,8 +24,8 @@ struct Photon {
     float x, y, z, ux, uy, uz, e;
     uint64_t h;
     uint32_t step;
-    int j;            // energy node of e, its fraction and the majorant there;
-    float te, mmax;   // they change only with e
+    int j;            // energy node of e, its fraction and 1 / the majorant there;
+    float te, imax;   // they change only with e
 };
 
 // Philox block of (history, step, stream) of request q: the round keys are
@@ -39,12 +39,12 @@ __device__ __forceinline__ U4 draw(const RequestDesc &q, uint64_t h, uint32_t st
     return block(q.seed, h, step, stream);
 }
 
-// energy node, fraction and majorant of the photon's energy
+// energy node, fraction and inverse majorant of the photon's energy
 __device__ __forceinline__ void set_energy(Photon &ph, const SharedTables &sh, const float *__restrict__ s_mm)
 {
     ph.j = enode(ph.e, sh.e_min, sh.n_e, ph.te);
     const float m0 = s_mm[ph.j], m1 = s_mm[ph.j + 1];
-    ph.mmax = m0 + ph.te * (m1 - m0);
+    ph.imax = 1.0f / (m0 + ph.te * (m1 - m0));
 }
 
 // A lane's once-per-history event counts, energy totals and the real
@@ -269,8 +269,8 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     ph.step++;
     const int n_e = sh.n_e;
     const int j = ph.j;
-    const float te = ph.te, mmax = ph.mmax;
-    const float path = (-log32(uni(b.x))) / mmax;
+    const float te = ph.te, imax = ph.imax;
+    const float path = (-log32(uni(b.x))) * imax;
     ph.x = ph.x + path * ph.ux;
     ph.y = ph.y + path * ph.uy;
     ph.z = ph.z + path * ph.uz;
@@ -291,11 +291,12 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     const float c2 = A.y + te * (B.y - A.y);
     const float c3 = A.z + te * (B.z - A.z);
     // interaction type with probabilities mu_i / mu_max
-    const float y = uni(b.y) * mmax;
+    const float y = uni(b.y);
+    const float sr = rho * imax;
     int type;
-    if (y < rho * c1) type = 0;
-    else if (y < rho * c2) type = 1;
-    else if (y < rho * c3) type = 2;
+    if (y < sr * c1) type = 0;
+    else if (y < sr * c2) type = 1;
+    else if (y < sr * c3) type = 2;
     else type = 3;
     if (type == 3) {
         cnt.event(kCntFict);
@@ -326,7 +327,7 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
     if (hit.type == 1) {
         // Compton: E' = E / (1 + (E/mc^2)(1 - mu)), the electron gets E - E'
         cnt.event(kCntCompton);
-        const float k = ph.e / static_cast<float>(kMec2);
+        const float k = ph.e * static_cast<float>(1.0 / kMec2);
         const float ep = ph.e / (1.0f + k * (1.0f - mu));
         if (ep < static_cast<float>(sh.e_min)) {
             cnt.event(kCntCutoff);

@@ -42,8 +42,8 @@ LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes issue per SM clock
 # (smsp__inst_executed x thread-per-instruction ratio / histories) and DRAM
 # bytes per launch (dram__bytes_read + dram__bytes_write).
 KERNEL_PROFILE = {
-    "cbct_water": {"lane_inst_per_history": 3072.0, "dram_bytes_per_launch": 13.60e9, "histories_per_launch": 1e8},
-    "head": {"lane_inst_per_history": 4490.0, "dram_bytes_per_launch": 23.33e9, "histories_per_launch": 2e8},
+    "cbct_water": {"lane_inst_per_history": 3046.0, "dram_bytes_per_launch": 9.07e9, "histories_per_launch": 1e8},
+    "head": {"lane_inst_per_history": 4420.0, "dram_bytes_per_launch": 14.16e9, "histories_per_launch": 2e8},
 }
 
 
@@ -514,7 +514,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--flight-cap", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the memory-ceiling probes")
     ap.add_argument("--rsd-stop", type=int, default=1, help="measure sec-to-1%% with the RSD-stopped form")

@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 5
+#define CTD_ABI_VERSION 6
 
 typedef enum {
     CTD_OK = 0,
@@ -272,9 +272,10 @@ int ctd_cancel(ctd_ctx *ctx, ctd_req_id id);
 /* Autotuner: launch-shape search for the single-request transport kernel.
  * It times probe launches of the phantom's current problem (its source,
  * spectrum and physics; the first batch of 10 * n_probe histories with seed,
- * that is n_probe histories over every 1 keV bin) for blocks per SM in {3, 4},
- * claims of {64, 256, 1024} histories and flight caps of {1, 2, 4, 8}, and
- * keeps the fastest shape in the context for later runs.  Results of a run do
+ * that is n_probe histories over every 1 keV bin) for blocks of 256 threads,
+ * 3 or 4 per SM, or of 128 threads, 7 or 8 per SM; claims of {64, 256, 1024}
+ * histories; flight caps of {1, 2, 4, 8} (48 shapes and the context's own),
+ * and keeps the fastest shape in the context for later runs.  Results of a run do
  * not depend on the launch shape (up to the order of binary64 additions). */
 typedef struct {
     int blocks_per_sm;
@@ -283,6 +284,7 @@ typedef struct {
     int n_tried;
     double histories_per_s;    /* of the chosen shape on the probe */
     double baseline_per_s;     /* of the shape the context had before */
+    int threads_per_block;
 } ctd_tune_result;
 
 int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, ctd_tune_result *out);

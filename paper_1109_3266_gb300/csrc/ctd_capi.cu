@@ -1582,19 +1582,24 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
     P->have_result = false;
     ctd::RequestDesc q;
     fill_request(*P, seed, q);
-    const int old_bps = ctx->blocks_per_sm, old_chunk = ctx->chunk, old_cap = ctx->flight_cap;
+    const int old_bps = ctx->blocks_per_sm, old_chunk = ctx->chunk, old_cap = ctx->flight_cap,
+              old_threads = ctx->threads;
     struct Shape {
-        int bps, chunk, cap;
+        int threads, bps, chunk, cap;
     };
     std::vector<Shape> shapes;
-    shapes.push_back({old_bps, old_chunk, old_cap});
-    for (int bps : {3, 4})
+    shapes.push_back({old_threads, old_bps, old_chunk, old_cap});
+    // blocks of 256 threads, 3 or 4 per SM, or of 128 threads, 7 or 8 per SM
+    const int blocks[4][2] = {{256, 3}, {256, 4}, {128, 7}, {128, 8}};
+    for (const auto &b : blocks)
         for (int chunk : {64, 256, 1024})
             for (int cap : {1, 2, 4, 8})
-                if (!(bps == old_bps && chunk == old_chunk && cap == old_cap)) shapes.push_back({bps, chunk, cap});
+                if (!(b[0] == old_threads && b[1] == old_bps && chunk == old_chunk && cap == old_cap))
+                    shapes.push_back({b[0], b[1], chunk, cap});
     double best = 1e300, base = 0.0;
     Shape pick = shapes[0];
     for (size_t k = 0; k < shapes.size(); ++k) {
+        ctx->threads = shapes[k].threads;
         ctx->blocks_per_sm = shapes[k].bps;
         ctx->chunk = shapes[k].chunk;
         ctx->flight_cap = shapes[k].cap;
@@ -1602,6 +1607,7 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
             if ((rc = transport(ctx, *P, q, 0, 0, 0, n_probe, P->tally.p, 0))) {
+                ctx->threads = old_threads;
                 ctx->blocks_per_sm = old_bps;
                 ctx->chunk = old_chunk;
                 ctx->flight_cap = old_cap;
@@ -1621,10 +1627,12 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
     CK(cudaMemsetAsync(P->tally.p, 0, P->nvox * sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->threads = pick.threads;
     ctx->blocks_per_sm = pick.bps;
     ctx->chunk = pick.chunk;
     ctx->flight_cap = pick.cap;
     if (out) {
+        out->threads_per_block = pick.threads;
         out->blocks_per_sm = pick.bps;
         out->chunk = pick.chunk;
         out->flight_cap = pick.cap;

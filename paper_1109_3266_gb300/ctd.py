@@ -81,7 +81,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(5)
 
 class ctd_tune_result(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int), ("n_tried", C.c_int),
-                ("histories_per_s", C.c_double), ("baseline_per_s", C.c_double)]
+                ("histories_per_s", C.c_double), ("baseline_per_s", C.c_double), ("threads_per_block", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -379,6 +379,9 @@ def run_ours(args):
             "sec_to_1pct_avg_rsd": measured_1["seconds"] if measured_1 else sec_to_1,
             "sec_to_1pct_avg_rsd_extrapolated": sec_to_1, "rsd_stopped_run": measured_1,
             "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
+            # Sec. 3.1's simulation efficiency 1 / (sigma_bar^2 T), T the device time of one run
+            "paper_efficiency_per_s": (1.0 / (stats["paper_sigma_bar"] ** 2 * sec_run)
+                                       if stats["paper_sigma_bar"] > 0 else None),
             "clocks": ck,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},

@@ -182,3 +182,35 @@ def test_autotune_picks_a_shape_and_results_do_not_depend_on_it(ctd, ctx):
     same(before, ctd.ctd_get_dose_and_stddev(c2, h, p.phantom.nvox))
     ctd.ctd_destroy_phantom(c2, h)
     ctd.ctd_destroy(c2)
+
+
+def test_batched_full_size_requests(ctd, oracle):
+    # the specified 64 requests (cubes of 64^3 to 256^3 voxels, water and head, 80-140 kVp)
+    # in the launch configuration the benchmark times, with histories scaled down: batched
+    # results equal separate runs, and sampled history ranges of two requests equal the
+    # binary32 oracle bit for bit
+    from test_gpu_parity import COUNT_KEYS as CK
+    reqs = [I.scaled(p, n_hist=max(20_000, p.n_hist // 2000)) for p in I.batched_requests(64)]
+    c = ctd.ctd_create(device=0)
+    hs = [ctd.load_problem(c, p) for p in reqs]
+    ctd.ctd_run_batch(c, hs, [p.n_hist for p in reqs], [p.seed for p in reqs], 10)
+    got = [ctd.ctd_get_dose_and_stddev(c, h, 0, want_arrays=False)[2] for h in hs]
+    picks = [0, 13, 38, 63]
+    doses = {r: ctd.ctd_get_dose_and_stddev(c, hs[r], reqs[r].phantom.nvox)[0] for r in picks}
+    for r, p in enumerate(reqs):
+        ctd.ctd_run(c, hs[r], p.n_hist, p.seed, 10)
+        st = ctd.ctd_get_dose_and_stddev(c, hs[r], 0, want_arrays=False)[2]
+        diff = {k: (got[r][k], st[k]) for k in CK if got[r][k] != st[k]}
+        assert not diff, (r, diff)
+        if r in picks:
+            assert np.allclose(ctd.ctd_get_dose_and_stddev(c, hs[r], p.phantom.nvox)[0], doses[r], rtol=1e-9, atol=0)
+    for r in (1, 62):
+        p = reqs[r]
+        s32 = oracle.Setup(p, 32)
+        for a, b in ((0, 3000), (p.n_hist - 3000, p.n_hist)):
+            ctd.ctd_run_range(c, hs[r], p.n_hist, p.seed, 10, a, b, clear=True)
+            st = ctd.ctd_get_dose_and_stddev(c, hs[r], 0, want_arrays=False)[2]
+            _, oc = s32.transport(a, b, threads=8)
+            diff = {k: (st[k], oc[k]) for k in CK if st[k] != oc[k]}
+            assert not diff, (r, a, diff)
+    ctd.ctd_destroy(c)

@@ -1,0 +1,132 @@
+// ctd_tune.cu -- the launch-shape search for the single-request transport
+// kernel (ctd_autotune) and the memory-ceiling probes (ctd_probe_memory) of
+// the C ABI in include/ctd.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ctd_host.h"
+
+using namespace ctd::host;
+
+// ---------------------------------------------------------------- autotuner
+extern "C" {
+
+int ctd_probe_memory(ctd_ctx *ctx, int kind, uint64_t n_slots, uint64_t n_ops, double *ops_per_s)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    if (kind < 0 || kind > 2 || n_slots < 1 || n_slots >= (1ull << 32) || n_ops < 1 || n_ops > (1ull << 40) ||
+        !ops_per_s)
+        return fail(CTD_EINVAL, "probe: kind 0-2, 1 <= n_slots < 2^32, 1 <= n_ops <= 2^40");
+    const int block = 256, grid = ctx->num_sms * 8;
+    const uint64_t per_round = static_cast<uint64_t>(grid) * block * 8;
+    const uint64_t rounds64 = (n_ops + per_round - 1) / per_round;
+    // operation indices are 32-bit
+    if (rounds64 * per_round >= (1ull << 32)) return fail(CTD_EINVAL, "probe: n_ops too large for one launch");
+    const uint32_t rounds = static_cast<uint32_t>(rounds64);
+    DevBuf<double> dbuf;
+    DevBuf<float> fbuf, out;
+    DevBuf<uint8_t> mbuf;
+    if (kind == 0) rc = dbuf.ensure(n_slots);
+    else rc = fbuf.ensure(n_slots);
+    if (!rc && kind == 2) rc = mbuf.ensure(n_slots);
+    if (!rc && kind != 0) rc = out.ensure(static_cast<size_t>(grid) * block);
+    if (rc) return rc;
+    if (kind == 0) CK(cudaMemsetAsync(dbuf.p, 0, n_slots * sizeof(double), ctx->stream));
+    if (kind != 0) CK(cudaMemsetAsync(fbuf.p, 0, n_slots * sizeof(float), ctx->stream));
+    if (kind == 2) CK(cudaMemsetAsync(mbuf.p, 0, n_slots, ctx->stream));
+    if (!event_at(ctx, 0) || !event_at(ctx, 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
+    const uint32_t n32 = static_cast<uint32_t>(n_slots);
+    CKS(ctd::launch_probe(kind, dbuf.p, fbuf.p, mbuf.p, out.p, n32, rounds, 0x9E3779B9u, grid, block, ctx->stream));
+    double t = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        CK(cudaEventRecord(ctx->events[0], ctx->stream));
+        CKS(ctd::launch_probe(kind, dbuf.p, fbuf.p, mbuf.p, out.p, n32, rounds, 0x85EBCA6Bu * (k + 1), grid, block,
+                              ctx->stream));
+        CK(cudaEventRecord(ctx->events[1], ctx->stream));
+        CK(cudaEventSynchronize(ctx->events[1]));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]));
+        t += ms * 1e-3;
+    }
+    *ops_per_s = 3.0 * static_cast<double>(rounds) * static_cast<double>(per_round) / t;
+    return CTD_OK;
+}
+
+int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, ctd_tune_result *out)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if ((rc = busy(P))) return rc;
+    if (n_probe < 1000) return fail(CTD_EINVAL, "n_probe must be at least 1000");
+    const uint64_t n = 10 * n_probe;
+    if ((rc = prepare_run(ctx, *P, n, 10))) return rc;
+    P->have_result = false;
+    ctd::RequestDesc q;
+    fill_request(*P, seed, q);
+    const int old_bps = ctx->blocks_per_sm, old_chunk = ctx->chunk, old_cap = ctx->flight_cap,
+              old_threads = ctx->threads;
+    struct Shape {
+        int threads, bps, chunk, cap;
+    };
+    std::vector<Shape> shapes;
+    shapes.push_back({old_threads, old_bps, old_chunk, old_cap});
+    // blocks of 256 threads, 3 or 4 per SM, or of 128 threads, 7 or 8 per SM
+    const int blocks[4][2] = {{256, 3}, {256, 4}, {128, 7}, {128, 8}};
+    for (const auto &b : blocks)
+        for (int chunk : {64, 256, 1024})
+            for (int cap : {1, 2, 4, 8})
+                if (!(b[0] == old_threads && b[1] == old_bps && chunk == old_chunk && cap == old_cap))
+                    shapes.push_back({b[0], b[1], chunk, cap});
+    double best = 1e300, base = 0.0;
+    Shape pick = shapes[0];
+    for (size_t k = 0; k < shapes.size(); ++k) {
+        ctx->threads = shapes[k].threads;
+        ctx->blocks_per_sm = shapes[k].bps;
+        ctx->chunk = shapes[k].chunk;
+        ctx->flight_cap = shapes[k].cap;
+        double t_min = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+            if ((rc = transport(ctx, *P, q, 0, 0, 0, n_probe, P->tally.p, 0))) {
+                ctx->threads = old_threads;
+                ctx->blocks_per_sm = old_bps;
+                ctx->chunk = old_chunk;
+                ctx->flight_cap = old_cap;
+                return rc;
+            }
+            CK(cudaStreamSynchronize(ctx->stream));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]));
+            t_min = std::min(t_min, static_cast<double>(ms) * 1e-3);
+        }
+        if (k == 0) base = t_min;
+        if (t_min < best) {
+            best = t_min;
+            pick = shapes[k];
+        }
+    }
+    CK(cudaMemsetAsync(P->tally.p, 0, P->nvox * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->threads = pick.threads;
+    ctx->blocks_per_sm = pick.bps;
+    ctx->chunk = pick.chunk;
+    ctx->flight_cap = pick.cap;
+    if (out) {
+        out->threads_per_block = pick.threads;
+        out->blocks_per_sm = pick.bps;
+        out->chunk = pick.chunk;
+        out->flight_cap = pick.cap;
+        out->n_tried = static_cast<int>(shapes.size());
+        out->histories_per_s = static_cast<double>(n_probe) / best;
+        out->baseline_per_s = static_cast<double>(n_probe) / base;
+    }
+    return CTD_OK;
+}
+
+}  // extern "C"

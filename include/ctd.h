@@ -150,7 +150,7 @@ int ctd_destroy(ctd_ctx *ctx);
  * origin; mat[v] < n_mat indexes mats; density[v] >= 0 (g/cm^3).  Host arrays;
  * the library copies them to the device and keeps them resident until
  * ctd_destroy_phantom.  Default physics: nodes 1..150 keV, n_zeta 1024, scale 1,
- * full transport. */
+ * full transport.  Fewer than 2^32 voxels (CTD_EINVAL otherwise). */
 int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz,
                        const uint8_t *mat, const float *density, int n_mat, const ctd_material *mats,
                        ctd_phantom *out);

@@ -499,7 +499,8 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
             !std::isfinite(mats[m].sq0))
             return fail(CTD_EINVAL, "material %d has non-positive or non-finite parameters", m);
     const size_t nvox = static_cast<size_t>(nx) * ny * nz;
-    if (nvox > (static_cast<size_t>(1) << 40)) return fail(CTD_EINVAL, "phantom too large");
+    // voxel indices are 32-bit on the device
+    if (nvox >= (static_cast<size_t>(1) << 32)) return fail(CTD_EINVAL, "phantom too large (2^32 voxels or more)");
     std::unique_ptr<Phantom> P(new Phantom());
     P->nx = nx; P->ny = ny; P->nz = nz;
     P->dx = dx; P->dy = dy; P->dz = dz;

@@ -245,7 +245,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
 
 // Site of a real interaction found by a flight
 struct Hit {
-    size_t idx;       // voxel
+    uint32_t idx;     // voxel (phantoms hold fewer than 2^32 voxels)
     int m;            // material
     int type;         // 0 photoelectric, 1 Compton, 2 Rayleigh
     uint32_t rz, rw;  // the step's random words for zeta and phi
@@ -281,9 +281,10 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
         cnt.escaped(ph.e);
         return kEnded;
     }
-    const size_t idx = static_cast<size_t>(static_cast<int>(fx)) +
-                       static_cast<size_t>(q.nx) * (static_cast<size_t>(static_cast<int>(fy)) +
-                                                    static_cast<size_t>(q.ny) * static_cast<size_t>(static_cast<int>(fz)));
+    const uint32_t idx = static_cast<uint32_t>(static_cast<int>(fx)) +
+                         static_cast<uint32_t>(q.nx) *
+                             (static_cast<uint32_t>(static_cast<int>(fy)) +
+                              static_cast<uint32_t>(q.ny) * static_cast<uint32_t>(static_cast<int>(fz)));
     const int m = __ldg(&q.mat[idx]);
     const float rho = __ldg(&q.rho[idx]);
     const float4 A = s_tab[m * n_e + j], B = s_tab[m * n_e + j + 1];

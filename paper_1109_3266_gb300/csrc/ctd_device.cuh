@@ -154,17 +154,17 @@ __device__ __forceinline__ float trunc32(double d)
     return __uint_as_float((hi & 0x80000000u) | (((ex - 896u) & 0xffu) << 23) | m);
 }
 
-// Back to unit length after a scatter: the squared norm n2 and the correction
-// e = c - 1 of one Newton step c = 1.5 - 0.5 n2 for 1/sqrt(n2) from 1 are
-// binary64 (the products of widened floats are exact, so the fused forms equal
-// the separately rounded ones); e, truncated to binary32, is applied to each
-// component with one fused multiply-add.
+// Back to unit length after a scatter: d = n2 - 1, the squared norm's excess,
+// in binary64 with three fused multiply-adds, ((y^2 - 1) + x^2) + z^2, from the
+// widened components (each square is exact in binary64); the correction
+// e = -d/2 of one Newton step c = 1.5 - 0.5 n2 for 1/sqrt(n2) from 1 is d
+// truncated to binary32 times -1/2, applied to each component with one fused
+// multiply-add.
 __device__ __forceinline__ void renorm(float &ux, float &uy, float &uz)
 {
     const double dx = widen(ux), dy = widen(uy), dz = widen(uz);
-    const double n2 = __fma_rn(dz, dz, __fma_rn(dx, dx, __dmul_rn(dy, dy)));
-    const double e = __fma_rn(-0.5, n2, 0.5);
-    const float ef = trunc32(e);
+    const double d = __fma_rn(dz, dz, __fma_rn(dx, dx, __fma_rn(dy, dy, -1.0)));
+    const float ef = trunc32(d) * -0.5f;
     ux = __fmaf_rn(ux, ef, ux);
     uy = __fmaf_rn(uy, ef, uy);
     uz = __fmaf_rn(uz, ef, uz);

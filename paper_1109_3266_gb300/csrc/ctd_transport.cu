@@ -219,7 +219,8 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
         ry = 0.0f;
         rz = -D;
     }
-    renorm(ux, uy, uz);
+    // (the source direction is normalised in binary32; binary64 renormalisation
+    // is for the directions made by scatters)
     // entry into the box (slab method); outside is vacuum
     const float t0x = (q.bx0 - rx) / ux, t1x = (q.bx1 - rx) / ux;
     const float t0y = (q.by0 - ry) / uy, t1y = (q.by1 - ry) / uy;

@@ -42,8 +42,8 @@ LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes issue per SM clock
 # (smsp__inst_executed x thread-per-instruction ratio / histories) and DRAM
 # bytes per launch (dram__bytes_read + dram__bytes_write).
 KERNEL_PROFILE = {
-    "cbct_water": {"lane_inst_per_history": 3046.0, "dram_bytes_per_launch": 9.07e9, "histories_per_launch": 1e8},
-    "head": {"lane_inst_per_history": 4420.0, "dram_bytes_per_launch": 14.16e9, "histories_per_launch": 2e8},
+    "cbct_water": {"lane_inst_per_history": 2890.0, "dram_bytes_per_launch": 8.55e9, "histories_per_launch": 1e8},
+    "head": {"lane_inst_per_history": 4007.0, "dram_bytes_per_launch": 13.16e9, "histories_per_launch": 2e8},
 }
 
 
@@ -182,8 +182,13 @@ def oracle_rate(p, seconds, threads, n_ranges=64):
         if dt > 0.5 or n >= batch:
             break
         n *= 4
+    # size the sample from the probe's rate, then once more from the sample's own
+    # rate if the first estimate (small samples pay thread start-up) fell short
     n = int(max(n_ranges, min(batch, done / max(dt, 1e-6) * seconds)))
     done, dt = sample(n)
+    if dt < 0.6 * seconds and n < batch:
+        n = int(max(n_ranges, min(batch, done / max(dt, 1e-6) * seconds)))
+        done, dt = sample(n)
     return done / dt, done, dt, None
 
 

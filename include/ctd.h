@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 6
+#define CTD_ABI_VERSION 7
 
 typedef enum {
     CTD_OK = 0,
@@ -54,6 +54,9 @@ typedef struct {
     double serve_round_histories; /* requests are admitted first in, first out while one
                                  batch of every running request stays within this many
                                  histories (default 1e8); one request always runs     */
+    double serve_reserve_bytes; /* served form: a request is admitted only while the device's
+                                 free memory exceeds what its buffers need by this much
+                                 (default 1 GiB)                                        */
     int shared_launch;        /* batched and served forms: 0 (default) runs each request's
                                  batches as its own chain of single-request launches on
                                  its own stream, so that one request's tail overlaps the
@@ -218,7 +221,7 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
  * random numbers keyed by seed until, after at least min_batches batches, its
  * avg RSD is <= rsd_target, or until n_histories_max histories have run.
  * Requests wait in a queue until admitted, first in, first out (free device
- * memory above the context's 1 GiB reserve, fewer than serve_max_active
+ * memory above the context's reserve, serve_reserve_bytes, fewer than serve_max_active
  * running, one round within serve_round_histories); each call of ctd_serve_step
  * admits what fits, runs one batch of every running request (each on its own
  * stream, or with shared_launch = 1 in one shared launch, which needs every

@@ -445,6 +445,7 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
         if (opt->multi_blocks_per_sm > 0) ctx->multi_blocks_per_sm = opt->multi_blocks_per_sm;
         if (opt->serve_max_active > 0) ctx->max_active = opt->serve_max_active;
         if (opt->serve_round_histories > 0) ctx->round_histories = opt->serve_round_histories;
+        if (opt->serve_reserve_bytes > 0) ctx->reserve_bytes = opt->serve_reserve_bytes;
         if (opt->threads_per_block > 0) ctx->threads = opt->threads_per_block;
         if (opt->chunk > 0) ctx->chunk = opt->chunk;
         if (opt->flight_cap > 0) ctx->flight_cap = opt->flight_cap;

@@ -44,4 +44,4 @@ def test_calls_fail_cleanly_without_a_device():
     rc = ctd.lib().ctd_create(ctypes.byref(h), None)
     assert rc == 3 and not h.value
     assert ctd.lib().ctd_last_error()
-    assert ctd.lib().ctd_abi_version() == 6
+    assert ctd.lib().ctd_abi_version() == 7

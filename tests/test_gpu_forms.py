@@ -214,3 +214,25 @@ def test_batched_full_size_requests(ctd, oracle):
             diff = {k: (st[k], oc[k]) for k in CK if st[k] != oc[k]}
             assert not diff, (r, a, diff)
     ctd.ctd_destroy(c)
+
+
+def test_served_admission_by_free_device_memory(ctd):
+    # a reserve larger than any GPU's memory keeps a request queued: waiting on it is
+    # refused with CTD_ENOMEM instead of spinning, and it can still be cancelled
+    p = problems()[3]
+    tight = ctd.ctd_create(device=0, serve_reserve_bytes=1e15)
+    h = ctd.load_problem(tight, p)
+    rid = ctd.ctd_submit(tight, h, 5_000, 0.5, 1)
+    with pytest.raises(ctd.CtdError) as e:
+        ctd.ctd_wait(tight, rid, 30.0)
+    assert e.value.code == 2                                   # CTD_ENOMEM
+    assert ctd.ctd_poll(tight, rid)["state"] == ctd.REQ_QUEUED
+    ctd.ctd_cancel(tight, rid)
+    assert ctd.ctd_poll(tight, rid)["state"] == ctd.REQ_CANCELLED
+    ctd.ctd_destroy(tight)
+    # the same request under the default reserve is admitted and finishes
+    c = ctd.ctd_create(device=0)
+    h = ctd.load_problem(c, p)
+    rid = ctd.ctd_submit(c, h, 5_000, 0.5, 1)
+    assert ctd.ctd_wait(c, rid, 60.0)["state"] == ctd.REQ_DONE
+    ctd.ctd_destroy(c)

@@ -483,7 +483,7 @@ def run_served(args):
     out = {}
     for label, max_active in (("continuous", 0), ("one_at_a_time", 1)):
         ctx = ctd.ctd_create(device=0, multi_blocks_per_sm=args.multi_blocks_per_sm, serve_max_active=max_active,
-                             shared_launch=args.shared_launch)
+                             shared_launch=args.shared_launch, serve_round_histories=args.round_histories)
         # warm-up: one request alone
         serve.serve(ctx, [(0.0, 4999)], make, args.batch_histories, 0.01, n_histories_max=40 * args.batch_histories)
         with Clocks(0) as clk:
@@ -504,7 +504,8 @@ def run_served(args):
         "config": {"workload": "served", "phantom": [nx, ny, nz], "voxel_cm": d, "rate_per_s": args.rate,
                    "requests": args.n_requests, "batch_histories": args.batch_histories, "rsd_target": 0.01,
                    "min_batches": 10, "phantom_pool": args.pool, "time_limit_s": args.time_limit,
-                   "launches": "shared multi-request launch" if args.shared_launch else "one stream per request"},
+                   "launches": "shared multi-request launch" if args.shared_launch else "one stream per request",
+                   "round_histories": args.round_histories or 1e8},
         "continuous": c, "one_at_a_time": o,
         "throughput_vs_one_at_a_time": (c["histories_per_s"] / o["histories_per_s"]) if o["histories_per_s"] else None,
     }), flush=True)
@@ -536,6 +537,8 @@ def main():
     ap.add_argument("--time-limit", type=float, default=None)
     ap.add_argument("--multi-blocks-per-sm", type=int, default=0)
     ap.add_argument("--shared-launch", type=int, default=0, help="served form: one shared multi-request launch")
+    ap.add_argument("--round-histories", type=float, default=0.0,
+                    help="served form: histories one round may hold before admission stops (0: 1e8)")
     ap.add_argument("--compton", default="kn", choices=["kn", "wh"],
                     help="Compton model: free-electron Klein-Nishina or Waller-Hartree")
     ap.add_argument("--hist-lo", type=float, default=1e7)

@@ -289,21 +289,21 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     const int m = __ldg(&q.mat[idx]);
     const float rho = __ldg(&q.rho[idx]);
     const float4 A = s_tab[m * n_e + j], B = s_tab[m * n_e + j + 1];
-    const float c1 = A.x + te * (B.x - A.x);
-    const float c2 = A.y + te * (B.y - A.y);
-    const float c3 = A.z + te * (B.z - A.z);
-    // interaction type with probabilities mu_i / mu_max
+    // interaction type with probabilities mu_i / mu_max: fictitious when u1 is at or
+    // above the total share; otherwise the first cumulative share above u1
     const float y = uni(b.y);
     const float sr = rho * imax;
-    int type;
-    if (y < sr * c1) type = 0;
-    else if (y < sr * c2) type = 1;
-    else if (y < sr * c3) type = 2;
-    else type = 3;
-    if (type == 3) {
+    const float c3 = A.z + te * (B.z - A.z);
+    if (!(y < sr * c3)) {
         cnt.event(kCntFict);
         return kFictitious;
     }
+    const float c1 = A.x + te * (B.x - A.x);
+    const float c2 = A.y + te * (B.y - A.y);
+    int type;
+    if (y < sr * c1) type = 0;
+    else if (y < sr * c2) type = 1;
+    else type = 2;
     hit.idx = idx;
     hit.m = m;
     hit.type = type;

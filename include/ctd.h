@@ -184,6 +184,15 @@ int ctd_get_fluence_table(ctd_ctx *ctx, ctd_phantom ph, int *n, uint32_t *thr, i
 int ctd_set_spectrum(ctd_ctx *ctx, ctd_phantom ph, const double *e_lo, const double *e_hi,
                      const double *w, int nbins);
 
+/* Helper: a synthetic tube spectrum for ctd_set_spectrum, Kramers' thick-target
+ * law (kvp - E)/E on 1 keV bins [j, j+1) for j = e_min .. kvp-1, evaluated at
+ * the bin middle and filtered by mm_al millimetres of aluminium with the mass
+ * attenuation fit 26300/E^3 + 0.15 cm^2/g (E in keV) at 2.699 g/cm^3.  Writes
+ * *nbins = kvp - e_min entries to e_lo, e_hi and w when they are non-NULL (call
+ * once with NULL arrays for the count).  Host only; needs no context or GPU.
+ * 1 <= e_min < kvp <= 100000, mm_al >= 0, else CTD_EINVAL. */
+int ctd_spectrum_kramers(int kvp, double mm_al, int e_min, double *e_lo, double *e_hi, double *w, int *nbins);
+
 /* Transport n_histories in n_batches (>= 2) batches (Sec. 2.2.1) with random
  * numbers keyed by seed; afterwards mean dose and batch uncertainty are ready
  * for ctd_get_dose_and_stddev.  Blocks until the device is done. */

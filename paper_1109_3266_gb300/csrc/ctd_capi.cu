@@ -680,6 +680,22 @@ int ctd_set_spectrum(ctd_ctx *ctx, ctd_phantom ph, const double *e_lo, const dou
     return CTD_OK;
 }
 
+int ctd_spectrum_kramers(int kvp, double mm_al, int e_min, double *e_lo, double *e_hi, double *w, int *nbins)
+{
+    g_error.clear();
+    if (e_min < 1 || kvp <= e_min || kvp > 100000 || !(mm_al >= 0.0) || !std::isfinite(mm_al) || !nbins)
+        return fail(CTD_EINVAL, "need 1 <= e_min < kvp <= 100000 and mm_al >= 0");
+    *nbins = kvp - e_min;
+    for (int j = 0; j < *nbins; ++j) {
+        const double lo = static_cast<double>(e_min + j), mid = lo + 0.5;
+        const double mu_al = 26300.0 / (mid * mid * mid) + 0.15;
+        if (e_lo) e_lo[j] = lo;
+        if (e_hi) e_hi[j] = lo + 1.0;
+        if (w) w[j] = (static_cast<double>(kvp) - mid) / mid * std::exp(-mu_al * 2.699 * (mm_al / 10.0));
+    }
+    return CTD_OK;
+}
+
 int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches)
 {
     int rc;

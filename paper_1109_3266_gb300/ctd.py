@@ -127,6 +127,7 @@ def lib():
         L.ctd_autotune.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.POINTER(ctd_tune_result)]
         L.ctd_probe_memory.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, dp]
         L.ctd_set_fluence.argtypes = [P, C.c_int32, C.c_int, C.c_int, dp]
+        L.ctd_spectrum_kramers.argtypes = [C.c_int, C.c_double, C.c_int, dp, dp, dp, C.POINTER(C.c_int)]
         L.ctd_get_fluence_table.argtypes = [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_uint32),
                                             C.POINTER(C.c_int32)]
         _lib = L
@@ -336,6 +337,15 @@ def load_problem(ctx, problem, physics=True):
         ctd_set_physics(ctx, h, p.e_min, p.e_max, p.n_zeta, p.majorant_scale, p.mode, p.max_real,
                         getattr(p, "compton", "kn"))
     return h
+
+
+def ctd_spectrum_kramers(kvp, mm_al, e_min=1):
+    """Kramers' spectrum with aluminium filtration on 1 keV bins: (e_lo, e_hi, w)."""
+    n = C.c_int()
+    _check(lib().ctd_spectrum_kramers(int(kvp), float(mm_al), int(e_min), None, None, None, C.byref(n)))
+    lo, hi, w = (np.empty(n.value) for _ in range(3))
+    _check(lib().ctd_spectrum_kramers(int(kvp), float(mm_al), int(e_min), _dp(lo), _dp(hi), _dp(w), C.byref(n)))
+    return lo, hi, w
 
 
 def ctd_set_fluence(ctx, ph, f):

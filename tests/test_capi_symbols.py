@@ -3,6 +3,7 @@ that include/ctd.h declares; the binding keeps the C names."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -45,3 +46,16 @@ def test_calls_fail_cleanly_without_a_device():
     assert rc == 3 and not h.value
     assert ctd.lib().ctd_last_error()
     assert ctd.lib().ctd_abi_version() == 7
+
+
+def test_kramers_helper_matches_the_input_recipe():
+    # a host-only helper: the library's Kramers spectrum equals the input generator's
+    from paper_1109_3266_gb300 import ctd, inputs as I
+    for kvp, mm, e_min in ((120, 2.5, 1), (80, 0.0, 10), (140, 4.0, 1)):
+        lo, hi, w = ctd.ctd_spectrum_kramers(kvp, mm, e_min)
+        ref = I.spectrum_kramers(kvp, mm, e_min)
+        assert np.array_equal(lo, ref.e_lo) and np.array_equal(hi, ref.e_hi)
+        assert np.allclose(w, ref.w, rtol=1e-13, atol=0)
+    for bad in ((10, 1.0, 10), (100, -1.0, 1), (100, 1.0, 0)):
+        with pytest.raises(ctd.CtdError):
+            ctd.ctd_spectrum_kramers(*bad)

@@ -59,3 +59,60 @@ def test_kramers_helper_matches_the_input_recipe():
     for bad in ((10, 1.0, 10), (100, -1.0, 1), (100, 1.0, 0)):
         with pytest.raises(ctd.CtdError):
             ctd.ctd_spectrum_kramers(*bad)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "ctd.h"
+
+int main(void)
+{
+    double lo[200], hi[200], w[200];
+    int n = 0;
+    if (ctd_spectrum_kramers(120, 2.5, 1, lo, hi, w, &n) != CTD_OK) return 1;
+    if (ctd_spectrum_kramers(10, 1.0, 10, NULL, NULL, NULL, &n) != CTD_EINVAL) return 2;
+    if (ctd_last_error()[0] == '\0') return 3;
+    ctd_spectrum_kramers(120, 2.5, 1, lo, hi, w, &n);
+    /* the layouts the Python binding mirrors */
+    printf("%d %d %.17g %.17g\n", ctd_abi_version(), n, w[0], w[n - 1]);
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ctd_options), sizeof(ctd_material), sizeof(ctd_source),
+           sizeof(ctd_physics), sizeof(ctd_run_stats), sizeof(ctd_request), sizeof(ctd_req_status),
+           sizeof(ctd_tune_result));
+    printf("%zu %zu %zu\n", offsetof(ctd_options, shared_launch), offsetof(ctd_source, z1_cm),
+           offsetof(ctd_physics, compton_model));
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_layouts_match_the_binding(tmp_path):
+    # a C99 program built against the header and linked to the library: the host-only
+    # entry points run, and C's struct sizes and offsets are the ones the binding uses
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1109_3266_gb300 import build, ctd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    r = subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), lib, f"-Wl,-rpath,{os.path.dirname(lib)}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    first, sizes, offs = r.stdout.split("\n")[:3]
+    abi, n, w0, wl = first.split()
+    assert int(abi) == ctd.lib().ctd_abi_version() and int(n) == 119
+    lo, hi, w = ctd.ctd_spectrum_kramers(120, 2.5, 1)
+    assert float(w0) == w[0] and float(wl) == w[-1]
+    want = [ctypes.sizeof(t) for t in (ctd.ctd_options, ctd.ctd_material, ctd.ctd_source, ctd.ctd_physics,
+                                       ctd.ctd_run_stats, ctd.ctd_request, ctd.ctd_req_status, ctd.ctd_tune_result)]
+    assert [int(x) for x in sizes.split()] == want
+    assert [int(x) for x in offs.split()] == [ctd.ctd_options.shared_launch.offset, ctd.ctd_source.z1_cm.offset,
+                                              ctd.ctd_physics.compton_model.offset]

@@ -3,16 +3,20 @@
 // Persistent grid.  Warps claim runs of consecutive histories from a global
 // counter, so a warp works on one 1 keV spectrum interval at a time
 // (Sec. 2.2.5).  Each warp keeps a queue of source photons in shared memory,
-// filled 32 at a time by the whole warp (source sampling, Secs. 2.2.5-2.2.6);
+// filled 32 at a time by the whole warp (source sampling, Secs. 2.2.4-2.2.6);
 // a lane whose history has ended takes the next photon from the queue.  A lane
 // then runs up to flight_cap Woodcock flights against mu_max(E) (Sec. 2.1),
 // stopping at a real interaction, which it carries out: photoelectric or
-// Compton deposition into the FP64 tally with L2 atomics, polar angle from the
-// C or R surface (Secs. 2.2.2-2.2.3), rotation.
+// Compton deposition into the FP64 tally as L2 reductions, polar angle from the
+// C or R surface (Secs. 2.2.2-2.2.3), rotation and binary64 renormalisation.
+// Per-step event counts live in registers, the rest of a lane's counts in its
+// shared-memory slot.
 //
-// One kernel template serves one request (its parameters in the kernel's
-// parameter space) and many requests at once (blocks walk through a request
-// table, one request at a time, its descriptor and tables in shared memory).
+// One kernel template, three forms: one request without a fluence map, one
+// request with one (its source path compiled only there), both with the request
+// in the kernel's parameter space; and many requests at once (blocks walk
+// through a request table, one request at a time, its descriptor and tables in
+// shared memory).
 #include "ctd_device.cuh"
 
 namespace ctd {
@@ -487,7 +491,7 @@ __device__ __forceinline__ void load_tables(const RequestDesc &q, int n_e, float
     for (int i = threadIdx.x; i < n_e; i += blockDim.x) s_mm[i] = q.mmax[i];
 }
 
-// Single request (kMulti = false): the request lives in the kernel's parameter
+// Single request (kForm 0 or 1): the request lives in the kernel's parameter
 // space.  Several requests: each block works on one request at a time, a copy
 // of its descriptor, attenuation table and majorant in shared memory, and when
 // that request has no history left to claim the block moves on to the next

@@ -236,3 +236,17 @@ def test_served_admission_by_free_device_memory(ctd):
     rid = ctd.ctd_submit(c, h, 5_000, 0.5, 1)
     assert ctd.ctd_wait(c, rid, 60.0)["state"] == ctd.REQ_DONE
     ctd.ctd_destroy(c)
+
+
+@pytest.mark.parametrize("shape", [dict(threads_per_block=128, blocks_per_sm=7, chunk=64, flight_cap=1),
+                                   dict(threads_per_block=256, blocks_per_sm=3, chunk=1024, flight_cap=8),
+                                   dict(threads_per_block=128, blocks_per_sm=8, chunk=256, flight_cap=2),
+                                   dict(threads_per_block=64, blocks_per_sm=5, chunk=96, flight_cap=3)])
+def test_results_do_not_depend_on_the_launch_shape(ctd, ctx, shape):
+    # every history's random numbers depend only on (seed, history): block shape,
+    # residency, claim size and flight cap change only the order of the tally's additions
+    p = problems()[1]
+    before = alone(ctd, ctx, p)
+    c2 = ctd.ctd_create(device=0, **shape)
+    same(before, alone(ctd, c2, p))
+    ctd.ctd_destroy(c2)

@@ -324,9 +324,10 @@ int ctd_get_tables(ctd_ctx *ctx, ctd_phantom ph, int *n_e, int *n_zeta, int *n_m
 int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e_kev, uint64_t seed,
                   uint64_t n, double *out);
 
-/* Device evaluation of the transport's binary32 logarithm (fn 0: out = ln x)
- * and sincos of 2 pi x (fn 1: out[2i] = cos, out[2i+1] = sin) for n host
- * floats; out holds n (fn 0) or 2n (fn 1) host floats. */
+/* Device evaluation of the transport's binary32 logarithm (fn 0: out = ln x),
+ * sincos of 2 pi x (fn 1: out[2i] = cos, out[2i+1] = sin) and uniform mapping
+ * of a random word (fn 2: the 32 bits of x[i] taken as the word, out = its
+ * uniform in (0, 1)) for n host floats; out holds 2n (fn 1) or n host floats. */
 int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n);
 
 /* Memory-system probes for the roofline of the transport kernel.  The paper has

@@ -155,6 +155,11 @@ void or_eval_log_f32(const float *u, float *out, size_t n)
     for (size_t i = 0; i < n; ++i) out[i] = or_log_f32(u[i]);
 }
 
+void or_eval_uniform_f32(const uint32_t *x, float *out, size_t n)
+{
+    for (size_t i = 0; i < n; ++i) out[i] = or_uniform_f(x[i]);
+}
+
 void or_eval_sincos_f32(const float *t, float *c, float *s, size_t n)
 {
     for (size_t i = 0; i < n; ++i) or_sincos_turns_f32(t[i], &c[i], &s[i]);

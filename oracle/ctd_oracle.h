@@ -117,6 +117,7 @@ float or_log_f32(float u);
 void or_sincos_turns_f32(float t, float *c, float *s);
 void or_eval_log_f32(const float *u, float *out, size_t n);
 void or_eval_sincos_f32(const float *t, float *c, float *s, size_t n);
+void or_eval_uniform_f32(const uint32_t *x, float *out, size_t n);   /* or_uniform in binary32, n words */
 
 /* problem set-up (tables and surfaces) and transport of a history range */
 typedef struct or_setup or_setup;

@@ -83,6 +83,7 @@ def _declare(L):
     L.or_log_f32.argtypes = [C.c_float]
     L.or_eval_log_f32.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_size_t]
     L.or_eval_sincos_f32.argtypes = [C.POINTER(C.c_float)] * 3 + [C.c_size_t]
+    L.or_eval_uniform_f32.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_float), C.c_size_t]
     for n in ("or_setup_create_f64", "or_setup_create_f32"):
         getattr(L, n).restype = P
         getattr(L, n).argtypes = [C.POINTER(OrProblem)]
@@ -165,6 +166,14 @@ def log_f32(u):
     u = np.ascontiguousarray(u, dtype=np.float32)
     out = np.empty_like(u)
     lib().or_eval_log_f32(_ptr(u, C.c_float), _ptr(out, C.c_float), u.size)
+    return out
+
+
+def uniform_f32(x):
+    """The uniform mapping of 32-bit words, as binary32."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    out = np.empty(x.size, dtype=np.float32)
+    lib().or_eval_uniform_f32(_ptr(x, C.c_uint32), _ptr(out, C.c_float), x.size)
     return out
 
 

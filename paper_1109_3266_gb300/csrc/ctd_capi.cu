@@ -191,6 +191,9 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     q.nx = P.nx;
     q.ny = P.ny;
     q.nz = P.nz;
+    q.fnx = static_cast<float>(P.nx);
+    q.fny = static_cast<float>(P.ny);
+    q.fnz = static_cast<float>(P.nz);
     const double hx = static_cast<double>(P.nx) * P.dx / 2.0, hy = static_cast<double>(P.ny) * P.dy / 2.0,
                  hz = static_cast<double>(P.nz) * P.dz / 2.0;
     q.bx0 = static_cast<float>(-hx);
@@ -866,11 +869,11 @@ int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n)
 {
     int rc;
     if ((rc = use_device(ctx))) return rc;
-    if (fn != 0 && fn != 1) return fail(CTD_EINVAL, "fn is 0 (log) or 1 (sincos of 2 pi x)");
+    if (fn < 0 || fn > 2) return fail(CTD_EINVAL, "fn is 0 (log), 1 (sincos of 2 pi x) or 2 (uniform of a word)");
     if (n == 0) return CTD_OK;
     if (!x || !out) return fail(CTD_EINVAL, "null buffer");
     DevBuf<float> bx, bo;
-    const size_t no = fn == 0 ? n : 2 * n;
+    const size_t no = fn == 1 ? 2 * n : n;
     if ((rc = bx.ensure(n)) || (rc = bo.ensure(no))) return rc;
     CK(cudaMemcpyAsync(bx.p, x, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CKS(ctd::launch_eval_math(fn, bx.p, bo.p, n, ctx->stream));

@@ -68,11 +68,12 @@ __device__ __forceinline__ U4 block(uint64_t seed, uint64_t h, uint32_t step, ui
 }
 
 // (2 (x >> 9) + 1) 2^-24: exact in binary32, never 0 or 1.  Built from bits:
-// 1 + k 2^-23 (k = x >> 9 as the significand), minus 1 (exact), plus 2^-24
-// (exact, 2k + 1 < 2^24): the same value without an integer conversion.
+// a = 1 + k 2^-23 (k = x >> 9 as the significand) minus (1 - 2^-24) is
+// (2k + 1) 2^-24 exactly (2k + 1 < 2^24 fits the significand, so the one
+// subtraction does not round): the same value without an integer conversion.
 __device__ __forceinline__ float uni(uint32_t x)
 {
-    return (__uint_as_float((x >> 9) | 0x3f800000u) - 1.0f) + 0x1p-24f;
+    return __uint_as_float((x >> 9) | 0x3f800000u) - 0x1.fffffep-1f;
 }
 
 // ---------------------------------------------------------------- binary32 log and sincos

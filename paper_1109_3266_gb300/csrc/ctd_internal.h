@@ -89,6 +89,7 @@ struct alignas(16) RequestDesc {
     int n_mat;
     int nbins;
     int nx, ny, nz;
+    float fnx, fny, fnz;         // nx, ny, nz as binary32 (the escape test's bounds)
     float bx0, by0, bz0, bx1, by1, bz1;
     float ix, iy, iz;
     int src_kind, n_proj, continuous;

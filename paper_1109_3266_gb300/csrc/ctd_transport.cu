@@ -280,8 +280,7 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     ph.y = ph.y + path * ph.uy;
     ph.z = ph.z + path * ph.uz;
     const float fx = (ph.x - q.bx0) * q.ix, fy = (ph.y - q.by0) * q.iy, fz = (ph.z - q.bz0) * q.iz;
-    if (!(fx >= 0.0f && fx < static_cast<float>(q.nx) && fy >= 0.0f && fy < static_cast<float>(q.ny) &&
-          fz >= 0.0f && fz < static_cast<float>(q.nz))) {
+    if (!(fx >= 0.0f && fx < q.fnx && fy >= 0.0f && fy < q.fny && fz >= 0.0f && fz < q.fnz)) {
         cnt.event(kCntEscaped);
         cnt.escaped(ph.e);
         return kEnded;
@@ -582,6 +581,8 @@ __global__ void eval_math_kernel(int fn, const float *x, float *out, size_t n)
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
         if (fn == 0) {
             out[i] = log32(x[i]);
+        } else if (fn == 2) {
+            out[i] = uni(__float_as_uint(x[i]));
         } else {
             float c, s;
             sincos_turns(x[i], c, s);

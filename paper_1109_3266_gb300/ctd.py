@@ -305,7 +305,7 @@ def ctd_sample_mu(ctx, ph, kind, material, e_kev, seed, n):
 
 def ctd_eval_math(ctx, fn, x):
     x = np.ascontiguousarray(x, dtype=np.float32)
-    out = np.empty(x.size * (1 if fn == 0 else 2), dtype=np.float32)
+    out = np.empty(x.size * (2 if fn == 1 else 1), dtype=np.float32)
     _check(lib().ctd_eval_math(ctx, fn, x.ctypes.data_as(C.POINTER(C.c_float)),
                                out.ctypes.data_as(C.POINTER(C.c_float)), x.size))
     return out

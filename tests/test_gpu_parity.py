@@ -69,6 +69,15 @@ def test_device_log_and_sincos_equal_oracle_on_every_uniform(ctd, ctx, oracle):
     assert np.array_equal(dev[:, 1].view(np.uint32), s.view(np.uint32))
 
 
+def test_device_uniform_mapping_equals_oracle_on_every_significand(ctd, ctx, oracle):
+    # every 23-bit significand k = x >> 9, with random low bits below it
+    k = np.arange(2 ** 23, dtype=np.uint32)
+    low = np.random.default_rng(11).integers(0, 512, k.size, dtype=np.uint32)
+    words = (k << np.uint32(9)) | low
+    dev = ctd.ctd_eval_math(ctx, 2, words.view(np.float32))
+    assert np.array_equal(dev.view(np.uint32), oracle.uniform_f32(words).view(np.uint32))
+
+
 # ----------------------------------------------------------------- tables
 @pytest.mark.parametrize("make", [lambda: I.tiny_water(1000), lambda: small_head(1000)])
 def test_tables_and_surfaces_equal_oracle_bitwise(ctd, ctx, oracle, make):

@@ -36,6 +36,20 @@ def test_uniform_grid_is_exact_and_open(oracle):
     assert np.all(k == (xs >> np.uint64(9)).astype(np.float64))
 
 
+def test_uniform_binary32_forms(oracle):
+    # the binary32 mapping equals the binary64 definition; and the one-subtraction
+    # construction from bits, (1 + k 2^-23) - (1 - 2^-24) in binary32, is exact for
+    # every significand k (2k + 1 < 2^24 fits), so it gives the same grid
+    xs = np.random.default_rng(1).integers(0, 2 ** 32, 20000, dtype=np.uint64)
+    f = oracle.uniform_f32(xs.astype(np.uint32))
+    assert np.array_equal(f.astype(np.float64), np.array([oracle.uniform(int(x)) for x in xs]))
+    k = np.arange(2 ** 23, dtype=np.uint32)
+    a = (k | np.uint32(0x3F800000)).view(np.float32)
+    one_sub = a - np.float32(1.0 - 2.0 ** -24)
+    assert one_sub.dtype == np.float32
+    assert np.array_equal(one_sub, oracle.uniform_f32(k << np.uint32(9)))
+
+
 def test_philox_uniforms_are_uniform(oracle):
     # a million uniforms from consecutive counters: mean, variance, 64-bin chi-square
     n = 250000

@@ -80,6 +80,13 @@ int build_tables(ctd_ctx *ctx, Phantom &P)
     P.h_tab.assign(static_cast<size_t>(nm) * n_e * 4, 0.0f);
     for (size_t i = 0; i < static_cast<size_t>(nm) * n_e; ++i)
         for (int c = 0; c < 3; ++c) P.h_tab[i * 4 + c] = static_cast<float>(cum[i * 3 + c]);
+    // fourth column: c3 at the next node minus c3 here, the binary32 difference the
+    // interpolation of the total share takes (0 at the last node)
+    for (int m = 0; m < nm; ++m)
+        for (int j = 0; j + 1 < n_e; ++j) {
+            const size_t i = static_cast<size_t>(m) * n_e + j;
+            P.h_tab[i * 4 + 3] = P.h_tab[(i + 1) * 4 + 2] - P.h_tab[i * 4 + 2];
+        }
     P.h_mm.resize(n_e);
     for (int j = 0; j < n_e; ++j) P.h_mm[j] = static_cast<float>(mmax[j]);
     const size_t row = static_cast<size_t>(n_e) * ph.n_zeta;

@@ -70,7 +70,7 @@ enum { kCntPe = 0, kCntCompton, kCntRayleigh, kCntFict, kCntEscaped, kCntMissed,
 struct alignas(16) RequestDesc {
     const uint8_t *mat;          // [nvox] material of the phantom
     const float *rho;            // [nvox] g/cm^3
-    const float *tab;            // [n_mat][n_e][4]: c1, c2, c3, 0 (cm^2/g)
+    const float *tab;            // [n_mat][n_e][4]: c1, c2, c3 (cm^2/g), c3[j+1] - c3[j] in binary32
     const float *mmax;           // [n_e] majorant mu_max(E), 1/cm
     const float *rsurf;          // [n_mat][n_e][n_zeta] R surfaces
     const float *csurf;          // [n_c][n_e][n_zeta] C surfaces, material m at m * cs_stride

@@ -291,16 +291,19 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
                               static_cast<uint32_t>(q.ny) * static_cast<uint32_t>(static_cast<int>(fz)));
     const int m = __ldg(&q.mat[idx]);
     const float rho = __ldg(&q.rho[idx]);
-    const float4 A = s_tab[m * n_e + j], B = s_tab[m * n_e + j + 1];
     // interaction type with probabilities mu_i / mu_max: fictitious when u1 is at or
-    // above the total share; otherwise the first cumulative share above u1
+    // above the total share; otherwise the first cumulative share above u1.  The
+    // table's fourth column is the total share's node difference, so a fictitious
+    // step reads one node; a real one reads the next node's c1 and c2 as well.
+    const float4 A = s_tab[m * n_e + j];
     const float y = uni(b.y);
     const float sr = rho * imax;
-    const float c3 = A.z + te * (B.z - A.z);
+    const float c3 = A.z + te * A.w;
     if (!(y < sr * c3)) {
         cnt.event(kCntFict);
         return kFictitious;
     }
+    const float2 B = *reinterpret_cast<const float2 *>(&s_tab[m * n_e + j + 1]);
     const float c1 = A.x + te * (B.x - A.x);
     const float c2 = A.y + te * (B.y - A.y);
     int type;

@@ -25,7 +25,8 @@ namespace {
 using namespace dev;
 
 struct Photon {
-    float x, y, z, ux, uy, uz, e;
+    float x, y, z;    // position in voxel units: (r - box origin) / voxel size per axis
+    float ux, uy, uz, e;
     uint64_t h;
     uint32_t step;
     int j;            // energy node of e, its fraction and 1 / the majorant there;
@@ -237,9 +238,9 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
         return false;
     }
     if (tn < 0.0f) tn = 0.0f;
-    ph.x = rx + tn * ux;
-    ph.y = ry + tn * uy;
-    ph.z = rz + tn * uz;
+    ph.x = ((rx + tn * ux) - q.bx0) * q.ix;
+    ph.y = ((ry + tn * uy) - q.by0) * q.iy;
+    ph.z = ((rz + tn * uz) - q.bz0) * q.iz;
     ph.ux = ux;
     ph.uy = uy;
     ph.uz = uz;
@@ -276,10 +277,11 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     const int j = ph.j;
     const float te = ph.te, imax = ph.imax;
     const float path = (-log32(uni(b.x))) * imax;
-    ph.x = ph.x + path * ph.ux;
-    ph.y = ph.y + path * ph.uy;
-    ph.z = ph.z + path * ph.uz;
-    const float fx = (ph.x - q.bx0) * q.ix, fy = (ph.y - q.by0) * q.iy, fz = (ph.z - q.bz0) * q.iz;
+    // the move in voxel units: each displacement s u_k times 1/d_k, added fused
+    ph.x = __fmaf_rn(path * ph.ux, q.ix, ph.x);
+    ph.y = __fmaf_rn(path * ph.uy, q.iy, ph.y);
+    ph.z = __fmaf_rn(path * ph.uz, q.iz, ph.z);
+    const float fx = ph.x, fy = ph.y, fz = ph.z;
     if (!(fx >= 0.0f && fx < q.fnx && fy >= 0.0f && fy < q.fny && fz >= 0.0f && fz < q.fnz)) {
         cnt.event(kCntEscaped);
         cnt.escaped(ph.e);

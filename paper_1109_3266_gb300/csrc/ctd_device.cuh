@@ -241,9 +241,9 @@ __device__ __forceinline__ float surface(const float *__restrict__ S, int n_zeta
     const float *r0 = S + static_cast<size_t>(j) * n_zeta + i;
     const float *r1 = r0 + n_zeta;
     const float a0 = __ldg(r0), a1 = __ldg(r0 + 1), b0 = __ldg(r1), b1 = __ldg(r1 + 1);
-    const float lo = a0 + a * (a1 - a0);
-    const float hi = b0 + a * (b1 - b0);
-    float mu = lo + te * (hi - lo);
+    const float lo = __fmaf_rn(a, a1 - a0, a0);
+    const float hi = __fmaf_rn(a, b1 - b0, b0);
+    float mu = __fmaf_rn(te, hi - lo, lo);
     if (mu > 1.0f) mu = 1.0f;
     if (mu < -1.0f) mu = -1.0f;
     return mu;

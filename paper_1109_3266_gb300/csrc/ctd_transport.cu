@@ -49,7 +49,7 @@ __device__ __forceinline__ void set_energy(Photon &ph, const SharedTables &sh, c
 {
     ph.j = enode(ph.e, sh.e_min, sh.n_e, ph.te);
     const float m0 = s_mm[ph.j], m1 = s_mm[ph.j + 1];
-    ph.imax = 1.0f / (m0 + ph.te * (m1 - m0));
+    ph.imax = 1.0f / __fmaf_rn(ph.te, m1 - m0, m0);
 }
 
 // A lane's once-per-history event counts, energy totals and the real
@@ -158,7 +158,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     while (bin < q.nbins - 1 && __ldg(&q.pref[bin + 1]) <= local) ++bin;
     const U4 b0 = draw<kKeys>(q, h, 0, kStreamSource);
     const float elo = __ldg(&q.bin_lo[bin]), ehi = __ldg(&q.bin_hi[bin]);
-    const float e = elo + (ehi - elo) * uni(b0.x);
+    const float e = __fmaf_rn(ehi - elo, uni(b0.x), elo);
     cnt.emitted(e);
     float cb = 1.0f, sb = 0.0f, zs = 0.0f;
     if (q.src_kind == CTD_SRC_ARC) {
@@ -300,14 +300,14 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     const float4 A = s_tab[m * n_e + j];
     const float y = uni(b.y);
     const float sr = rho * imax;
-    const float c3 = A.z + te * A.w;
+    const float c3 = __fmaf_rn(te, A.w, A.z);
     if (!(y < sr * c3)) {
         cnt.event(kCntFict);
         return kFictitious;
     }
     const float2 B = *reinterpret_cast<const float2 *>(&s_tab[m * n_e + j + 1]);
-    const float c1 = A.x + te * (B.x - A.x);
-    const float c2 = A.y + te * (B.y - A.y);
+    const float c1 = __fmaf_rn(te, B.x - A.x, A.x);
+    const float c2 = __fmaf_rn(te, B.y - A.y, A.y);
     int type;
     if (y < sr * c1) type = 0;
     else if (y < sr * c2) type = 1;

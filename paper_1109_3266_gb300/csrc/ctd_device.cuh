@@ -196,12 +196,12 @@ __device__ __forceinline__ void deposit(double *tally, size_t idx, float e)
 // New direction after a scatter of polar cosine mu and azimuth 2 pi tphi.
 __device__ __forceinline__ void rotate(float &ux, float &uy, float &uz, float mu, float tphi)
 {
-    float st2 = 1.0f - mu * mu;
+    float st2 = __fmaf_rn(-mu, mu, 1.0f);
     if (st2 < 0.0f) st2 = 0.0f;
     const float st = sqrtf(st2);
     float cp, sp;
     sincos_turns(tphi, cp, sp);
-    const float a2 = ux * ux + uy * uy;
+    const float a2 = __fmaf_rn(ux, ux, uy * uy);
     float nx, ny, nz;
     if (a2 < static_cast<float>(1e-12)) {
         nx = st * cp;
@@ -210,9 +210,9 @@ __device__ __forceinline__ void rotate(float &ux, float &uy, float &uz, float mu
     } else {
         const float a = sqrtf(a2);
         const float rr = st / a;
-        nx = ux * mu + rr * ((ux * uz) * cp - uy * sp);
-        ny = uy * mu + rr * ((uy * uz) * cp + ux * sp);
-        nz = uz * mu - (a * st) * cp;
+        nx = __fmaf_rn(rr, __fmaf_rn(ux * uz, cp, -(uy * sp)), ux * mu);
+        ny = __fmaf_rn(rr, __fmaf_rn(uy * uz, cp, ux * sp), uy * mu);
+        nz = __fmaf_rn(-(a * st), cp, uz * mu);
     }
     ux = nx;
     uy = ny;

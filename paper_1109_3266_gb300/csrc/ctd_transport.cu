@@ -163,8 +163,8 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     float cb = 1.0f, sb = 0.0f, zs = 0.0f;
     if (q.src_kind == CTD_SRC_ARC) {
         if (q.continuous) {
-            sincos_turns(q.a0t + q.awt * uni(b0.y), cb, sb);
-            zs = q.hz0 + q.hdz * uni(b0.y);
+            sincos_turns(__fmaf_rn(q.awt, uni(b0.y), q.a0t), cb, sb);
+            zs = __fmaf_rn(q.hdz, uni(b0.y), q.hz0);
         } else {
             const uint32_t k =
                 static_cast<uint32_t>((static_cast<uint64_t>(b0.y) * static_cast<uint64_t>(q.n_proj)) >> 32);
@@ -185,16 +185,16 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
         const uint32_t beam = b.y < __ldg(&q.fl_thr[k]) ? k : static_cast<uint32_t>(__ldg(&q.fl_alias[k]));
         const uint32_t iv = static_cast<uint32_t>((static_cast<uint64_t>(beam) * q.fl_magic) >> 40);
         const uint32_t iu = beam - iv * static_cast<uint32_t>(q.fl_nu);
-        uu = q.ulo + q.fl_du * (static_cast<float>(iu) + uni(b.z));
-        vv = q.vlo + q.fl_dv * (static_cast<float>(iv) + uni(b.w));
-        qq = (D2 + uu * uu) + vv * vv;
+        uu = __fmaf_rn(q.fl_du, static_cast<float>(iu) + uni(b.z), q.ulo);
+        vv = __fmaf_rn(q.fl_dv, static_cast<float>(iv) + uni(b.w), q.vlo);
+        qq = __fmaf_rn(vv, vv, __fmaf_rn(uu, uu, D2));
         accepted = true;
     }
     for (uint32_t t = 1; t <= kMaxTrials && !accepted; ++t) {
         const U4 b = draw<kKeys>(q, h, t, kStreamSource);
-        uu = q.ulo + q.uw * uni(b.x);
-        vv = q.vlo + q.vw * uni(b.y);
-        qq = (D2 + uu * uu) + vv * vv;
+        uu = __fmaf_rn(q.uw, uni(b.x), q.ulo);
+        vv = __fmaf_rn(q.vw, uni(b.y), q.vlo);
+        qq = __fmaf_rn(vv, vv, __fmaf_rn(uu, uu, D2));
         const float c2 = D2 / qq;
         const float acc = c2 * sqrtf(c2);
         if (uni(b.z) < acc) {
@@ -210,8 +210,8 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     const float inv = 1.0f / sqrtf(qq);
     float ux, uy, uz, rx, ry, rz;
     if (q.src_kind == CTD_SRC_ARC) {
-        ux = (uu * cb - D * sb) * inv;
-        uy = ((-uu) * sb - D * cb) * inv;
+        ux = __fmaf_rn(uu, cb, -(D * sb)) * inv;
+        uy = __fmaf_rn(-uu, sb, -(D * cb)) * inv;
         uz = vv * inv;
         rx = D * sb;
         ry = D * cb;
@@ -226,10 +226,11 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     }
     // (the source direction is normalised in binary32; binary64 renormalisation
     // is for the directions made by scatters)
-    // entry into the box (slab method); outside is vacuum
-    const float t0x = (q.bx0 - rx) / ux, t1x = (q.bx1 - rx) / ux;
-    const float t0y = (q.by0 - ry) / uy, t1y = (q.by1 - ry) / uy;
-    const float t0z = (q.bz0 - rz) / uz, t1z = (q.bz1 - rz) / uz;
+    // entry into the box (slab method, with the direction's reciprocals); outside is vacuum
+    const float iux = 1.0f / ux, iuy = 1.0f / uy, iuz = 1.0f / uz;
+    const float t0x = (q.bx0 - rx) * iux, t1x = (q.bx1 - rx) * iux;
+    const float t0y = (q.by0 - ry) * iuy, t1y = (q.by1 - ry) * iuy;
+    const float t0z = (q.bz0 - rz) * iuz, t1z = (q.bz1 - rz) * iuz;
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
     const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
     if (!(tn < tf) || !(tf > 0.0f)) {
@@ -238,9 +239,11 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
         return false;
     }
     if (tn < 0.0f) tn = 0.0f;
-    ph.x = ((rx + tn * ux) - q.bx0) * q.ix;
-    ph.y = ((ry + tn * uy) - q.by0) * q.iy;
-    ph.z = ((rz + tn * uz) - q.bz0) * q.iz;
+    // the entry point in voxel units, clamped into the box (it lies on the box's
+    // surface; rounding can leave it just outside): [0, the number below n]
+    ph.x = fminf(fmaxf((__fmaf_rn(tn, ux, rx) - q.bx0) * q.ix, 0.0f), __uint_as_float(__float_as_uint(q.fnx) - 1u));
+    ph.y = fminf(fmaxf((__fmaf_rn(tn, uy, ry) - q.by0) * q.iy, 0.0f), __uint_as_float(__float_as_uint(q.fny) - 1u));
+    ph.z = fminf(fmaxf((__fmaf_rn(tn, uz, rz) - q.bz0) * q.iz, 0.0f), __uint_as_float(__float_as_uint(q.fnz) - 1u));
     ph.ux = ux;
     ph.uy = uy;
     ph.uz = uz;
@@ -338,7 +341,7 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
         // Compton: E' = E / (1 + (E/mc^2)(1 - mu)), the electron gets E - E'
         cnt.event(kCntCompton);
         const float k = ph.e * static_cast<float>(1.0 / kMec2);
-        const float ep = ph.e / (1.0f + k * (1.0f - mu));
+        const float ep = ph.e / __fmaf_rn(k, 1.0f - mu, 1.0f);
         if (ep < static_cast<float>(sh.e_min)) {
             cnt.event(kCntCutoff);
             deposit(q.tally, hit.idx, ph.e);

@@ -285,7 +285,13 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     ph.y = __fmaf_rn(path * ph.uy, q.iy, ph.y);
     ph.z = __fmaf_rn(path * ph.uz, q.iz, ph.z);
     const float fx = ph.x, fy = ph.y, fz = ph.z;
-    if (!(fx >= 0.0f && fx < q.fnx && fy >= 0.0f && fy < q.fny && fz >= 0.0f && fz < q.fnz)) {
+    // 0 <= f < n on each axis, as one unsigned compare of the bit patterns: for
+    // floats other than -0 it is the same test (negative floats and NaNs have the
+    // sign bit or an all-ones exponent, so larger patterns than n), and a position
+    // is never -0 (the entry point is clamped to +0 at least, and adding a nonzero
+    // or +0 displacement to a value other than -0 never gives -0)
+    if (!(__float_as_uint(fx) < __float_as_uint(q.fnx) && __float_as_uint(fy) < __float_as_uint(q.fny) &&
+          __float_as_uint(fz) < __float_as_uint(q.fnz))) {
         cnt.event(kCntEscaped);
         cnt.escaped(ph.e);
         return kEnded;

@@ -55,8 +55,9 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload(name, compton="kn"):
-    """The named workload; compton "wh" switches it to the Waller-Hartree model."""
+def workload(name, compton="kn", rayleigh="gauss"):
+    """The named workload; compton "wh" switches it to the Waller-Hartree model,
+    rayleigh "iaa" to the independent-atom form factor of its materials' elements."""
     import dataclasses
 
     from paper_1109_3266_gb300 import inputs as I
@@ -65,8 +66,8 @@ def workload(name, compton="kn"):
     if name not in makers:
         raise SystemExit(f"unknown workload {name}")
     p = makers[name]()
-    if compton != "kn":
-        p = I.scaled(p, physics=dataclasses.replace(p.physics, compton=compton))
+    if compton != "kn" or rayleigh != "gauss":
+        p = I.scaled(p, physics=dataclasses.replace(p.physics, compton=compton, rayleigh=rayleigh))
     return p
 
 
@@ -219,7 +220,7 @@ def run_reference(args):
     rank, world = dist_init(args.gpus)
     if rank != 0:
         return
-    p = workload(args.workload, args.compton)
+    p = workload(args.workload, args.compton, args.rayleigh)
     threads = cpu_cores()
     for _ in range(args.warmup):
         oracle_rate(p, 0.5, threads)
@@ -235,7 +236,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ns[0] / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": p.name, "histories_per_step": ns[0], "compton": args.compton},
+        "config": {"workload": p.name, "histories_per_step": ns[0], "compton": args.compton,
+                   "rayleigh": args.rayleigh},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -252,7 +254,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    p = workload(args.workload, args.compton)
+    p = workload(args.workload, args.compton, args.rayleigh)
     seed = p.seed + 7919 * rank
     nvox = p.phantom.nvox
     ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
@@ -351,7 +353,7 @@ def run_ours(args):
     mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = SM_COUNT * LANES_PER_SM_CLK * mhz * 1e6 / 1e12        # tera lane-instructions / s
     # the lane-instruction count was measured for the Klein-Nishina model
-    prof = KERNEL_PROFILE.get(p.name, {}) if args.compton == "kn" else {}
+    prof = KERNEL_PROFILE.get(p.name, {}) if args.compton == "kn" and args.rayleigh == "gauss" else {}
     inst_per_hist = args.inst_per_history or prof.get("lane_inst_per_history")
     achieved = p.n_hist * args.steps * inst_per_hist / t_transport / 1e12 if inst_per_hist else None
     traffic = args.traffic_per_launch or prof.get("dram_bytes_per_launch")
@@ -406,7 +408,7 @@ def run_ours(args):
                        "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (256 MB write outside timed events)",
                        "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk,
-                       "flight_cap": args.flight_cap, "compton": args.compton},
+                       "flight_cap": args.flight_cap, "compton": args.compton, "rayleigh": args.rayleigh},
             "sec_to_1pct_avg_rsd": measured_1["seconds"] if measured_1 else sec_to_1,
             "sec_to_1pct_avg_rsd_extrapolated": sec_to_1, "rsd_stopped_run": measured_1,
             "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
@@ -567,6 +569,8 @@ def main():
                     help="served form: histories one round may hold before admission stops (0: 1e8)")
     ap.add_argument("--compton", default="kn", choices=["kn", "wh"],
                     help="Compton model: free-electron Klein-Nishina or Waller-Hartree")
+    ap.add_argument("--rayleigh", default="gauss", choices=["gauss", "iaa"],
+                    help="Rayleigh form factor: analytic exp(-q^2/q0^2) or independent-atom of the elements")
     ap.add_argument("--hist-lo", type=float, default=1e7)
     ap.add_argument("--hist-hi", type=float, default=1e9)
     ap.add_argument("--traffic-per-launch", type=float, default=None)

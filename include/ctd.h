@@ -26,6 +26,9 @@ extern "C" {
 
 #define CTD_ABI_VERSION 7
 
+/* largest number of elements of one material's formula unit (ctd_set_material_elements) */
+#define CTD_MAX_ELEMENTS 16
+
 typedef enum {
     CTD_OK = 0,
     CTD_EINVAL = 1,       /* an argument is out of range or inconsistent   */
@@ -159,6 +162,23 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
                        ctd_phantom *out);
 int ctd_destroy_phantom(ctd_ctx *ctx, ctd_phantom ph);
 int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys);
+
+/* Independent-atom (IAA) molecular form factor for Rayleigh scattering in
+ * material `material` of phantom ph (Sec. 2.2.2, Eq. 1).  The paper takes F^2
+ * from tables; the reading here: each element is a screened hydrogenic atom,
+ * F_Z(x) = Z / (1 + (2 pi a_Z x)^2)^2 with the Thomas-Fermi radius
+ * a_Z = 0.88534138 a0 Z^(-1/3) (a0 = 0.529177210903 Angstrom) and
+ * x = sin(theta/2)/lambda, and a formula unit's F^2 is sum_i count[i] F_Z[i]^2
+ * (independent atoms, no interference).  With n_el > 0 the material's Rayleigh
+ * total becomes pi r0^2 times the integral over mu of (1 + mu^2) F^2 (composite
+ * Simpson, 20000 intervals), divided by a_mol for cm^2/g, and its R surface is
+ * built from the same density; n_el = 0 restores F^2 = exp(-q^2/q0^2) and the
+ * closed-form total.  z: n_el atomic numbers in 1..100; count: atoms per formula
+ * unit, finite and > 0; both read during the call.  1 <= n_el <= CTD_MAX_ELEMENTS
+ * or 0.  Errors: CTD_ENOTFOUND (phantom), CTD_EINVAL (index or values),
+ * CTD_EBUSY (phantom in use by a served request). */
+int ctd_set_material_elements(ctd_ctx *ctx, ctd_phantom ph, int material, int n_el, const int *z,
+                              const double *count);
 int ctd_set_source(ctd_ctx *ctx, ctd_phantom ph, const ctd_source *src);
 
 /* Fluence map (Sec. 2.2.4): n_u x n_v beamlets tiling the source's field

@@ -12,7 +12,10 @@
  *   - photoelectric per formula unit 1e-2 Z^4 / E_MeV^3 in microbarn,
  *     Rayleigh per formula unit 1.565e-5 Z^2 / E_MeV^2 in barn, Compton
  *     = free-electron Klein-Nishina total per electron times electrons per gram;
- *   - Rayleigh form factor F^2(q^2) ~ exp(-q^2 / q0^2) (or 1, Thomson);
+ *   - Rayleigh form factor F^2(q^2) ~ exp(-q^2 / q0^2) (or 1, Thomson), or the
+ *     independent-atom molecular form factor sum_i n_i F_Zi^2 with a screened
+ *     hydrogenic atom per element (Thomas-Fermi radius), whose Rayleigh total is
+ *     then the integral of Eq. 1 by composite Simpson;
  *   - Waller-Hartree Compton (Eq. 2 with S(q)): S(q)/Z = 1 - exp(-q^2 / sq0^2)
  *     with q^2 = 2 k^2 (1 - cos theta), k = E / hc, the same momentum transfer as
  *     the form factor; its total is the integral of Eq. 2 by composite Simpson;
@@ -40,6 +43,8 @@
 #define OR_MAX_TRIALS 1000         /* rejection loops give up after this    */
 #define OR_MAX_TRIALS_WH (1u << 20) /* Waller-Hartree keeps about a(1-mu) of KN draws at low E */
 #define OR_MAX_STEPS 100000000u    /* Woodcock steps per history            */
+#define OR_BOHR 0.529177210903     /* Bohr radius, Angstrom                 */
+#define OR_TF 0.88534138           /* Thomas-Fermi radius / (a0 Z^-1/3): (3 pi / 4)^(2/3) / 2 */
 
 enum { OR_STREAM_TRANSPORT = 0, OR_STREAM_SOURCE = 1, OR_STREAM_EXACT = 2, OR_STREAM_SAMPLER = 3, OR_STREAM_MH = 4 };
 
@@ -240,6 +245,77 @@ double or_mu_compton_wh(const or_material *m, double e_kev)
     return (OR_NA * m->z_over_a) * or_sigma_wh(e_kev, m->sq0);
 }
 
+/* Independent-atom Rayleigh form factor.  A screened hydrogenic atom, electron
+ * density Z exp(-2 r / a) / (pi a^3), has the form factor F(Q) = Z / (1 + (Q a/2)^2)^2
+ * at momentum transfer Q = 4 pi x, x = sin(theta/2) / lambda; the screening length
+ * is the Thomas-Fermi radius a = 0.8853 a0 Z^(-1/3).  So F^2 = Z^2 / (1 + c x^2)^4
+ * with c = (2 pi a)^2.  The molecule's F^2 is the sum over its atoms (no
+ * interference between them). */
+static double or_ff_width(int z)
+{
+    double a = (OR_TF * OR_BOHR) / cbrt((double)z);
+    double w = (2.0 * OR_PI) * a;
+    return w * w;
+}
+
+static double or_ff_z2(double z, double c, double x2)
+{
+    double g = 1.0 / (1.0 + c * x2);
+    double f = z * (g * g);
+    return f * f;
+}
+
+double or_ff_atom2(int z, double x2)
+{
+    return or_ff_z2((double)z, or_ff_width(z), x2);
+}
+
+/* F^2_mol from the elements' widths c[i] */
+static double or_ff_sum2(const or_material *m, const double *c, double x2)
+{
+    double s = 0.0;
+    for (int i = 0; i < m->n_el; ++i) s += m->el_n[i] * or_ff_z2((double)m->el_z[i], c[i], x2);
+    return s;
+}
+
+double or_ff_mol2(const or_material *m, double x2)
+{
+    double c[OR_MAX_ELEMENTS];
+    for (int i = 0; i < m->n_el; ++i) c[i] = or_ff_width(m->el_z[i]);
+    return or_ff_sum2(m, c, x2);
+}
+
+/* Eq. 1 up to r0^2/2: (1 + mu^2) F^2_mol(x), x^2 = k^2 (1 - mu) / 2, k = E/hc in 1/Angstrom */
+static double or_pdf_rayleigh_iaa(const or_material *m, const double *c, double kr, double mu)
+{
+    double x2 = ((kr * kr) * (1.0 - mu)) * 0.5;
+    return (1.0 + mu * mu) * or_ff_sum2(m, c, x2);
+}
+
+double or_sigma_rayleigh_iaa(const or_material *m, double e_kev)
+{
+    const int M = OR_CDF_POINTS;
+    double kr = e_kev / OR_HC;
+    double c[OR_MAX_ELEMENTS];
+    for (int i = 0; i < m->n_el; ++i) c[i] = or_ff_width(m->el_z[i]);
+    /* Simpson weights 1, 4, 2, ..., 4, 1 on mu_n = (2n - M)/M, h = 2/M */
+    double odd = 0.0, even = 0.0;
+    for (int n = 1; n < M; ++n) {
+        double mu = (double)(2 * n - M) / (double)M;
+        if (n & 1) odd += or_pdf_rayleigh_iaa(m, c, kr, mu);
+        else even += or_pdf_rayleigh_iaa(m, c, kr, mu);
+    }
+    double ends = or_pdf_rayleigh_iaa(m, c, kr, -1.0) + or_pdf_rayleigh_iaa(m, c, kr, 1.0);
+    double integral = ((2.0 / (double)M) / 3.0) * (ends + (4.0 * odd + 2.0 * even));
+    /* dsigma/dOmega = (r0^2/2) (1 + mu^2) F^2, dOmega = 2 pi dmu */
+    return (OR_PI * OR_R0 * OR_R0) * integral;
+}
+
+double or_mu_rayleigh_iaa(const or_material *m, double e_kev)
+{
+    return (or_sigma_rayleigh_iaa(m, e_kev) * OR_NA) / m->a_mol;
+}
+
 /* ===================================================================== */
 /* Largest-remainder allocation of n histories to spectrum bins           */
 /* (Sec. 2.2.5: histories distributed to 1 keV intervals by the spectrum). */
@@ -327,12 +403,16 @@ static void or_invert_row(const double *cdf, int n_zeta, double *row)
 }
 
 /* kind 0: Klein-Nishina C surface; 1: Rayleigh R surface of width q0;
- * 2: Waller-Hartree C surface of scattering-function width q0 */
-static void or_build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out)
+ * 2: Waller-Hartree C surface of scattering-function width q0;
+ * 3: Rayleigh R surface with the independent-atom form factor of material m */
+static void or_build_surface(int kind, double q0, const or_material *m, int e_min, int n_e, int n_zeta, double *out)
 {
     const int M = OR_CDF_POINTS;
     double *pdf = (double *)malloc(sizeof(double) * (size_t)(M + 1));
     double *cdf = (double *)malloc(sizeof(double) * (size_t)(M + 1));
+    double c[OR_MAX_ELEMENTS];
+    if (kind == 3)
+        for (int i = 0; i < m->n_el; ++i) c[i] = or_ff_width(m->el_z[i]);
     for (int j = 0; j < n_e; ++j) {
         double e = (double)(e_min + j);
         double k = e / OR_MEC2;
@@ -340,7 +420,10 @@ static void or_build_surface(int kind, double q0, int e_min, int n_e, int n_zeta
         double a = q0 > 0.0 ? (2.0 * kr * kr) / (q0 * q0) : 0.0;
         for (int n = 0; n <= M; ++n) {
             double mu = (double)(2 * n - M) / (double)M;
-            pdf[n] = kind == 0 ? or_pdf_kn(k, mu) : kind == 1 ? or_pdf_rayleigh(a, mu) : or_pdf_wh(k, a, mu);
+            pdf[n] = kind == 0   ? or_pdf_kn(k, mu)
+                     : kind == 1 ? or_pdf_rayleigh(a, mu)
+                     : kind == 2 ? or_pdf_wh(k, a, mu)
+                                 : or_pdf_rayleigh_iaa(m, c, kr, mu);
         }
         cdf[0] = 0.0;
         for (int n = 1; n <= M; ++n) cdf[n] = cdf[n - 1] + (pdf[n - 1] + pdf[n]);
@@ -352,17 +435,22 @@ static void or_build_surface(int kind, double q0, int e_min, int n_e, int n_zeta
 
 void or_build_kn_surface(int e_min, int n_e, int n_zeta, double *out)
 {
-    or_build_surface(0, 0.0, e_min, n_e, n_zeta, out);
+    or_build_surface(0, 0.0, NULL, e_min, n_e, n_zeta, out);
 }
 
 void or_build_rayleigh_surface(double q0, int e_min, int n_e, int n_zeta, double *out)
 {
-    or_build_surface(1, q0, e_min, n_e, n_zeta, out);
+    or_build_surface(1, q0, NULL, e_min, n_e, n_zeta, out);
 }
 
 void or_build_wh_surface(double sq0, int e_min, int n_e, int n_zeta, double *out)
 {
-    or_build_surface(2, sq0, e_min, n_e, n_zeta, out);
+    or_build_surface(2, sq0, NULL, e_min, n_e, n_zeta, out);
+}
+
+void or_build_rayleigh_iaa_surface(const or_material *m, int e_min, int n_e, int n_zeta, double *out)
+{
+    or_build_surface(3, 0.0, m, e_min, n_e, n_zeta, out);
 }
 
 /* ===================================================================== */
@@ -515,7 +603,7 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
             double e = (double)(p->e_min + j);
             double pe = or_mu_pe(&p->mats[m], e);
             double c = p->compton == OR_COMPTON_WH ? or_mu_compton_wh(&p->mats[m], e) : or_mu_compton(&p->mats[m], e);
-            double r = or_mu_rayleigh(&p->mats[m], e);
+            double r = p->mats[m].n_el > 0 ? or_mu_rayleigh_iaa(&p->mats[m], e) : or_mu_rayleigh(&p->mats[m], e);
             size_t o = ((size_t)m * n_e + j) * 3;
             s->tab64[o + 0] = pe;
             s->tab64[o + 1] = pe + c;
@@ -546,7 +634,8 @@ static or_setup *or_setup_create(const or_problem *p, int prec)
     for (size_t i = 0; i < (size_t)s->n_cs * n_e * nz; ++i) s->cs32[i] = (float)s->cs64[i];
     for (int m = 0; m < nm; ++m) {
         double *dst = s->rs64 + (size_t)m * n_e * nz;
-        or_build_rayleigh_surface(p->mats[m].q0, p->e_min, n_e, nz, dst);
+        if (p->mats[m].n_el > 0) or_build_rayleigh_iaa_surface(&p->mats[m], p->e_min, n_e, nz, dst);
+        else or_build_rayleigh_surface(p->mats[m].q0, p->e_min, n_e, nz, dst);
         for (size_t i = 0; i < (size_t)n_e * nz; ++i) s->rs32[(size_t)m * n_e * nz + i] = (float)dst[i];
     }
     /* batches (Sec. 2.2.1) and the stratified allocation inside each (Sec. 2.2.5) */
@@ -712,6 +801,40 @@ static double or_exact_rayleigh(double q0, double e_kev, uint64_t seed, uint64_t
             mu = 2.0 * z - 1.0;
         }
         if (mu < -1.0) mu = -1.0;
+        if (r <= 0.5 * (1.0 + mu * mu)) { *ok = 1; return mu; }
+    }
+    *ok = 0;
+    return 1.0;
+}
+
+/* Independent-atom Rayleigh: s = x^2 on [0, k^2] drawn from sum_i n_i Z_i^2 /
+ * (1 + c_i s)^4 (an element with probability equal to its share of the integral,
+ * then s by inverting (1 + c s)^-3), kept with probability (1 + mu^2)/2,
+ * mu = 1 - 2 s / k^2.  One block per trial: element, s, acceptance. */
+static double or_exact_rayleigh_iaa(const or_material *m, double e_kev, uint64_t seed, uint64_t h, uint32_t step,
+                                    int *ok)
+{
+    double kr = e_kev / OR_HC;
+    double smax = kr * kr;
+    double c[OR_MAX_ELEMENTS], d[OR_MAX_ELEMENTS], w[OR_MAX_ELEMENTS];
+    double total = 0.0;
+    for (int i = 0; i < m->n_el; ++i) {
+        double z = (double)m->el_z[i];
+        c[i] = or_ff_width(m->el_z[i]);
+        d[i] = -expm1(-3.0 * log1p(c[i] * smax));             /* 1 - (1 + c smax)^-3 */
+        w[i] = (m->el_n[i] * (z * z)) * d[i] / (3.0 * c[i]);   /* n Z^2 int_0^smax (1 + c s)^-4 ds */
+        total += w[i];
+    }
+    for (uint32_t t = 0; t < OR_MAX_TRIALS; ++t) {
+        uint32_t b[4];
+        or_block(seed, h, step, OR_STREAM_EXACT | (t << 8), b);
+        double u = or_uniform(b[0]) * total, z = or_uniform(b[1]), r = or_uniform(b[2]);
+        int i = 0;
+        while (i < m->n_el - 1 && u >= w[i]) { u -= w[i]; ++i; }
+        double s = (pow(1.0 - z * d[i], -1.0 / 3.0) - 1.0) / c[i];
+        double mu = 1.0 - 2.0 * s / smax;
+        if (mu < -1.0) mu = -1.0;
+        if (mu > 1.0) mu = 1.0;
         if (r <= 0.5 * (1.0 + mu * mu)) { *ok = 1; return mu; }
     }
     *ok = 0;

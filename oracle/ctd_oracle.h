@@ -31,6 +31,8 @@ extern "C" {
 #endif
 
 /* Material record: the closed-form cross sections need these numbers. */
+#define OR_MAX_ELEMENTS 16
+
 typedef struct {
     double z_over_a;  /* electrons per gram / N_A (Compton, Eq. 2)                 */
     double a_mol;     /* molar mass of one formula unit, g/mol (PE and Rayleigh)   */
@@ -39,6 +41,12 @@ typedef struct {
     double sq0;       /* analytic scattering-function width for the Waller-Hartree
                          Compton model, S(q)/Z = 1 - exp(-q^2/sq0^2), 1/Angstrom;
                          <= 0 means S/Z = 1 (free electrons)                      */
+    /* elements of one formula unit for the independent-atom (IAA) molecular form
+     * factor of Rayleigh scattering: n_el > 0 selects it for the material's Rayleigh
+     * total and R surface (n_el = 0: F^2 = exp(-q^2/q0^2) and the closed-form total) */
+    int n_el;
+    int el_z[OR_MAX_ELEMENTS];    /* atomic numbers, 1..100 */
+    double el_n[OR_MAX_ELEMENTS]; /* atoms per formula unit, > 0 */
 } or_material;
 
 enum { OR_SRC_STATIC = 0, OR_SRC_ARC = 1 };
@@ -108,6 +116,17 @@ double or_mu_rayleigh(const or_material *m, double e_kev);
  * cm^2 per electron; sq0 <= 0 integrates Klein-Nishina alone */
 double or_sigma_wh(double e_kev, double sq0);
 double or_mu_compton_wh(const or_material *m, double e_kev);
+/* Independent-atom molecular form factor (Sec. 2.2.2, Eq. 1), a screened
+ * hydrogenic atom per element: F_Z(x) = Z / (1 + (2 pi a_Z x)^2)^2 with the
+ * Thomas-Fermi radius a_Z = 0.8853 a0 Z^(-1/3), x = sin(theta/2)/lambda in
+ * 1/Angstrom; F^2_mol(x) = sum_i n_i F_Zi(x)^2.  Arguments: x^2. */
+double or_ff_atom2(int z, double x2);
+double or_ff_mol2(const or_material *m, double x2);
+/* Rayleigh total per formula unit in cm^2 with the IAA form factor: pi r0^2 times
+ * the composite Simpson integral over mu in [-1, 1] (20000 intervals) of
+ * (1 + mu^2) F^2_mol(x), x^2 = k^2 (1 - mu) / 2, k = E / hc */
+double or_sigma_rayleigh_iaa(const or_material *m, double e_kev);
+double or_mu_rayleigh_iaa(const or_material *m, double e_kev);
 
 /* integer allocation of n histories to bins by largest remainder */
 int or_allocate(uint64_t n, int nbins, const double *w, uint64_t *out);
@@ -136,6 +155,7 @@ void or_setup_surfaces(const or_setup *s, double *c_surf /* n_c*n_e*n_zeta, n_c 
 /* the surfaces on their own (Sec. 2.2.2 and 2.2.3), binary64 */
 void or_build_kn_surface(int e_min, int n_e, int n_zeta, double *out);
 void or_build_rayleigh_surface(double q0, int e_min, int n_e, int n_zeta, double *out);
+void or_build_rayleigh_iaa_surface(const or_material *m, int e_min, int n_e, int n_zeta, double *out);
 void or_build_wh_surface(double sq0, int e_min, int n_e, int n_zeta, double *out);
 
 /* angular samplers for the sampler validation of Figs. 3-4:

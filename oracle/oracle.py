@@ -30,9 +30,13 @@ def lib():
     return _lib
 
 
+MAX_ELEMENTS = 16
+
+
 class OrMaterial(C.Structure):
     _fields_ = [("z_over_a", C.c_double), ("a_mol", C.c_double), ("z_eff", C.c_double), ("q0", C.c_double),
-                ("sq0", C.c_double)]
+                ("sq0", C.c_double), ("n_el", C.c_int), ("el_z", C.c_int * MAX_ELEMENTS),
+                ("el_n", C.c_double * MAX_ELEMENTS)]
 
 
 class OrProblem(C.Structure):
@@ -95,6 +99,12 @@ def _declare(L):
     L.or_setup_surfaces.argtypes = [P, dp, dp]
     L.or_build_kn_surface.argtypes = [C.c_int, C.c_int, C.c_int, dp]
     L.or_build_rayleigh_surface.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int, dp]
+    L.or_build_rayleigh_iaa_surface.argtypes = [C.POINTER(OrMaterial), C.c_int, C.c_int, C.c_int, dp]
+    L.or_ff_atom2.restype = C.c_double
+    L.or_ff_atom2.argtypes = [C.c_int, C.c_double]
+    for n in ("or_ff_mol2", "or_sigma_rayleigh_iaa", "or_mu_rayleigh_iaa"):
+        getattr(L, n).restype = C.c_double
+        getattr(L, n).argtypes = [C.POINTER(OrMaterial), C.c_double]
     L.or_sample_mu_f64.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64, dp]
     L.or_sample_mu_f32.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint64, dp]
     L.or_alias_build.argtypes = [C.c_int, dp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]
@@ -124,8 +134,18 @@ def uniform(x: int) -> float:
     return lib().or_uniform(x)
 
 
-def material_struct(m) -> OrMaterial:
-    return OrMaterial(m.z_over_a, m.a_mol, m.z_eff, m.q0, m.sq0)
+def material_struct(m, iaa=False) -> OrMaterial:
+    """The C record of a material; iaa=True carries its elements (independent-atom
+    Rayleigh form factor)."""
+    s = OrMaterial(m.z_over_a, m.a_mol, m.z_eff, m.q0, m.sq0)
+    if iaa:
+        if not 0 < len(m.elements) <= MAX_ELEMENTS:
+            raise ValueError(f"material {m.name}: 1..{MAX_ELEMENTS} elements needed for the IAA form factor")
+        s.n_el = len(m.elements)
+        for i, (z, n) in enumerate(m.elements):
+            s.el_z[i] = int(z)
+            s.el_n[i] = float(n)
+    return s
 
 
 def mu_pe(m, e):
@@ -151,6 +171,32 @@ def sigma_wh(e, sq0):
 
 def mu_compton_wh(m, e):
     return lib().or_mu_compton_wh(C.byref(material_struct(m)), e)
+
+
+def ff_atom2(z, x2):
+    """Squared form factor of element z at x^2 = (sin(theta/2)/lambda)^2, 1/Angstrom^2."""
+    return lib().or_ff_atom2(int(z), float(x2))
+
+
+def ff_mol2(m, x2):
+    """Independent-atom molecular F^2 of material m at x^2."""
+    return lib().or_ff_mol2(C.byref(material_struct(m, iaa=True)), float(x2))
+
+
+def sigma_rayleigh_iaa(m, e):
+    """Rayleigh total per formula unit (cm^2) with the IAA form factor, Simpson over mu."""
+    return lib().or_sigma_rayleigh_iaa(C.byref(material_struct(m, iaa=True)), e)
+
+
+def mu_rayleigh_iaa(m, e):
+    return lib().or_mu_rayleigh_iaa(C.byref(material_struct(m, iaa=True)), e)
+
+
+def rayleigh_iaa_surface(m, e_min, n_e, n_zeta):
+    out = np.empty((n_e, n_zeta), dtype=np.float64)
+    lib().or_build_rayleigh_iaa_surface(C.byref(material_struct(m, iaa=True)), e_min, n_e, n_zeta,
+                                        _ptr(out, C.c_double))
+    return out
 
 
 def allocate(n: int, w) -> np.ndarray:
@@ -256,7 +302,8 @@ class Setup:
         self.precision = precision
         self._mat = np.ascontiguousarray(ph.mat, dtype=np.uint8).ravel()
         self._rho = np.ascontiguousarray(ph.rho, dtype=np.float32).ravel()
-        self._mats = (OrMaterial * len(ph.materials))(*[material_struct(m) for m in ph.materials])
+        iaa = getattr(phy, 'rayleigh', 'gauss') == 'iaa'
+        self._mats = (OrMaterial * len(ph.materials))(*[material_struct(m, iaa) for m in ph.materials])
         self._elo = np.ascontiguousarray(sp.e_lo, dtype=np.float64)
         self._ehi = np.ascontiguousarray(sp.e_hi, dtype=np.float64)
         self._w = np.ascontiguousarray(sp.w, dtype=np.float64)

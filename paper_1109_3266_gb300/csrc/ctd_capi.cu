@@ -53,16 +53,22 @@ int busy(Phantom *P)
 // Klein-Nishina C (kind 0), Rayleigh R (kind 1, form-factor width q0) or
 // Waller-Hartree C (kind 2, scattering-function width q0) surface in binary32,
 // built once per context and node grid.
-const std::vector<float> &angular_surface(ctd_ctx *ctx, int kind, double q0, int e_min, int n_e, int n_zeta)
+const std::vector<float> &angular_surface(ctd_ctx *ctx, int kind, double q0, const ctd::Elements *el, int e_min, int n_e,
+                                         int n_zeta)
 {
-    const std::array<double, 5> key{static_cast<double>(kind), kind ? (q0 > 0.0 ? q0 : 0.0) : 0.0,
-                                    static_cast<double>(e_min), static_cast<double>(n_e), static_cast<double>(n_zeta)};
+    std::vector<double> key{static_cast<double>(kind), (kind == 1 || kind == 2) && q0 > 0.0 ? q0 : 0.0,
+                            static_cast<double>(e_min), static_cast<double>(n_e), static_cast<double>(n_zeta)};
+    if (kind == 3)
+        for (int i = 0; i < el->n; ++i) {
+            key.push_back(static_cast<double>(el->z[i]));
+            key.push_back(el->count[i]);
+        }
     auto it = ctx->surfaces.find(key);
     if (it != ctx->surfaces.end()) return it->second;
     if (ctx->surfaces.size() >= 64) ctx->surfaces.clear();
     const size_t row = static_cast<size_t>(n_e) * n_zeta;
     std::vector<double> tmp(row);
-    ctd::build_surface(kind, q0, e_min, n_e, n_zeta, tmp.data());
+    ctd::build_surface(kind, q0, el, e_min, n_e, n_zeta, tmp.data());
     std::vector<float> f(row);
     for (size_t i = 0; i < row; ++i) f[i] = static_cast<float>(tmp[i]);
     return ctx->surfaces.emplace(key, std::move(f)).first->second;
@@ -75,8 +81,8 @@ int build_tables(ctd_ctx *ctx, Phantom &P)
     const int n_e = ph.e_max_kev - ph.e_min_kev + 1;
     const int nm = static_cast<int>(P.mats.size());
     std::vector<double> cum, mmax;
-    ctd::build_tables(P.mats, P.rho_max, P.present, ph.e_min_kev, n_e, ph.majorant_scale, ph.compton_model, cum,
-                      mmax);
+    ctd::build_tables(P.mats, P.els, P.rho_max, P.present, ph.e_min_kev, n_e, ph.majorant_scale, ph.compton_model,
+                      cum, mmax);
     P.h_tab.assign(static_cast<size_t>(nm) * n_e * 4, 0.0f);
     for (size_t i = 0; i < static_cast<size_t>(nm) * n_e; ++i)
         for (int c = 0; c < 3; ++c) P.h_tab[i * 4 + c] = static_cast<float>(cum[i * 3 + c]);
@@ -94,15 +100,17 @@ int build_tables(ctd_ctx *ctx, Phantom &P)
         // one Waller-Hartree C surface per material
         P.h_cs.resize(row * nm);
         for (int m = 0; m < nm; ++m) {
-            const std::vector<float> &c = angular_surface(ctx, 2, P.mats[m].sq0, ph.e_min_kev, n_e, ph.n_zeta);
+            const std::vector<float> &c = angular_surface(ctx, 2, P.mats[m].sq0, nullptr, ph.e_min_kev, n_e, ph.n_zeta);
             std::copy(c.begin(), c.end(), P.h_cs.begin() + m * row);
         }
     } else {
-        P.h_cs = angular_surface(ctx, 0, 0.0, ph.e_min_kev, n_e, ph.n_zeta);
+        P.h_cs = angular_surface(ctx, 0, 0.0, nullptr, ph.e_min_kev, n_e, ph.n_zeta);
     }
     P.h_rs.resize(row * nm);
     for (int m = 0; m < nm; ++m) {
-        const std::vector<float> &r = angular_surface(ctx, 1, P.mats[m].q0, ph.e_min_kev, n_e, ph.n_zeta);
+        const std::vector<float> &r = P.els[m].n > 0
+                                          ? angular_surface(ctx, 3, 0.0, &P.els[m], ph.e_min_kev, n_e, ph.n_zeta)
+                                          : angular_surface(ctx, 1, P.mats[m].q0, nullptr, ph.e_min_kev, n_e, ph.n_zeta);
         std::copy(r.begin(), r.end(), P.h_rs.begin() + m * row);
     }
     int rc;
@@ -517,6 +525,7 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     P->dx = dx; P->dy = dy; P->dz = dz;
     P->nvox = nvox;
     P->mats.assign(mats, mats + n_mat);
+    P->els.assign(static_cast<size_t>(n_mat), ctd::Elements{});
     P->rho_max.assign(n_mat, 0.0);
     P->present.assign(n_mat, 0);
     for (size_t v = 0; v < nvox; ++v) {
@@ -574,6 +583,30 @@ int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys)
     if (phys->compton_model != CTD_COMPTON_KN && phys->compton_model != CTD_COMPTON_WH)
         return fail(CTD_EINVAL, "unknown Compton model");
     P->phys = *phys;
+    P->tables_ok = false;
+    return CTD_OK;
+}
+
+int ctd_set_material_elements(ctd_ctx *ctx, ctd_phantom ph, int material, int n_el, const int *z,
+                              const double *count)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if ((rc = busy(P))) return rc;
+    if (material < 0 || material >= static_cast<int>(P->mats.size())) return fail(CTD_EINVAL, "material out of range");
+    if (n_el < 0 || n_el > CTD_MAX_ELEMENTS) return fail(CTD_EINVAL, "n_el must be 0..%d", CTD_MAX_ELEMENTS);
+    if (n_el > 0 && (!z || !count)) return fail(CTD_EINVAL, "null element arrays");
+    ctd::Elements el;
+    el.n = n_el;
+    for (int i = 0; i < n_el; ++i) {
+        if (z[i] < 1 || z[i] > 100) return fail(CTD_EINVAL, "atomic number %d out of 1..100", z[i]);
+        if (!(count[i] > 0.0) || !std::isfinite(count[i])) return fail(CTD_EINVAL, "atom counts must be finite and > 0");
+        el.z[i] = z[i];
+        el.count[i] = count[i];
+    }
+    P->els[material] = el;
     P->tables_ok = false;
     return CTD_OK;
 }

@@ -68,6 +68,7 @@ struct Phantom {
     double dx = 0, dy = 0, dz = 0;
     size_t nvox = 0;
     std::vector<ctd_material> mats;
+    std::vector<ctd::Elements> els;   // per material: independent-atom Rayleigh form factor (n = 0: none)
     std::vector<double> rho_max;
     std::vector<int> present;
     ctd_physics phys{};
@@ -161,8 +162,9 @@ struct ctd_ctx {
     int shared_launch = 0;
     ctd::host::Staged *staged = nullptr;      // pinned read-back of counts and results
     size_t staged_n = 0;
-    // angular surfaces by (kind, q0, e_min, n_e, n_zeta): they do not depend on the phantom
-    std::map<std::array<double, 5>, std::vector<float>> surfaces;
+    // angular surfaces by (kind, q0, e_min, n_e, n_zeta[, the elements' (Z, count) pairs]):
+    // they do not depend on the phantom
+    std::map<std::vector<double>, std::vector<float>> surfaces;
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> lane_done;
     cudaEvent_t fork_event = nullptr;
@@ -178,7 +180,8 @@ int busy(Phantom *P);
 // Klein-Nishina C (kind 0), Rayleigh R (kind 1, form-factor width q0) or
 // Waller-Hartree C (kind 2, scattering-function width q0) surface in binary32,
 // built once per context and node grid
-const std::vector<float> &angular_surface(ctd_ctx *ctx, int kind, double q0, int e_min, int n_e, int n_zeta);
+const std::vector<float> &angular_surface(ctd_ctx *ctx, int kind, double q0, const ctd::Elements *el, int e_min, int n_e,
+                                         int n_zeta);
 // attenuation tables, majorant and surfaces of the phantom's physics, uploaded
 int build_tables(ctd_ctx *ctx, Phantom &P);
 // bin starts of the stratified allocation for batches of n / nb (and one more)

@@ -22,6 +22,16 @@ constexpr double kPeCoef = 1.0e-2;              // photoelectric coefficient, mi
 constexpr double kRayCoef = 1.565e-5;           // Rayleigh coefficient, barn MeV^2
 constexpr double kKevToJ = 1.602176634e-16;
 constexpr int kCdfIntervals = 20000;            // mu intervals of the numeric cdf
+constexpr double kBohr = 0.529177210903;         // Bohr radius, Angstrom
+constexpr double kThomasFermi = 0.88534138;     // Thomas-Fermi radius / (a0 Z^-1/3): (3 pi / 4)^(2/3) / 2
+
+// Elements of a material's formula unit for the independent-atom Rayleigh form
+// factor (n = 0: the analytic F^2 = exp(-q^2/q0^2) and the closed-form total).
+struct Elements {
+    int n = 0;
+    int z[CTD_MAX_ELEMENTS] = {};
+    double count[CTD_MAX_ELEMENTS] = {};
+};
 
 // message returned by ctd_last_error() on the calling thread (ctd_capi.cu)
 void set_error(const char *msg);
@@ -33,14 +43,19 @@ double mu_compton(const ctd_material &m, double e_kev);
 double mu_rayleigh(const ctd_material &m, double e_kev);
 double sigma_wh(double e_kev, double sq0);
 double mu_compton_wh(const ctd_material &m, double e_kev);
+// independent-atom Rayleigh: total per formula unit (cm^2) and mass attenuation (cm^2/g)
+double sigma_rayleigh_iaa(const Elements &el, double e_kev);
+double mu_rayleigh_iaa(const ctd_material &m, const Elements &el, double e_kev);
 
 // Node tables: cum[(m*n_e + j)*3 + c] cumulative mass attenuation; mmax[j] majorant.
-void build_tables(const std::vector<ctd_material> &mats, const std::vector<double> &rho_max,
-                  const std::vector<int> &present, int e_min, int n_e, double scale, int compton_model,
-                  std::vector<double> &cum, std::vector<double> &mmax);
+// els[m].n > 0 gives material m the independent-atom Rayleigh total.
+void build_tables(const std::vector<ctd_material> &mats, const std::vector<Elements> &els,
+                  const std::vector<double> &rho_max, const std::vector<int> &present, int e_min, int n_e,
+                  double scale, int compton_model, std::vector<double> &cum, std::vector<double> &mmax);
 // Inverse-cdf surface rows for node energies e_min..e_min+n_e-1: kind 0 Klein-Nishina,
-// 1 Rayleigh of form-factor width q0, 2 Waller-Hartree of scattering-function width q0.
-void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out);
+// 1 Rayleigh of form-factor width q0, 2 Waller-Hartree of scattering-function width q0,
+// 3 Rayleigh with the independent-atom form factor of *el.
+void build_surface(int kind, double q0, const Elements *el, int e_min, int n_e, int n_zeta, double *out);
 // Walker alias table of n intensities (Vose's construction): thr[k] = floor(p 2^32)
 // of the kept share of column k, alias[k] the beamlet it borrows from; false if
 // the intensities are unusable.

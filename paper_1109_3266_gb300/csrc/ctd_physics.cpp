@@ -71,6 +71,75 @@ double mu_compton_wh(const ctd_material &m, double e_kev)
     return (kNA * m.z_over_a) * sigma_wh(e_kev, m.sq0);
 }
 
+namespace {
+
+// Independent-atom form factor of Rayleigh scattering.  Each element is a screened
+// hydrogenic atom: the density Z exp(-2r/a) / (pi a^3) transforms to
+// F(Q) = Z / (1 + (Q a / 2)^2)^2, Q = 4 pi x, x = sin(theta/2)/lambda, with the
+// Thomas-Fermi radius a = 0.8853 a0 Z^(-1/3); so F^2 = Z^2 / (1 + c x^2)^4,
+// c = (2 pi a)^2.  A formula unit's F^2 is the sum over its atoms.
+inline double ff_width(int z)
+{
+    const double a = (kThomasFermi * kBohr) / std::cbrt(static_cast<double>(z));
+    const double w = (2.0 * kPi) * a;
+    return w * w;
+}
+
+struct FormFactor {
+    int n = 0;
+    double z[CTD_MAX_ELEMENTS], count[CTD_MAX_ELEMENTS], c[CTD_MAX_ELEMENTS];
+    explicit FormFactor(const Elements &el) : n(el.n)
+    {
+        for (int i = 0; i < n; ++i) {
+            z[i] = static_cast<double>(el.z[i]);
+            count[i] = el.count[i];
+            c[i] = ff_width(el.z[i]);
+        }
+    }
+    // F^2 of the formula unit at x^2
+    double f2(double x2) const
+    {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double g = 1.0 / (1.0 + c[i] * x2);
+            const double f = z[i] * (g * g);
+            s += count[i] * (f * f);
+        }
+        return s;
+    }
+    // Eq. 1 up to r0^2/2 at polar cosine mu, kr = E/hc: (1 + mu^2) F^2, x^2 = kr^2 (1 - mu) / 2
+    double density(double kr, double mu) const
+    {
+        const double x2 = ((kr * kr) * (1.0 - mu)) * 0.5;
+        return (1.0 + mu * mu) * f2(x2);
+    }
+};
+
+}  // namespace
+
+// Rayleigh total per formula unit in cm^2 with the independent-atom form factor:
+// pi r0^2 times the composite Simpson integral of Eq. 1 over mu in [-1, 1].
+double sigma_rayleigh_iaa(const Elements &el, double e_kev)
+{
+    const FormFactor ff(el);
+    const int M = kCdfIntervals;
+    const double kr = e_kev / kHc;
+    double odd = 0.0, even = 0.0;
+    for (int n = 1; n < M; ++n) {
+        const double mu = static_cast<double>(2 * n - M) / static_cast<double>(M);
+        if (n & 1) odd += ff.density(kr, mu);
+        else even += ff.density(kr, mu);
+    }
+    const double ends = ff.density(kr, -1.0) + ff.density(kr, 1.0);
+    const double integral = ((2.0 / static_cast<double>(M)) / 3.0) * (ends + (4.0 * odd + 2.0 * even));
+    return (kPi * kR0 * kR0) * integral;
+}
+
+double mu_rayleigh_iaa(const ctd_material &m, const Elements &el, double e_kev)
+{
+    return (sigma_rayleigh_iaa(el, e_kev) * kNA) / m.a_mol;
+}
+
 // Photoelectric absorption, 1e-2 Z^4 / E_MeV^3 microbarn per formula unit (cm^2/g).
 double mu_pe(const ctd_material &m, double e_kev)
 {
@@ -89,9 +158,9 @@ double mu_rayleigh(const ctd_material &m, double e_kev)
     return ((sigma * kBarn) * kNA) / m.a_mol;
 }
 
-void build_tables(const std::vector<ctd_material> &mats, const std::vector<double> &rho_max,
-                  const std::vector<int> &present, int e_min, int n_e, double scale, int compton_model,
-                  std::vector<double> &cum, std::vector<double> &mmax)
+void build_tables(const std::vector<ctd_material> &mats, const std::vector<Elements> &els,
+                  const std::vector<double> &rho_max, const std::vector<int> &present, int e_min, int n_e,
+                  double scale, int compton_model, std::vector<double> &cum, std::vector<double> &mmax)
 {
     const size_t nm = mats.size();
     cum.assign(nm * n_e * 3, 0.0);
@@ -101,7 +170,7 @@ void build_tables(const std::vector<ctd_material> &mats, const std::vector<doubl
             const double e = static_cast<double>(e_min + j);
             const double pe = mu_pe(mats[m], e);
             const double c = compton_model == CTD_COMPTON_WH ? mu_compton_wh(mats[m], e) : mu_compton(mats[m], e);
-            const double r = mu_rayleigh(mats[m], e);
+            const double r = els[m].n > 0 ? mu_rayleigh_iaa(mats[m], els[m], e) : mu_rayleigh(mats[m], e);
             double *dst = &cum[(m * n_e + j) * 3];
             dst[0] = pe;
             dst[1] = pe + c;
@@ -142,19 +211,21 @@ inline double grid_mu(int n)
 
 }  // namespace
 
-void build_surface(int kind, double q0, int e_min, int n_e, int n_zeta, double *out)
+void build_surface(int kind, double q0, const Elements *el, int e_min, int n_e, int n_zeta, double *out)
 {
     const int M = kCdfIntervals;
     std::vector<double> pdf(M + 1), cdf(M + 1);
+    const FormFactor ff(kind == 3 && el ? *el : Elements{});
     for (int j = 0; j < n_e; ++j) {
         const double e = static_cast<double>(e_min + j);
         const double k = e / kMec2;
         const double kr = e / kHc;
         const double a = q0 > 0.0 ? (2.0 * kr * kr) / (q0 * q0) : 0.0;
         for (int n = 0; n <= M; ++n)
-            pdf[n] = kind == 0 ? density_kn(k, grid_mu(n))
+            pdf[n] = kind == 0   ? density_kn(k, grid_mu(n))
                      : kind == 1 ? density_rayleigh(a, grid_mu(n))
-                                 : density_wh(k, a, grid_mu(n));
+                     : kind == 2 ? density_wh(k, a, grid_mu(n))
+                                 : ff.density(kr, grid_mu(n));
         // cumulative trapezoid without the common factor h/2
         cdf[0] = 0.0;
         for (int n = 1; n <= M; ++n) cdf[n] = cdf[n - 1] + (pdf[n - 1] + pdf[n]);

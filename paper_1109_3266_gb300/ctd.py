@@ -106,6 +106,7 @@ def lib():
                                          C.POINTER(C.c_int32)]
         L.ctd_destroy_phantom.argtypes = [P, C.c_int32]
         L.ctd_set_physics.argtypes = [P, C.c_int32, C.POINTER(ctd_physics)]
+        L.ctd_set_material_elements.argtypes = [P, C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int), dp]
         L.ctd_set_source.argtypes = [P, C.c_int32, C.POINTER(ctd_source)]
         L.ctd_set_spectrum.argtypes = [P, C.c_int32, dp, dp, dp, C.c_int]
         L.ctd_run.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int]
@@ -190,6 +191,15 @@ def ctd_set_physics(ctx, ph, e_min_kev=1, e_max_kev=150, n_zeta=1024, majorant_s
     c = {"kn": CTD_COMPTON_KN, "wh": CTD_COMPTON_WH}[compton] if isinstance(compton, str) else int(compton)
     p = ctd_physics(e_min_kev, e_max_kev, n_zeta, majorant_scale, m, max_real, c)
     _check(lib().ctd_set_physics(ctx, ph, C.byref(p)))
+
+
+def ctd_set_material_elements(ctx, ph, material, elements):
+    """Independent-atom Rayleigh form factor for one material: elements is
+    ((Z, atoms per formula unit), ...); empty restores the analytic form factor."""
+    n = len(elements)
+    z = (C.c_int * max(n, 1))(*[int(e[0]) for e in elements])
+    cnt = np.ascontiguousarray([float(e[1]) for e in elements] or [0.0], dtype=np.float64)
+    _check(lib().ctd_set_material_elements(ctx, ph, int(material), n, z, _dp(cnt)))
 
 
 def ctd_set_source(ctx, ph, kind, sad_cm, u_lo_cm, u_hi_cm, v_lo_cm, v_hi_cm, n_proj=1, arc0_rad=0.0,
@@ -336,6 +346,9 @@ def load_problem(ctx, problem, physics=True):
         p = problem.physics
         ctd_set_physics(ctx, h, p.e_min, p.e_max, p.n_zeta, p.majorant_scale, p.mode, p.max_real,
                         getattr(p, "compton", "kn"))
+        if getattr(p, "rayleigh", "gauss") == "iaa":
+            for m, mat in enumerate(ph_.materials):
+                ctd_set_material_elements(ctx, h, m, mat.elements)
     return h
 
 

@@ -37,6 +37,8 @@ class Material:
     density  : nominal density (g/cm^3), used by the phantom generators only
     sq0      : scattering-function width in 1/Angstrom for the Waller-Hartree
                Compton model, S(q)/Z = 1 - exp(-q^2/sq0^2); 0 selects S/Z = 1
+    elements : ((Z, atoms per formula unit), ...) for the independent-atom
+               Rayleigh form factor (used when the physics asks for it)
     """
     name: str
     z_over_a: float
@@ -45,6 +47,7 @@ class Material:
     q0: float
     density: float
     sq0: float = 0.55
+    elements: tuple = ()
 
 
 # proposed scattering-function width (the paper's PENELOPE tables are not
@@ -52,15 +55,32 @@ class Material:
 SQ0 = 0.55
 
 
-def _mat(name, z_over_a, z_eff, density, a_mol=None, q0=1.0, sq0=SQ0):
-    return Material(name, z_over_a, a_mol if a_mol is not None else 10.0 / z_over_a, z_eff, q0, density, sq0)
+# standard atomic weights (g/mol) of the elements in the materials below
+ATOMIC_WEIGHT = {1: 1.008, 6: 12.011, 7: 14.007, 8: 15.999, 11: 22.990, 12: 24.305, 15: 30.974, 16: 32.06,
+                 17: 35.45, 18: 39.948, 19: 39.098, 20: 40.078}
 
 
-WATER = _mat("water", 0.5551, 7.42, 1.0, a_mol=18.015)
-SOFT_TISSUE = _mat("soft_tissue", 0.5494, 7.4, 1.03)
-BRAIN = _mat("brain", 0.5520, 7.5, 1.04)
-BONE = _mat("bone", 0.5148, 13.8, 1.85)
-AIR = _mat("air", 0.4992, 7.64, 0.0012)
+def atoms_per_unit(mass_fractions, a_mol):
+    """((Z, atoms per formula unit), ...) from mass fractions {Z: w} (normalised
+    to 1) for a formula unit of molar mass a_mol."""
+    tot = float(sum(mass_fractions.values()))
+    return tuple((z, (w / tot) * a_mol / ATOMIC_WEIGHT[z]) for z, w in sorted(mass_fractions.items()))
+
+
+def _mat(name, z_over_a, z_eff, density, a_mol=None, q0=1.0, sq0=SQ0, mass_fractions=None, elements=None):
+    a = a_mol if a_mol is not None else 10.0 / z_over_a
+    els = elements if elements is not None else (atoms_per_unit(mass_fractions, a) if mass_fractions else ())
+    return Material(name, z_over_a, a, z_eff, q0, density, sq0, els)
+
+
+# elemental compositions by mass: the ICRU reference tissues and dry air
+WATER = _mat("water", 0.5551, 7.42, 1.0, a_mol=18.015, elements=((1, 2.0), (8, 1.0)))
+SOFT_TISSUE = _mat("soft_tissue", 0.5494, 7.4, 1.03, mass_fractions={1: 0.101, 6: 0.111, 7: 0.026, 8: 0.762})
+BRAIN = _mat("brain", 0.5520, 7.5, 1.04, mass_fractions={1: 0.107, 6: 0.145, 7: 0.022, 8: 0.712, 11: 0.002,
+                                                          15: 0.004, 16: 0.002, 17: 0.003, 19: 0.003})
+BONE = _mat("bone", 0.5148, 13.8, 1.85, mass_fractions={1: 0.034, 6: 0.155, 7: 0.042, 8: 0.435, 11: 0.001,
+                                                        12: 0.002, 15: 0.103, 16: 0.003, 20: 0.225})
+AIR = _mat("air", 0.4992, 7.64, 0.0012, mass_fractions={6: 0.000124, 7: 0.755268, 8: 0.231781, 18: 0.012827})
 
 
 def thomson(m: Material) -> Material:
@@ -128,6 +148,7 @@ class Physics:
     mode: str = "full"          # "full" | "max_real" ("primary" is max_real with 1)
     max_real: int = 0
     compton: str = "kn"         # "kn" free-electron Klein-Nishina | "wh" Waller-Hartree (Eq. 2 with S)
+    rayleigh: str = "gauss"     # "gauss" F^2 = exp(-q^2/q0^2) | "iaa" independent-atom form factor of the elements
 
 
 @dataclass

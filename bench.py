@@ -346,8 +346,8 @@ def run_ours(args):
     h2d = nvox * (1 + 4) + 3 * 8 * len(p.spectrum.w)
     d2h = nvox * 16
 
-    # roofline of the transport kernel: lane-instructions per history over the
-    # SM issue ceiling 152 SM x 128 lanes x clock
+    # roofline of the transport kernel: lane-instructions per history (KERNEL_PROFILE, from
+    # the ncu capture) over the SM issue ceiling 152 SM x 128 lanes x clock
     peaks, peak_kind = load_peaks()
     ck = clk.summary()
     mhz = peaks.get("sm_max_mhz", 2070.0)

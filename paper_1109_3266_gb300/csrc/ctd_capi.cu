@@ -528,14 +528,6 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     P->els.assign(static_cast<size_t>(n_mat), ctd::Elements{});
     P->rho_max.assign(n_mat, 0.0);
     P->present.assign(n_mat, 0);
-    for (size_t v = 0; v < nvox; ++v) {
-        const int m = mat[v];
-        const double r = density[v];
-        if (m >= n_mat) return fail(CTD_EINVAL, "voxel %zu has material %d >= n_mat", v, m);
-        if (!(r >= 0.0) || !std::isfinite(r)) return fail(CTD_EINVAL, "voxel %zu has an invalid density", v);
-        if (!P->present[m] || r > P->rho_max[m]) P->rho_max[m] = r;
-        P->present[m] = 1;
-    }
     P->phys.e_min_kev = 1;
     P->phys.e_max_kev = 150;
     P->phys.n_zeta = 1024;
@@ -546,7 +538,23 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     if ((rc = P->mat.ensure(nvox)) || (rc = P->rho.ensure(nvox))) return rc;
     CK(cudaMemcpyAsync(P->mat.p, mat, nvox, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(P->rho.p, density, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    // range checks, materials present and their largest densities, on the device
+    DevBuf<ctd::PhantomScan> scan;
+    if ((rc = scan.ensure(1))) return rc;
+    CKS(ctd::launch_scan_phantom(P->mat.p, P->rho.p, nvox, n_mat, scan.p, ctx->stream));
+    ctd::PhantomScan sc{};
+    CK(cudaMemcpyAsync(&sc, scan.p, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (sc.first_bad_mat != ~0ull && sc.first_bad_mat <= sc.first_bad_rho)
+        return fail(CTD_EINVAL, "voxel %llu has material %d >= n_mat", sc.first_bad_mat,
+                    static_cast<int>(mat[sc.first_bad_mat]));
+    if (sc.first_bad_rho != ~0ull) return fail(CTD_EINVAL, "voxel %llu has an invalid density", sc.first_bad_rho);
+    for (int m = 0; m < n_mat; ++m) {
+        P->present[m] = static_cast<int>(sc.present_mask >> m & 1u);
+        float r;
+        std::memcpy(&r, &sc.max_bits[m], sizeof(r));
+        P->rho_max[m] = P->present[m] ? static_cast<double>(r) : 0.0;
+    }
     const int id = ctx->next_id++;
     ctx->phantoms[id] = std::move(P);
     *out = id;

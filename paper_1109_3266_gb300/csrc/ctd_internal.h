@@ -125,6 +125,19 @@ static_assert(sizeof(RequestDesc) % 16 == 0, "RequestDesc must be a whole number
 
 constexpr int kMaxPhantomMaterials = 16;
 
+// What a phantom's voxels hold, found on the device when the phantom is created:
+// the first voxel whose material index is out of range and the first whose
+// density is not a finite number >= 0 (~0 if none), which materials occur, and the
+// largest density of each (binary32 bit patterns, which order like the values
+// for non-negative numbers).
+struct PhantomScan {
+    unsigned long long first_bad_mat, first_bad_rho;
+    unsigned int present_mask;
+    unsigned int max_bits[kMaxPhantomMaterials];
+};
+int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, PhantomScan *out,
+                        void *stream);
+
 // What every request of a launch shares: the node grid and the C surface.
 struct SharedTables {
     int n_e, n_zeta, e_min;

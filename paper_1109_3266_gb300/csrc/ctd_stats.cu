@@ -184,6 +184,46 @@ __global__ void sum_final_kernel(const double *partials, int n_parts, double *re
     }
 }
 
+// One pass over a new phantom's voxels (grid-stride): range checks and the
+// per-material presence and largest density, reduced in shared memory, then one
+// global atomic per block and quantity.  -0 densities count as +0.
+__global__ void scan_phantom_kernel(const uint8_t *__restrict__ mat, const float *__restrict__ rho, size_t nvox,
+                                    int n_mat, PhantomScan *out)
+{
+    __shared__ unsigned int s_max[kMaxPhantomMaterials];
+    __shared__ unsigned int s_mask;
+    __shared__ unsigned long long s_bad_mat, s_bad_rho;
+    if (threadIdx.x < kMaxPhantomMaterials) s_max[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        s_mask = 0u;
+        s_bad_mat = ~0ull;
+        s_bad_rho = ~0ull;
+    }
+    __syncthreads();
+    for (size_t v = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; v < nvox;
+         v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int m = mat[v];
+        const float r = rho[v];
+        if (m >= n_mat) {
+            atomicMin(&s_bad_mat, static_cast<unsigned long long>(v));
+            continue;
+        }
+        if (!(r >= 0.0f) || !isfinite(r)) {
+            atomicMin(&s_bad_rho, static_cast<unsigned long long>(v));
+            continue;
+        }
+        atomicMax(&s_max[m], __float_as_uint(r + 0.0f));
+        atomicOr(&s_mask, 1u << m);
+    }
+    __syncthreads();
+    if (threadIdx.x < n_mat && (s_mask >> threadIdx.x & 1u)) atomicMax(&out->max_bits[threadIdx.x], s_max[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        if (s_mask) atomicOr(&out->present_mask, s_mask);
+        if (s_bad_mat != ~0ull) atomicMin(&out->first_bad_mat, s_bad_mat);
+        if (s_bad_rho != ~0ull) atomicMin(&out->first_bad_rho, s_bad_rho);
+    }
+}
+
 int grid_for(size_t n)
 {
     size_t g = (n + kThreads - 1) / kThreads;
@@ -229,6 +269,18 @@ int launch_rsd(const double *dose, const double *sd, const float *rho, size_t nv
     max_final_kernel<<<1, 32, 0, s>>>(partials, n_parts, result + 2);
     rsd_kernel<<<n_parts, kThreads, 0, s>>>(dose, sd, rho, nvox, result + 2, partials + n_parts, n_parts);
     rsd_final_kernel<<<1, 32, 0, s>>>(partials + n_parts, n_parts, result + 2, result);
+    return ok();
+}
+
+int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, PhantomScan *out,
+                        void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PhantomScan init{};
+    init.first_bad_mat = ~0ull;
+    init.first_bad_rho = ~0ull;
+    if (cudaMemcpyAsync(out, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess) return CTD_ECUDA;
+    scan_phantom_kernel<<<grid_for(nvox), kThreads, 0, s>>>(mat, rho, nvox, n_mat, out);
     return ok();
 }
 

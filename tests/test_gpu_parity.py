@@ -261,3 +261,38 @@ def test_memory_probes_report_rates(ctd):
                 ctd.ctd_probe_memory(c, *bad)
     finally:
         ctd.ctd_destroy(c)
+
+
+def test_phantom_checks_on_the_device(ctd, ctx):
+    # the voxel scan at creation names the first voxel that breaks a rule
+    nx, ny, nz = 64, 48, 40
+    mat = np.zeros(nx * ny * nz, dtype=np.uint8)
+    rho = np.ones(nx * ny * nz, dtype=np.float32)
+    mats = [I.WATER, I.BONE]
+
+    def make(m, r):
+        return ctd.ctd_create_phantom(ctx, nx, ny, nz, 0.5, 0.5, 0.5, m, r, mats)
+
+    def msg(m, r):
+        with pytest.raises(ctd.CtdError) as e:
+            make(m, r)
+        return str(e.value)
+
+    m1 = mat.copy()
+    m1[[100_000, 20_000]] = [2, 7]
+    assert "voxel 20000 has material 7" in msg(m1, rho)
+    for bad in (np.nan, np.inf, -1.0, -1e-30):
+        r1 = rho.copy()
+        r1[[99_999, 5_001]] = bad
+        assert "voxel 5001 has an invalid density" in msg(mat, r1)
+    r1 = rho.copy()
+    r1[4_000] = np.nan
+    assert "voxel 3000 has material" in msg(np.where(np.arange(mat.size) == 3000, 5, mat).astype(np.uint8), r1)
+    assert "voxel 4000 has an invalid density" in msg(np.where(np.arange(mat.size) == 5000, 5, mat).astype(np.uint8), r1)
+    # -0 is a valid density
+    m2 = mat.copy()
+    m2[:10] = 1
+    r2 = rho.copy()
+    r2[:10] = -0.0
+    h = make(m2, r2)
+    ctd.ctd_destroy_phantom(ctx, h)

@@ -74,6 +74,28 @@ const std::vector<float> &angular_surface(ctd_ctx *ctx, int kind, double q0, con
     return ctx->surfaces.emplace(key, std::move(f)).first->second;
 }
 
+// Surfaces [k][n_e][n_zeta] as cells [k][n_e - 1][n_zeta - 1][4]: the corners
+// S[j][i], S[j][i+1], S[j+1][i], S[j+1][i+1] of the bilinear lookup in cell (j, i)
+static std::vector<float> surface_cells(const std::vector<float> &rows, int n_e, int n_zeta)
+{
+    const size_t row = static_cast<size_t>(n_e) * n_zeta;
+    const size_t cells = static_cast<size_t>(n_e - 1) * (n_zeta - 1);
+    const size_t k_max = rows.size() / row;
+    std::vector<float> out(k_max * cells * 4);
+    for (size_t k = 0; k < k_max; ++k)
+        for (int j = 0; j + 1 < n_e; ++j)
+            for (int i = 0; i + 1 < n_zeta; ++i) {
+                const float *r0 = &rows[k * row + static_cast<size_t>(j) * n_zeta + i];
+                const float *r1 = r0 + n_zeta;
+                float *o = &out[((k * (n_e - 1) + j) * (n_zeta - 1) + i) * 4];
+                o[0] = r0[0];
+                o[1] = r0[1];
+                o[2] = r1[0];
+                o[3] = r1[1];
+            }
+    return out;
+}
+
 int build_tables(ctd_ctx *ctx, Phantom &P)
 {
     if (P.tables_ok) return CTD_OK;
@@ -113,14 +135,17 @@ int build_tables(ctd_ctx *ctx, Phantom &P)
                                           : angular_surface(ctx, 1, P.mats[m].q0, nullptr, ph.e_min_kev, n_e, ph.n_zeta);
         std::copy(r.begin(), r.end(), P.h_rs.begin() + m * row);
     }
+    // the device holds each surface as cells of the four corners of a bilinear lookup
+    const std::vector<float> cs_cells = surface_cells(P.h_cs, n_e, ph.n_zeta);
+    const std::vector<float> rs_cells = surface_cells(P.h_rs, n_e, ph.n_zeta);
     int rc;
-    if ((rc = P.tab.ensure(P.h_tab.size())) || (rc = P.mm.ensure(n_e)) || (rc = P.cs.ensure(P.h_cs.size())) ||
-        (rc = P.rs.ensure(row * nm)))
+    if ((rc = P.tab.ensure(P.h_tab.size())) || (rc = P.mm.ensure(n_e)) || (rc = P.cs.ensure(cs_cells.size())) ||
+        (rc = P.rs.ensure(rs_cells.size())))
         return rc;
     CK(cudaMemcpyAsync(P.tab.p, P.h_tab.data(), P.h_tab.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(P.mm.p, P.h_mm.data(), n_e * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(P.cs.p, P.h_cs.data(), P.h_cs.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(P.rs.p, P.h_rs.data(), row * nm * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P.cs.p, cs_cells.data(), cs_cells.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(P.rs.p, rs_cells.data(), rs_cells.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     P.n_e = n_e;
     P.tables_ok = true;
@@ -181,7 +206,7 @@ void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
     q.mmax = P.mm.p;
     q.rsurf = P.rs.p;
     q.csurf = P.cs.p;
-    q.cs_stride = P.phys.compton_model == CTD_COMPTON_WH ? P.n_e * P.phys.n_zeta : 0;
+    q.cs_stride = P.phys.compton_model == CTD_COMPTON_WH ? (P.n_e - 1) * (P.phys.n_zeta - 1) : 0;
     if (P.fl_nu > 0) {
         q.fl_thr = P.fl_thr.p;
         q.fl_alias = P.fl_alias.p;
@@ -903,9 +928,9 @@ int ctd_sample_mu(ctd_ctx *ctx, ctd_phantom ph, int kind, int material, double e
     if (n == 0) return CTD_OK;
     DevBuf<double> buf;
     if ((rc = buf.ensure(n))) return rc;
-    const size_t row = static_cast<size_t>(P->n_e) * P->phys.n_zeta;
-    const float *surf = kind == 1 ? P->rs.p + material * row
-                                  : P->cs.p + (P->phys.compton_model == CTD_COMPTON_WH ? material * row : 0);
+    const size_t cell_floats = static_cast<size_t>(P->n_e - 1) * (P->phys.n_zeta - 1) * 4;
+    const float *surf = kind == 1 ? P->rs.p + material * cell_floats
+                                  : P->cs.p + (P->phys.compton_model == CTD_COMPTON_WH ? material * cell_floats : 0);
     CKS(ctd::launch_sample_mu(surf, P->phys.n_zeta, P->n_e, P->phys.e_min_kev, static_cast<float>(e_kev), seed, n,
                               buf.p, ctx->stream));
     CK(cudaMemcpyAsync(out, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

@@ -231,16 +231,17 @@ __device__ __forceinline__ int enode(float e, int e_min, int n_e, float &te)
     return j;
 }
 
-// bilinear lookup of mu(zeta, E) on a surface (Sec. 2.2.2)
+// bilinear lookup of mu(zeta, E) on a surface (Sec. 2.2.2); S holds the surface as
+// cells of the four corners of a lookup, [n_e - 1][n_zeta - 1] float4, so one
+// 16-byte read fetches them
 __device__ __forceinline__ float surface(const float *__restrict__ S, int n_zeta, int j, float te, float z)
 {
     const float zf = z * static_cast<float>(n_zeta - 1);
     int i = static_cast<int>(zf);
     if (i > n_zeta - 2) i = n_zeta - 2;
     const float a = zf - static_cast<float>(i);
-    const float *r0 = S + static_cast<size_t>(j) * n_zeta + i;
-    const float *r1 = r0 + n_zeta;
-    const float a0 = __ldg(r0), a1 = __ldg(r0 + 1), b0 = __ldg(r1), b1 = __ldg(r1 + 1);
+    const float4 c = __ldg(reinterpret_cast<const float4 *>(S) + (static_cast<size_t>(j) * (n_zeta - 1) + i));
+    const float a0 = c.x, a1 = c.y, b0 = c.z, b1 = c.w;
     const float lo = __fmaf_rn(a, a1 - a0, a0);
     const float hi = __fmaf_rn(a, b1 - b0, b0);
     float mu = __fmaf_rn(te, hi - lo, lo);

@@ -87,8 +87,10 @@ struct alignas(16) RequestDesc {
     const float *rho;            // [nvox] g/cm^3
     const float *tab;            // [n_mat][n_e][4]: c1, c2, c3 (cm^2/g), c3[j+1] - c3[j] in binary32
     const float *mmax;           // [n_e] majorant mu_max(E), 1/cm
-    const float *rsurf;          // [n_mat][n_e][n_zeta] R surfaces
-    const float *csurf;          // [n_c][n_e][n_zeta] C surfaces, material m at m * cs_stride
+    // R and C surfaces as cells of 4 floats, [n_e - 1][n_zeta - 1] per surface: cell (j, i)
+    // holds S[j][i], S[j][i+1], S[j+1][i], S[j+1][i+1], the corners of one bilinear lookup
+    const float *rsurf;          // [n_mat] surfaces of cells
+    const float *csurf;          // [n_c] surfaces of cells, material m at m * cs_stride cells
     const uint64_t *pref;        // [nbins+1] bin starts inside the batch
     const float *bin_lo;         // [nbins]
     const float *bin_hi;         // [nbins]
@@ -111,7 +113,7 @@ struct alignas(16) RequestDesc {
     float D, D2, ulo, uw, vlo, vw, a0t, awt;
     float hz0, hdz;              // z0 and z1 - z0 of a continuous helical trajectory
     int mode, max_real;
-    int cs_stride;               // 0 (one Klein-Nishina surface) or n_e * n_zeta (Waller-Hartree)
+    int cs_stride;               // 0 (one Klein-Nishina surface) or (n_e - 1)(n_zeta - 1) (Waller-Hartree)
     const uint32_t *fl_thr;      // [fl_n] fluence-map alias thresholds (fl_n = 0: no map)
     const int32_t *fl_alias;     // [fl_n]
     int fl_n, fl_nu;

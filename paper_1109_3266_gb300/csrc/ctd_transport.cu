@@ -340,8 +340,9 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
         deposit(q.tally, hit.idx, ph.e);
         return false;
     }
-    const float *S = hit.type == 1 ? q.csurf + static_cast<size_t>(hit.m) * q.cs_stride
-                                   : q.rsurf + static_cast<size_t>(hit.m) * sh.n_e * sh.n_zeta;
+    const float *S = hit.type == 1
+                         ? q.csurf + static_cast<size_t>(hit.m) * q.cs_stride * 4
+                         : q.rsurf + static_cast<size_t>(hit.m) * (sh.n_e - 1) * (sh.n_zeta - 1) * 4;
     const float mu = surface(S, sh.n_zeta, ph.j, ph.te, uni(hit.rz));
     if (hit.type == 1) {
         // Compton: E' = E / (1 + (E/mc^2)(1 - mu)), the electron gets E - E'

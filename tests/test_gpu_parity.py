@@ -296,3 +296,17 @@ def test_phantom_checks_on_the_device(ctd, ctx):
     r2[:10] = -0.0
     h = make(m2, r2)
     ctd.ctd_destroy_phantom(ctx, h)
+
+
+def test_odd_voxel_count_dose_equals_oracle(ctd, ctx, oracle):
+    # dose, stddev and energy per voxel on a grid of odd size
+    p = I.head(60_000, seed=12, phantom_seed=4, shape=(33, 31, 21), d=0.8)
+    assert p.phantom.nvox % 2 == 1
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    r32 = oracle.run(p, precision=32)
+    assert_counts_equal(st, r32.counts)
+    assert np.allclose(dose, r32.dose, rtol=1e-9, atol=1e-30)
+    assert np.allclose(sd, r32.std, rtol=1e-6, atol=1e-30)
+    ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
+    assert np.allclose(ed, r32.edep, rtol=1e-12, atol=1e-9)
+    ctd.ctd_destroy_phantom(ctx, h)

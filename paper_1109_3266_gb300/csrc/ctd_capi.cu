@@ -96,15 +96,36 @@ static std::vector<float> surface_cells(const std::vector<float> &rows, int n_e,
     return out;
 }
 
+// One material's node-table columns, from the context's cache
+static const std::vector<double> &material_columns(ctd_ctx *ctx, const ctd_material &mat, const ctd::Elements &el,
+                                                   int e_min, int n_e, int compton_model)
+{
+    std::vector<double> key{static_cast<double>(compton_model), static_cast<double>(e_min), static_cast<double>(n_e),
+                            mat.z_over_a, mat.a_mol, mat.z_eff, mat.q0, mat.sq0, static_cast<double>(el.n)};
+    for (int i = 0; i < el.n; ++i) {
+        key.push_back(static_cast<double>(el.z[i]));
+        key.push_back(el.count[i]);
+    }
+    auto it = ctx->columns.find(key);
+    if (it != ctx->columns.end()) return it->second;
+    if (ctx->columns.size() >= 256) ctx->columns.clear();
+    std::vector<double> col(static_cast<size_t>(n_e) * 3);
+    ctd::material_columns(mat, el, e_min, n_e, compton_model, col.data());
+    return ctx->columns.emplace(std::move(key), std::move(col)).first->second;
+}
+
 int build_tables(ctd_ctx *ctx, Phantom &P)
 {
     if (P.tables_ok) return CTD_OK;
     const ctd_physics &ph = P.phys;
     const int n_e = ph.e_max_kev - ph.e_min_kev + 1;
     const int nm = static_cast<int>(P.mats.size());
-    std::vector<double> cum, mmax;
-    ctd::build_tables(P.mats, P.els, P.rho_max, P.present, ph.e_min_kev, n_e, ph.majorant_scale, ph.compton_model,
-                      cum, mmax);
+    std::vector<double> cum(static_cast<size_t>(nm) * n_e * 3), mmax;
+    for (int m = 0; m < nm; ++m) {
+        const std::vector<double> &col = material_columns(ctx, P.mats[m], P.els[m], ph.e_min_kev, n_e, ph.compton_model);
+        std::copy(col.begin(), col.end(), cum.begin() + static_cast<size_t>(m) * n_e * 3);
+    }
+    ctd::build_majorant(cum, P.rho_max, P.present, n_e, ph.majorant_scale, mmax);
     P.h_tab.assign(static_cast<size_t>(nm) * n_e * 4, 0.0f);
     for (size_t i = 0; i < static_cast<size_t>(nm) * n_e; ++i)
         for (int c = 0; c < 3; ++c) P.h_tab[i * 4 + c] = static_cast<float>(cum[i * 3 + c]);

@@ -165,6 +165,9 @@ struct ctd_ctx {
     // angular surfaces by (kind, q0, e_min, n_e, n_zeta[, the elements' (Z, count) pairs]):
     // they do not depend on the phantom
     std::map<std::vector<double>, std::vector<float>> surfaces;
+    // node-table columns of a material by (Compton model, e_min, n_e, its parameters and
+    // elements): the Waller-Hartree and independent-atom totals are Simpson integrals
+    std::map<std::vector<double>, std::vector<double>> columns;
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> lane_done;
     cudaEvent_t fork_event = nullptr;

@@ -47,11 +47,14 @@ double mu_compton_wh(const ctd_material &m, double e_kev);
 double sigma_rayleigh_iaa(const Elements &el, double e_kev);
 double mu_rayleigh_iaa(const ctd_material &m, const Elements &el, double e_kev);
 
-// Node tables: cum[(m*n_e + j)*3 + c] cumulative mass attenuation; mmax[j] majorant.
-// els[m].n > 0 gives material m the independent-atom Rayleigh total.
-void build_tables(const std::vector<ctd_material> &mats, const std::vector<Elements> &els,
-                  const std::vector<double> &rho_max, const std::vector<int> &present, int e_min, int n_e,
-                  double scale, int compton_model, std::vector<double> &cum, std::vector<double> &mmax);
+// Node-table columns of one material: out[j*3 + c] the cumulative mass attenuation
+// (photoelectric, + Compton, + Rayleigh) at node e_min + j; el.n > 0 gives the
+// independent-atom Rayleigh total.
+void material_columns(const ctd_material &mat, const Elements &el, int e_min, int n_e, int compton_model,
+                      double *out);
+// mmax[j]: the majorant scale * max over present materials of rho_max[m] * cum[(m*n_e + j)*3 + 2]
+void build_majorant(const std::vector<double> &cum, const std::vector<double> &rho_max, const std::vector<int> &present,
+                    int n_e, double scale, std::vector<double> &mmax);
 // Inverse-cdf surface rows for node energies e_min..e_min+n_e-1: kind 0 Klein-Nishina,
 // 1 Rayleigh of form-factor width q0, 2 Waller-Hartree of scattering-function width q0,
 // 3 Rayleigh with the independent-atom form factor of *el.

@@ -158,25 +158,26 @@ double mu_rayleigh(const ctd_material &m, double e_kev)
     return ((sigma * kBarn) * kNA) / m.a_mol;
 }
 
-void build_tables(const std::vector<ctd_material> &mats, const std::vector<Elements> &els,
-                  const std::vector<double> &rho_max, const std::vector<int> &present, int e_min, int n_e,
-                  double scale, int compton_model, std::vector<double> &cum, std::vector<double> &mmax)
+void material_columns(const ctd_material &mat, const Elements &el, int e_min, int n_e, int compton_model,
+                      double *out)
 {
-    const size_t nm = mats.size();
-    cum.assign(nm * n_e * 3, 0.0);
-    mmax.assign(n_e, 0.0);
-    for (size_t m = 0; m < nm; ++m) {
-        for (int j = 0; j < n_e; ++j) {
-            const double e = static_cast<double>(e_min + j);
-            const double pe = mu_pe(mats[m], e);
-            const double c = compton_model == CTD_COMPTON_WH ? mu_compton_wh(mats[m], e) : mu_compton(mats[m], e);
-            const double r = els[m].n > 0 ? mu_rayleigh_iaa(mats[m], els[m], e) : mu_rayleigh(mats[m], e);
-            double *dst = &cum[(m * n_e + j) * 3];
-            dst[0] = pe;
-            dst[1] = pe + c;
-            dst[2] = (pe + c) + r;
-        }
+    for (int j = 0; j < n_e; ++j) {
+        const double e = static_cast<double>(e_min + j);
+        const double pe = mu_pe(mat, e);
+        const double c = compton_model == CTD_COMPTON_WH ? mu_compton_wh(mat, e) : mu_compton(mat, e);
+        const double r = el.n > 0 ? mu_rayleigh_iaa(mat, el, e) : mu_rayleigh(mat, e);
+        double *dst = out + static_cast<size_t>(j) * 3;
+        dst[0] = pe;
+        dst[1] = pe + c;
+        dst[2] = (pe + c) + r;
     }
+}
+
+void build_majorant(const std::vector<double> &cum, const std::vector<double> &rho_max, const std::vector<int> &present,
+                    int n_e, double scale, std::vector<double> &mmax)
+{
+    const size_t nm = rho_max.size();
+    mmax.assign(n_e, 0.0);
     // mu_max(E): the largest total attenuation anywhere in the volume
     for (int j = 0; j < n_e; ++j) {
         double best = 0.0;

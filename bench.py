@@ -338,6 +338,12 @@ def run_ours(args):
         ctd.ctd_set_spectrum(ctx, h2, p.spectrum.e_lo, p.spectrum.e_hi, p.spectrum.w)
         if s.fluence is not None:
             ctd.ctd_set_fluence(ctx, h2, s.fluence)
+        phy = p.physics
+        ctd.ctd_set_physics(ctx, h2, phy.e_min, phy.e_max, phy.n_zeta, phy.majorant_scale, phy.mode, phy.max_real,
+                            phy.compton)
+        if phy.rayleigh == "iaa":
+            for m, mat in enumerate(ph.materials):
+                ctd.ctd_set_material_elements(ctx, h2, m, mat.elements)
         ctd.ctd_run(ctx, h2, p.n_hist, seed, p.n_batches)
         ctd._check(L.ctd_get_dose_and_stddev(ctx, h2, ctd._dp(dose_h), ctd._dp(sd_h), nvox, ctd.C.byref(st)))
         ctd.ctd_destroy_phantom(ctx, h2)

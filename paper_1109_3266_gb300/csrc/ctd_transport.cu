@@ -385,7 +385,7 @@ struct WarpPool {
 
 struct Queue {
     uint64_t *h;
-    float *f;   // [7][kQueue]: x y z ux uy uz e
+    float *f;   // [7][kQueue]: x y z (voxel units) ux uy uz e
     WarpPool *pool;
 };
 

@@ -307,15 +307,17 @@ int ctd_cancel(ctd_ctx *ctx, ctd_req_id id);
  * that is n_probe histories over every 1 keV bin) for blocks of 256 threads,
  * 3 or 4 per SM, or of 128 threads, 7 or 8 per SM; claims of {64, 256, 1024}
  * histories; flight caps of {1, 2, 4, 8} (48 shapes and the context's own),
- * and keeps the fastest shape in the context for later runs.  Results of a run do
- * not depend on the launch shape (up to the order of binary64 additions). */
+ * each best of two.  The four fastest and the context's own shape are then timed
+ * again on probes five times longer, and the fastest of those is kept in the
+ * context for later runs.  Results of a run do not depend on the launch shape
+ * (up to the order of binary64 additions). */
 typedef struct {
     int blocks_per_sm;
     int chunk;
     int flight_cap;
-    int n_tried;
-    double histories_per_s;    /* of the chosen shape on the probe */
-    double baseline_per_s;     /* of the shape the context had before */
+    int n_tried;               /* shapes timed in the first round */
+    double histories_per_s;    /* of the chosen shape on the longer probe */
+    double baseline_per_s;     /* of the shape the context had before, on the longer probe */
     int threads_per_block;
 } ctd_tune_result;
 

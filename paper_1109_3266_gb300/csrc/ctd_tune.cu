@@ -82,31 +82,63 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
             for (int cap : {1, 2, 4, 8})
                 if (!(b[0] == old_threads && b[1] == old_bps && chunk == old_chunk && cap == old_cap))
                     shapes.push_back({b[0], b[1], chunk, cap});
-    double best = 1e300, base = 0.0;
-    Shape pick = shapes[0];
-    for (size_t k = 0; k < shapes.size(); ++k) {
-        ctx->threads = shapes[k].threads;
-        ctx->blocks_per_sm = shapes[k].bps;
-        ctx->chunk = shapes[k].chunk;
-        ctx->flight_cap = shapes[k].cap;
-        double t_min = 1e300;
+    // best of two timed probes of histories [0, n) of batch 0 in shape s
+    auto time_shape = [&](const Shape &s, uint64_t n, double &t_min) -> int {
+        ctx->threads = s.threads;
+        ctx->blocks_per_sm = s.bps;
+        ctx->chunk = s.chunk;
+        ctx->flight_cap = s.cap;
+        t_min = 1e300;
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
-            if ((rc = transport(ctx, *P, q, 0, 0, 0, n_probe, P->tally.p, 0))) {
-                ctx->threads = old_threads;
-                ctx->blocks_per_sm = old_bps;
-                ctx->chunk = old_chunk;
-                ctx->flight_cap = old_cap;
-                return rc;
-            }
+            int e;
+            if ((e = transport(ctx, *P, q, 0, 0, 0, n, P->tally.p, 0))) return e;
             CK(cudaStreamSynchronize(ctx->stream));
             float ms = 0.0f;
             CK(cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]));
             t_min = std::min(t_min, static_cast<double>(ms) * 1e-3);
         }
-        if (k == 0) base = t_min;
-        if (t_min < best) {
-            best = t_min;
+        return CTD_OK;
+    };
+    auto restore = [&]() {
+        ctx->threads = old_threads;
+        ctx->blocks_per_sm = old_bps;
+        ctx->chunk = old_chunk;
+        ctx->flight_cap = old_cap;
+    };
+    // round 1: every shape on n_probe histories
+    std::vector<std::pair<double, size_t>> t1;
+    for (size_t k = 0; k < shapes.size(); ++k) {
+        double t;
+        if ((rc = time_shape(shapes[k], n_probe, t))) {
+            restore();
+            return rc;
+        }
+        t1.push_back({t, k});
+    }
+    // round 2: the four fastest and the current shape on 5 n_probe histories (short
+    // probes overrate shapes whose blocks drain a launch's tail sooner)
+    std::sort(t1.begin(), t1.end());
+    std::vector<size_t> finalists{0};
+    for (size_t r = 0; r < t1.size() && finalists.size() < 5; ++r)
+        if (t1[r].second != 0) finalists.push_back(t1[r].second);
+    const uint64_t n2 = 5 * n_probe;
+    if ((rc = prepare_run(ctx, *P, 10 * n2, 10))) {
+        restore();
+        return rc;
+    }
+    fill_request(*P, seed, q);
+    double best = 1e300, base = 0.0;
+    Shape pick = shapes[0];
+    for (size_t k : finalists) {
+        double t;
+        if ((rc = time_shape(shapes[k], n2, t))) {
+            restore();
+            return rc;
+        }
+        if (k == 0) base = t;
+        if (t < best) {
+            best = t;
             pick = shapes[k];
         }
     }
@@ -123,8 +155,8 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
         out->chunk = pick.chunk;
         out->flight_cap = pick.cap;
         out->n_tried = static_cast<int>(shapes.size());
-        out->histories_per_s = static_cast<double>(n_probe) / best;
-        out->baseline_per_s = static_cast<double>(n_probe) / base;
+        out->histories_per_s = static_cast<double>(n2) / best;
+        out->baseline_per_s = static_cast<double>(n2) / base;
     }
     return CTD_OK;
 }

@@ -171,9 +171,17 @@ def test_majorant_scale_counts_bit_exact(ctd, ctx, oracle, scale):
 
 
 # ----------------------------------------------------------------- full-size workloads, sampled
+def _physics(p, **kw):
+    import dataclasses
+    return I.scaled(p, physics=dataclasses.replace(p.physics, **kw))
+
+
 @pytest.mark.parametrize("make,ranges", [
     (lambda: I.cbct_water(), [(0, 20_000), (123_456_789, 123_476_789), (1_000_000_000 - 15_000, 1_000_000_000)]),
     (lambda: I.head(), [(0, 10_000), (1_999_990_000, 2_000_000_000)]),
+    (lambda: _physics(I.cbct_water(), compton="wh"), [(0, 10_000), (777_777_777, 777_787_777)]),
+    (lambda: _physics(I.cbct_water(), rayleigh="iaa"), [(0, 10_000), (999_990_000, 1_000_000_000)]),
+    (lambda: _physics(I.head(), compton="wh", rayleigh="iaa"), [(1_234_567_890, 1_234_575_890)]),
 ])
 def test_full_size_sampled_history_ranges(ctd, ctx, oracle, make, ranges):
     p = make()

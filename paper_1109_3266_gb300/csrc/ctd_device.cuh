@@ -183,13 +183,25 @@ __device__ __forceinline__ unsigned long long kev_fixed(float e)
     return ex >= 0 ? (m << ex) : (m >> -ex);
 }
 
+// binary32 -> binary64 for positive normal numbers only: the exponent rebiased and
+// the significand moved into place (the general widen() without its branches)
+__device__ __forceinline__ double widen_normal(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t hi = (((u >> 23) + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
+
 // Tally deposit of a non-negative binary32 energy into the binary64 grid, as a
 // global reduction that returns nothing (a fire-and-forget L2 atomic), also
-// when the grid's address was read from shared memory.
+// when the grid's address was read from shared memory.  A positive deposit is a
+// normal number: a photon energy (at least 1 keV) or the difference of two
+// energies of at least 1 keV, which is a multiple of their binary32 ulp.
 __device__ __forceinline__ void deposit(double *tally, size_t idx, float e)
 {
     if (e > 0.0f)
-        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(tally + idx)), "d"(widen(e))
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(tally + idx)),
+                     "d"(widen_normal(e))
                      : "memory");
 }
 

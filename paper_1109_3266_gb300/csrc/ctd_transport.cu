@@ -265,15 +265,11 @@ enum { kEnded = 0, kFictitious = 1, kReal = 2 };
 // One Woodcock flight (Sec. 2.1): free path against mu_max(E), the move, the
 // escape test, the voxel and the interaction type.  s_tab and s_mm are the
 // request's attenuation table and majorant in shared memory.
+// The caller keeps ph.step below kMaxSteps (the history's step limit).
 template <bool kKeys>
 __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc &q, const float4 *__restrict__ s_tab,
                                       Photon &ph, LaneCounts &cnt, Hit &hit)
 {
-    if (ph.step >= kMaxSteps) {
-        cnt.event(kCntAborted);
-        cnt.escaped(ph.e);
-        return kEnded;
-    }
     const U4 b = draw<kKeys>(q, ph.h, ph.step, kStreamTransport);
     ph.step++;
     const int n_e = sh.n_e;
@@ -486,14 +482,24 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
             continue;
         }
         if (alive) {
-            // flights until a real interaction, the escape or flight_cap flights; then the interaction
-            Hit hit;
-            int f, k = 0;
-            do {
-                f = flight<kKeys>(P.sh, q, s_tab, ph, cnt, hit);
-            } while (f == kFictitious && ++k < P.flight_cap);
-            if (f == kEnded) alive = false;
-            else if (f == kReal) alive = interact(P.sh, q, s_mm, ph, hit, cnt);
+            // flights until a real interaction, the escape or flight_cap flights; then the
+            // interaction.  A run stops short of the history's step limit; a history that
+            // has reached it is aborted when its next run would start.
+            const uint32_t room = kMaxSteps - ph.step;
+            const int lim = room < static_cast<uint32_t>(P.flight_cap) ? static_cast<int>(room) : P.flight_cap;
+            if (lim == 0) {
+                cnt.event(kCntAborted);
+                cnt.escaped(ph.e);
+                alive = false;
+            } else {
+                Hit hit;
+                int f, k = 0;
+                do {
+                    f = flight<kKeys>(P.sh, q, s_tab, ph, cnt, hit);
+                } while (f == kFictitious && ++k < lim);
+                if (f == kEnded) alive = false;
+                else if (f == kReal) alive = interact(P.sh, q, s_mm, ph, hit, cnt);
+            }
         }
     }
 }

@@ -260,11 +260,12 @@ struct Hit {
     uint32_t rz, rw;  // the step's random words for zeta and phi
 };
 
-enum { kEnded = 0, kFictitious = 1, kReal = 2 };
+enum { kEscaped = 0, kFictitious = 1, kReal = 2 };
 
 // One Woodcock flight (Sec. 2.1): free path against mu_max(E), the move, the
 // escape test, the voxel and the interaction type.  s_tab and s_mm are the
-// request's attenuation table and majorant in shared memory.
+// request's attenuation table and majorant in shared memory.  An escape is
+// counted by the caller, outside the loop of flights.
 // The caller keeps ph.step below kMaxSteps (the history's step limit).
 template <bool kKeys>
 __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc &q, const float4 *__restrict__ s_tab,
@@ -287,11 +288,8 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
     // is never -0 (the entry point is clamped to +0 at least, and adding a nonzero
     // or +0 displacement to a value other than -0 never gives -0)
     if (!(__float_as_uint(fx) < __float_as_uint(q.fnx) && __float_as_uint(fy) < __float_as_uint(q.fny) &&
-          __float_as_uint(fz) < __float_as_uint(q.fnz))) {
-        cnt.event(kCntEscaped);
-        cnt.escaped(ph.e);
-        return kEnded;
-    }
+          __float_as_uint(fz) < __float_as_uint(q.fnz)))
+        return kEscaped;
     const uint32_t idx = static_cast<uint32_t>(static_cast<int>(fx)) +
                          static_cast<uint32_t>(q.nx) *
                              (static_cast<uint32_t>(static_cast<int>(fy)) +
@@ -497,8 +495,13 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
                 do {
                     f = flight<kKeys>(P.sh, q, s_tab, ph, cnt, hit);
                 } while (f == kFictitious && ++k < lim);
-                if (f == kEnded) alive = false;
-                else if (f == kReal) alive = interact(P.sh, q, s_mm, ph, hit, cnt);
+                if (f == kEscaped) {
+                    cnt.event(kCntEscaped);
+                    cnt.escaped(ph.e);
+                    alive = false;
+                } else if (f == kReal) {
+                    alive = interact(P.sh, q, s_mm, ph, hit, cnt);
+                }
             }
         }
     }

@@ -42,8 +42,8 @@ LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes issue per SM clock
 # (smsp__inst_executed x thread-per-instruction ratio / histories) and DRAM
 # bytes per launch (dram__bytes_read + dram__bytes_write).
 KERNEL_PROFILE = {
-    "cbct_water": {"lane_inst_per_history": 2687.0, "dram_bytes_per_launch": 9.16e9, "histories_per_launch": 1e8},
-    "head": {"lane_inst_per_history": 3241.0, "dram_bytes_per_launch": 13.42e9, "histories_per_launch": 2e8},
+    "cbct_water": {"lane_inst_per_history": 2603.0, "dram_bytes_per_launch": 9.16e9, "histories_per_launch": 1e8},
+    "head": {"lane_inst_per_history": 3128.0, "dram_bytes_per_launch": 13.42e9, "histories_per_launch": 2e8},
 }
 
 

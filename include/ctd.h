@@ -315,7 +315,7 @@ typedef struct {
     int blocks_per_sm;
     int chunk;
     int flight_cap;
-    int n_tried;               /* shapes timed in the first round */
+    int n_tried;               /* shapes timed in the first pass */
     double histories_per_s;    /* of the chosen shape on the longer probe */
     double baseline_per_s;     /* of the shape the context had before, on the longer probe */
     int threads_per_block;

@@ -106,7 +106,7 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
         ctx->chunk = old_chunk;
         ctx->flight_cap = old_cap;
     };
-    // round 1: every shape on n_probe histories
+    // first pass: every shape on n_probe histories
     std::vector<std::pair<double, size_t>> t1;
     for (size_t k = 0; k < shapes.size(); ++k) {
         double t;
@@ -116,7 +116,7 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
         }
         t1.push_back({t, k});
     }
-    // round 2: the four fastest and the current shape on 5 n_probe histories (short
+    // second pass: the four fastest and the current shape on 5 n_probe histories (short
     // probes overrate shapes whose blocks drain a launch's tail sooner)
     std::sort(t1.begin(), t1.end());
     std::vector<size_t> finalists{0};

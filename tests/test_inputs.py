@@ -38,3 +38,19 @@ def test_batched_requests_are_reproducible():
     assert [p.n_hist for p in a] == [p.n_hist for p in b]
     assert all(1e7 <= p.n_hist <= 1e9 for p in a)
     assert [p.seed for p in a] == list(range(1000, 1008))
+
+
+def test_material_compositions_reproduce_their_mass_fractions():
+    from paper_1109_3266_gb300 import inputs as I
+    assert I.WATER.elements == ((1, 2.0), (8, 1.0))
+    for m in (I.SOFT_TISSUE, I.BRAIN, I.BONE, I.AIR):
+        mass = [n * I.ATOMIC_WEIGHT[z] for z, n in m.elements]
+        # the atoms of one formula unit weigh its molar mass
+        assert abs(sum(mass) - m.a_mol) < 1e-9 * m.a_mol
+        # and electrons per gram agree with the material's Z/A to about 1 %
+        zsum = sum(z * n for z, n in m.elements)
+        assert abs(zsum / m.a_mol - m.z_over_a) < 0.012 * m.z_over_a, m.name
+        assert all(n > 0 for _, n in m.elements) and len(m.elements) <= 16
+    ev = dict(I.BONE.elements)
+    w_ca = ev[20] * I.ATOMIC_WEIGHT[20] / I.BONE.a_mol
+    assert abs(w_ca - 0.225) < 1e-12

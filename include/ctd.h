@@ -213,6 +213,29 @@ int ctd_set_spectrum(ctd_ctx *ctx, ctd_phantom ph, const double *e_lo, const dou
  * 1 <= e_min < kvp <= 100000, mm_al >= 0, else CTD_EINVAL. */
 int ctd_spectrum_kramers(int kvp, double mm_al, int e_min, double *e_lo, double *e_hi, double *w, int *nbins);
 
+/* Host physics of one material, as the library builds it for a phantom (host
+ * only; needs no context or GPU).  Elements (n_el > 0, z, count) select the
+ * independent-atom Rayleigh form factor as in ctd_set_material_elements; n_el = 0
+ * the analytic one.  Node energies E_j = e_min_kev + j, j = 0 .. e_max_kev - e_min_kev.
+ *
+ * ctd_material_columns: the binary64 node-table columns out[3 j + c] (cm^2/g) =
+ * photoelectric, + Compton (compton_model), + Rayleigh at E_j (Sec. 2.1); the
+ * device holds them rounded to binary32.
+ *
+ * ctd_angular_surface: the binary64 inverse-CDF rows out[j n_zeta + i], mu at
+ * zeta = i / (n_zeta - 1) and E_j (Sec. 2.2.2): kind 0 the Klein-Nishina C
+ * surface (Eq. 2 with S = 1), 1 the material's R surface (Eq. 1), 2 its
+ * Waller-Hartree C surface (Eq. 2 with S of width mat->sq0); the device holds
+ * them rounded to binary32.
+ *
+ * Arrays are the caller's; out holds 3 n_e or n_e n_zeta doubles.  Errors:
+ * CTD_EINVAL (null pointers, a bad node grid, n_zeta outside 2..2^20, an unknown
+ * model or kind, element values as in ctd_set_material_elements). */
+int ctd_material_columns(const ctd_material *mat, int n_el, const int *z, const double *count, int e_min_kev,
+                         int e_max_kev, int compton_model, double *out);
+int ctd_angular_surface(int kind, const ctd_material *mat, int n_el, const int *z, const double *count,
+                        int e_min_kev, int e_max_kev, int n_zeta, double *out);
+
 /* Transport n_histories in n_batches (>= 2) batches (Sec. 2.2.1) with random
  * numbers keyed by seed; afterwards mean dose and batch uncertainty are ready
  * for ctd_get_dose_and_stddev.  Blocks until the device is done. */

@@ -793,6 +793,64 @@ int ctd_spectrum_kramers(int kvp, double mm_al, int e_min, double *e_lo, double 
     return CTD_OK;
 }
 
+// elements of ctd_material_columns / ctd_angular_surface, checked as in ctd_set_material_elements
+static int host_elements(int n_el, const int *z, const double *count, ctd::Elements &el)
+{
+    if (n_el < 0 || n_el > CTD_MAX_ELEMENTS) return fail(CTD_EINVAL, "n_el must be 0..%d", CTD_MAX_ELEMENTS);
+    if (n_el > 0 && (!z || !count)) return fail(CTD_EINVAL, "null element arrays");
+    el.n = n_el;
+    for (int i = 0; i < n_el; ++i) {
+        if (z[i] < 1 || z[i] > 100) return fail(CTD_EINVAL, "atomic number %d out of 1..100", z[i]);
+        if (!(count[i] > 0.0) || !std::isfinite(count[i])) return fail(CTD_EINVAL, "atom counts must be finite and > 0");
+        el.z[i] = z[i];
+        el.count[i] = count[i];
+    }
+    return CTD_OK;
+}
+
+static int host_grid(const ctd_material *mat, int e_min_kev, int e_max_kev, const double *out)
+{
+    if (!mat || !out) return fail(CTD_EINVAL, "null pointer argument");
+    if (!(mat->z_over_a > 0 && mat->a_mol > 0 && mat->z_eff > 0) || !std::isfinite(mat->q0) || !std::isfinite(mat->sq0))
+        return fail(CTD_EINVAL, "material has non-positive or non-finite parameters");
+    if (e_min_kev < 1 || e_max_kev <= e_min_kev || e_max_kev > 100000)
+        return fail(CTD_EINVAL, "node grid must satisfy 1 <= e_min < e_max <= 100000");
+    return CTD_OK;
+}
+
+int ctd_material_columns(const ctd_material *mat, int n_el, const int *z, const double *count, int e_min_kev,
+                         int e_max_kev, int compton_model, double *out)
+{
+    g_error.clear();
+    int rc;
+    ctd::Elements el;
+    if ((rc = host_grid(mat, e_min_kev, e_max_kev, out)) || (rc = host_elements(n_el, z, count, el))) return rc;
+    if (compton_model != CTD_COMPTON_KN && compton_model != CTD_COMPTON_WH) return fail(CTD_EINVAL, "unknown Compton model");
+    ctd::material_columns(*mat, el, e_min_kev, e_max_kev - e_min_kev + 1, compton_model, out);
+    return CTD_OK;
+}
+
+int ctd_angular_surface(int kind, const ctd_material *mat, int n_el, const int *z, const double *count,
+                        int e_min_kev, int e_max_kev, int n_zeta, double *out)
+{
+    g_error.clear();
+    int rc;
+    ctd::Elements el;
+    if ((rc = host_grid(mat, e_min_kev, e_max_kev, out)) || (rc = host_elements(n_el, z, count, el))) return rc;
+    if (n_zeta < 2 || n_zeta > (1 << 20)) return fail(CTD_EINVAL, "n_zeta must be 2..2^20");
+    const int n_e = e_max_kev - e_min_kev + 1;
+    switch (kind) {
+    case 0: ctd::build_surface(0, 0.0, nullptr, e_min_kev, n_e, n_zeta, out); break;
+    case 1:
+        if (el.n > 0) ctd::build_surface(3, 0.0, &el, e_min_kev, n_e, n_zeta, out);
+        else ctd::build_surface(1, mat->q0, nullptr, e_min_kev, n_e, n_zeta, out);
+        break;
+    case 2: ctd::build_surface(2, mat->sq0, nullptr, e_min_kev, n_e, n_zeta, out); break;
+    default: return fail(CTD_EINVAL, "kind is 0 (Klein-Nishina C), 1 (R) or 2 (Waller-Hartree C)");
+    }
+    return CTD_OK;
+}
+
 int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches)
 {
     int rc;

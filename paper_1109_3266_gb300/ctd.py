@@ -129,6 +129,10 @@ def lib():
         L.ctd_probe_memory.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, dp]
         L.ctd_set_fluence.argtypes = [P, C.c_int32, C.c_int, C.c_int, dp]
         L.ctd_spectrum_kramers.argtypes = [C.c_int, C.c_double, C.c_int, dp, dp, dp, C.POINTER(C.c_int)]
+        L.ctd_material_columns.argtypes = [C.POINTER(ctd_material), C.c_int, C.POINTER(C.c_int), dp, C.c_int,
+                                           C.c_int, C.c_int, dp]
+        L.ctd_angular_surface.argtypes = [C.c_int, C.POINTER(ctd_material), C.c_int, C.POINTER(C.c_int), dp,
+                                          C.c_int, C.c_int, C.c_int, dp]
         L.ctd_get_fluence_table.argtypes = [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_uint32),
                                             C.POINTER(C.c_int32)]
         _lib = L
@@ -196,9 +200,7 @@ def ctd_set_physics(ctx, ph, e_min_kev=1, e_max_kev=150, n_zeta=1024, majorant_s
 def ctd_set_material_elements(ctx, ph, material, elements):
     """Independent-atom Rayleigh form factor for one material: elements is
     ((Z, atoms per formula unit), ...); empty restores the analytic form factor."""
-    n = len(elements)
-    z = (C.c_int * max(n, 1))(*[int(e[0]) for e in elements])
-    cnt = np.ascontiguousarray([float(e[1]) for e in elements] or [0.0], dtype=np.float64)
+    n, z, cnt = _element_arrays(elements)
     _check(lib().ctd_set_material_elements(ctx, ph, int(material), n, z, _dp(cnt)))
 
 
@@ -359,6 +361,38 @@ def ctd_spectrum_kramers(kvp, mm_al, e_min=1):
     lo, hi, w = (np.empty(n.value) for _ in range(3))
     _check(lib().ctd_spectrum_kramers(int(kvp), float(mm_al), int(e_min), _dp(lo), _dp(hi), _dp(w), C.byref(n)))
     return lo, hi, w
+
+
+def _element_arrays(elements):
+    n = len(elements)
+    z = (C.c_int * max(n, 1))(*[int(e[0]) for e in elements])
+    cnt = np.ascontiguousarray([float(e[1]) for e in elements] or [0.0], dtype=np.float64)
+    return n, z, cnt
+
+
+def ctd_material_columns(material, e_min_kev=1, e_max_kev=150, compton="kn", elements=()):
+    """Host physics: the binary64 node-table columns [n_e][3] of one material
+    (photoelectric, + Compton, + Rayleigh); elements select the independent-atom
+    Rayleigh form factor."""
+    m = ctd_material(material.z_over_a, material.a_mol, material.z_eff, material.q0, material.sq0)
+    c = {"kn": CTD_COMPTON_KN, "wh": CTD_COMPTON_WH}[compton] if isinstance(compton, str) else int(compton)
+    n, z, cnt = _element_arrays(elements)
+    out = np.empty((e_max_kev - e_min_kev + 1, 3), dtype=np.float64)
+    _check(lib().ctd_material_columns(C.byref(m), n, z, _dp(cnt), int(e_min_kev), int(e_max_kev), c, _dp(out)))
+    return out
+
+
+def ctd_angular_surface(kind, material, e_min_kev=1, e_max_kev=150, n_zeta=1024, elements=()):
+    """Host physics: the binary64 surface rows [n_e][n_zeta]; kind "kn" (C surface),
+    "rayleigh" (R surface; elements select the independent-atom form factor) or
+    "wh" (Waller-Hartree C surface)."""
+    k = {"kn": 0, "rayleigh": 1, "wh": 2}[kind] if isinstance(kind, str) else int(kind)
+    m = ctd_material(material.z_over_a, material.a_mol, material.z_eff, material.q0, material.sq0)
+    n, z, cnt = _element_arrays(elements)
+    out = np.empty((e_max_kev - e_min_kev + 1, n_zeta), dtype=np.float64)
+    _check(lib().ctd_angular_surface(k, C.byref(m), n, z, _dp(cnt), int(e_min_kev), int(e_max_kev), int(n_zeta),
+                                     _dp(out)))
+    return out
 
 
 def ctd_set_fluence(ctx, ph, f):

@@ -81,6 +81,15 @@ int main(void)
            sizeof(ctd_tune_result));
     printf("%zu %zu %zu\n", offsetof(ctd_options, shared_launch), offsetof(ctd_source, z1_cm),
            offsetof(ctd_physics, compton_model));
+    {
+        /* host physics: water's node-table columns with the independent-atom form factor */
+        const ctd_material water = {0.5551, 18.015, 7.42, 1.0, 0.55};
+        const int z[2] = {1, 8};
+        const double n[2] = {2.0, 1.0};
+        double col[3 * 150];
+        if (ctd_material_columns(&water, 2, z, n, 1, 150, CTD_COMPTON_WH, col) != CTD_OK) return 4;
+        printf("%.17g %.17g\n", col[3 * 59 + 2], col[3 * 149 + 1]);
+    }
     return 0;
 }
 """
@@ -106,7 +115,7 @@ def test_header_is_plain_c_and_layouts_match_the_binding(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
-    first, sizes, offs = r.stdout.split("\n")[:3]
+    first, sizes, offs, cols = r.stdout.split("\n")[:4]
     abi, n, w0, wl = first.split()
     assert int(abi) == ctd.lib().ctd_abi_version() and int(n) == 119
     lo, hi, w = ctd.ctd_spectrum_kramers(120, 2.5, 1)
@@ -116,3 +125,6 @@ def test_header_is_plain_c_and_layouts_match_the_binding(tmp_path):
     assert [int(x) for x in sizes.split()] == want
     assert [int(x) for x in offs.split()] == [ctd.ctd_options.shared_launch.offset, ctd.ctd_source.z1_cm.offset,
                                               ctd.ctd_physics.compton_model.offset]
+    from paper_1109_3266_gb300 import inputs as I
+    py = ctd.ctd_material_columns(I.WATER, 1, 150, "wh", ((1, 2.0), (8, 1.0)))
+    assert [float(x) for x in cols.split()] == [py[59, 2], py[149, 1]]

@@ -263,10 +263,10 @@ struct Hit {
 enum { kEscaped = 0, kFictitious = 1, kReal = 2 };
 
 // One Woodcock flight (Sec. 2.1): free path against mu_max(E), the move, the
-// escape test, the voxel and the interaction type.  s_tab and s_mm are the
-// request's attenuation table and majorant in shared memory.  An escape is
-// counted by the caller, outside the loop of flights.
-// The caller keeps ph.step below kMaxSteps (the history's step limit).
+// escape test, the voxel and the interaction type.  s_tab is the request's
+// attenuation table in shared memory.  An escape is counted by the caller,
+// outside the loop of flights, and the caller keeps ph.step below kMaxSteps
+// (the history's step limit).
 template <bool kKeys>
 __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc &q, const float4 *__restrict__ s_tab,
                                       Photon &ph, LaneCounts &cnt, Hit &hit)

@@ -236,6 +236,23 @@ int ctd_material_columns(const ctd_material *mat, int n_el, const int *z, const 
 int ctd_angular_surface(int kind, const ctd_material *mat, int n_el, const int *z, const double *count,
                         int e_min_kev, int e_max_kev, int n_zeta, double *out);
 
+/* Host logic of a run, as the library applies it (host only; needs no context or
+ * GPU).
+ *
+ * ctd_allocate_histories: n histories over nbins spectrum bins of weights w >= 0
+ * (not all zero) by largest remainder (Sec. 2.2.5): out[j] = floor(n w_j / W) plus
+ * one for the bins with the largest fractional parts (ties to the lower bin);
+ * the out[j] sum to n.  One batch of a run is allocated this way.
+ *
+ * ctd_alias_table: the Walker alias table of a fluence map's n beamlet
+ * intensities f >= 0 (finite, not all zero; Sec. 2.2.4): thresholds thr[k] =
+ * floor(p_k 2^32) and aliases alias[k] of Vose's construction, as
+ * ctd_get_fluence_table returns them.
+ *
+ * Errors: CTD_EINVAL (null pointers, nbins or n < 1, unusable weights). */
+int ctd_allocate_histories(uint64_t n, int nbins, const double *w, uint64_t *out);
+int ctd_alias_table(int n, const double *f, uint32_t *thr, int32_t *alias);
+
 /* Transport n_histories in n_batches (>= 2) batches (Sec. 2.2.1) with random
  * numbers keyed by seed; afterwards mean dose and batch uncertainty are ready
  * for ctd_get_dose_and_stddev.  Blocks until the device is done. */

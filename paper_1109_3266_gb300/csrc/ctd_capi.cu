@@ -851,6 +851,25 @@ int ctd_angular_surface(int kind, const ctd_material *mat, int n_el, const int *
     return CTD_OK;
 }
 
+int ctd_allocate_histories(uint64_t n, int nbins, const double *w, uint64_t *out)
+{
+    g_error.clear();
+    if (!w || !out || nbins < 1) return fail(CTD_EINVAL, "need weights, output and nbins >= 1");
+    const std::vector<double> wv(w, w + nbins);
+    std::vector<uint64_t> o;
+    if (!ctd::allocate(n, wv, o)) return fail(CTD_EINVAL, "weights must be >= 0 and not all zero");
+    std::copy(o.begin(), o.end(), out);
+    return CTD_OK;
+}
+
+int ctd_alias_table(int n, const double *f, uint32_t *thr, int32_t *alias)
+{
+    g_error.clear();
+    if (!f || !thr || !alias || n < 1) return fail(CTD_EINVAL, "need intensities, outputs and n >= 1");
+    if (!ctd::alias_build(n, f, thr, alias)) return fail(CTD_EINVAL, "intensities must be finite, >= 0 and not all zero");
+    return CTD_OK;
+}
+
 int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches)
 {
     int rc;

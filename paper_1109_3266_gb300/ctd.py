@@ -131,6 +131,8 @@ def lib():
         L.ctd_spectrum_kramers.argtypes = [C.c_int, C.c_double, C.c_int, dp, dp, dp, C.POINTER(C.c_int)]
         L.ctd_material_columns.argtypes = [C.POINTER(ctd_material), C.c_int, C.POINTER(C.c_int), dp, C.c_int,
                                            C.c_int, C.c_int, dp]
+        L.ctd_allocate_histories.argtypes = [C.c_uint64, C.c_int, dp, C.POINTER(C.c_uint64)]
+        L.ctd_alias_table.argtypes = [C.c_int, dp, C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]
         L.ctd_angular_surface.argtypes = [C.c_int, C.POINTER(ctd_material), C.c_int, C.POINTER(C.c_int), dp,
                                           C.c_int, C.c_int, C.c_int, dp]
         L.ctd_get_fluence_table.argtypes = [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_uint32),
@@ -393,6 +395,24 @@ def ctd_angular_surface(kind, material, e_min_kev=1, e_max_kev=150, n_zeta=1024,
     _check(lib().ctd_angular_surface(k, C.byref(m), n, z, _dp(cnt), int(e_min_kev), int(e_max_kev), int(n_zeta),
                                      _dp(out)))
     return out
+
+
+def ctd_allocate_histories(n, w):
+    """Host logic: n histories over spectrum bins of weights w by largest remainder."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty(w.size, dtype=np.uint64)
+    _check(lib().ctd_allocate_histories(int(n), w.size, _dp(w), out.ctypes.data_as(C.POINTER(C.c_uint64))))
+    return out
+
+
+def ctd_alias_table(f):
+    """Host logic: the Walker alias table (thresholds uint32, aliases int32) of intensities f."""
+    f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+    thr = np.empty(f.size, dtype=np.uint32)
+    al = np.empty(f.size, dtype=np.int32)
+    _check(lib().ctd_alias_table(f.size, _dp(f), thr.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                 al.ctypes.data_as(C.POINTER(C.c_int32))))
+    return thr, al
 
 
 def ctd_set_fluence(ctx, ph, f):

@@ -1,11 +1,14 @@
-"""The library's host physics equals the oracle's, bit for bit, without a GPU.
+"""The library's host physics and host logic equal the oracle's, bit for bit,
+without a GPU.
 
 The two are written separately; they agree because both take the same closed
 forms and integrals in the same order of operations (binary64, the C
 library's functions).  Checked here through the host-only C calls
-ctd_material_columns and ctd_angular_surface: node-table columns under both
-Compton models and both Rayleigh form factors, and the C and R surfaces of
-every kind.  (The GPU tests check the same on a phantom's uploaded tables.)"""
+ctd_material_columns and ctd_angular_surface (node-table columns under both
+Compton models and both Rayleigh form factors; the C and R surfaces of every
+kind), ctd_allocate_histories (the largest-remainder spectrum allocation) and
+ctd_alias_table (the fluence map's alias table).  The GPU tests check the same
+on a phantom's uploaded tables and through the counts of runs."""
 import numpy as np
 import pytest
 
@@ -70,3 +73,35 @@ def test_host_physics_refuses_bad_arguments(ctd):
         ctd.ctd_angular_surface(3, m, 1, 150)
     with pytest.raises(ctd.CtdError):
         ctd.ctd_angular_surface("kn", m, 1, 150, n_zeta=1)
+
+
+@pytest.mark.parametrize("case", ["kramers120", "kramers80", "ties", "zeros", "one_bin"])
+def test_allocation_equals_oracle(ctd, oracle, case):
+    rng = np.random.default_rng(5)
+    w = {"kramers120": I.spectrum_kramers(120, 2.5, 1).w,
+         "kramers80": I.spectrum_kramers(80, 0.0, 10).w,
+         "ties": np.ones(7),
+         "zeros": np.where(rng.random(40) < 0.3, 0.0, rng.random(40)),
+         "one_bin": np.array([3.0])}[case]
+    for n in (0, 1, 9, 1_000_003, 10**9 + 7):
+        got = ctd.ctd_allocate_histories(n, w)
+        assert np.array_equal(got, oracle.allocate(n, w))
+        assert int(got.sum()) == n
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_allocate_histories(10, np.zeros(3))
+
+
+@pytest.mark.parametrize("case", ["bowtie", "random", "uniform", "one_hot", "zeros"])
+def test_alias_table_equals_oracle(ctd, oracle, case):
+    rng = np.random.default_rng(3)
+    f = {"bowtie": I.bowtie_fluence(128, 32, seed=1).ravel(),
+         "random": rng.exponential(size=1000),
+         "uniform": np.ones(777),
+         "one_hot": np.eye(1, 50, 17).ravel(),
+         "zeros": np.where(rng.random(300) < 0.3, 0.0, rng.random(300))}[case]
+    thr, al = ctd.ctd_alias_table(f)
+    othr, oal = oracle.alias_table(f)
+    assert np.array_equal(thr, othr) and np.array_equal(al, oal)
+    for bad in (np.zeros(4), np.array([1.0, -1.0]), np.array([1.0, np.nan])):
+        with pytest.raises(ctd.CtdError):
+            ctd.ctd_alias_table(bad)

@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 7
+#define CTD_ABI_VERSION 8
 
 /* largest number of elements of one material's formula unit (ctd_set_material_elements) */
 #define CTD_MAX_ELEMENTS 16
@@ -265,6 +265,33 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
  * clear != 0. */
 int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches,
                   uint64_t h_begin, uint64_t h_end, int clear);
+
+/* Per-history records for validation (the primary-only comparison of the
+ * interaction choice, Sec. 2.1, and of the source, Secs. 2.2.4-2.2.6, history
+ * by history).  Runs histories [h_begin, h_end) of the n_histories/n_batches
+ * problem like ctd_run_range with clear != 0 (the deposit tally and stats are
+ * replaced by this range's) and writes one record per history to the host
+ * array out[h_end - h_begin]:
+ *   code bits 0-7: how the history ended, plus one: 1 photoelectric absorption,
+ *        2 Compton cutoff (E' below e_min), 3 escaped, 4 missed the phantom,
+ *        5 terminated (CTD_MODE_MAX_REAL), 6 aborted (step or trial limit);
+ *   code bits 8-15: type of its last real interaction plus one (1 photoelectric,
+ *        2 Compton, 3 Rayleigh; 0 none);
+ *   steps: Woodcock steps taken;  idx: voxel of the last real interaction
+ *        (meaningful when it has one);  e_end_kev: energy deposited by the event
+ *        that ended the history (0 for escaped, missed, aborted).
+ * The records come from a separate instantiation of the transport kernel that
+ * also writes them; the histories, random numbers and arithmetic are those of
+ * ctd_run.  At most 2^26 histories per call (CTD_EINVAL beyond); the call
+ * allocates 16 bytes of device memory per history for the call's duration. */
+typedef struct {
+    uint32_t code;
+    uint32_t steps;
+    uint32_t idx;
+    float e_end_kev;
+} ctd_track;
+int ctd_trace_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches,
+                    uint64_t h_begin, uint64_t h_end, ctd_track *out);
 
 /* Batched form: n_req dose calculations in one call.  Request r transports
  * n_histories[r] histories of phantoms[r] (distinct phantoms, each with its

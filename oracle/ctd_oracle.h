@@ -146,6 +146,40 @@ void or_setup_destroy(or_setup *s);
 int or_transport_f64(const or_setup *s, uint64_t h0, uint64_t h1, double *edep, or_counts *c);
 int or_transport_f32(const or_setup *s, uint64_t h0, uint64_t h1, double *edep, or_counts *c);
 
+/* Per-history records with decision margins (the primary-only comparison of
+ * the interaction choice, Sec. 2.1, against a single-precision run).
+ *
+ * Every integer decision of a history -- the source's acceptance test, the
+ * miss test at the box, escape, the voxel a flight ends in, the interaction
+ * type and the Compton cutoff -- compares two numbers.  The binary64 run logs,
+ * for each decision, the gap between them divided by a bound on how far a
+ * binary32 evaluation of the same numbers can be off (a few units of 2^-24 of
+ * the quantities involved; the bounds are stated in ctd_oracle_transport.inc).
+ * `margin` is the smallest such ratio over the decisions that change the
+ * history's path; `margin_loc` also takes the voxel boundaries that change only
+ * where a deposit lands.  A history with margin >= 1 must take every decision
+ * the same way in binary32; one below 1 may legitimately differ.  The bounds
+ * hold up to the first real interaction (all of a primary-only history); after
+ * a scatter the direction's error is not bounded here.  The binary32 run
+ * leaves both margins at +inf. */
+enum { OR_END_PE = 0, OR_END_CUTOFF = 1, OR_END_ESCAPED = 2, OR_END_MISSED = 3, OR_END_TERMINATED = 4,
+       OR_END_ABORTED = 5 };
+enum { OR_MARGIN_NONE = 0, OR_MARGIN_ACCEPT = 1, OR_MARGIN_ENTRY = 2, OR_MARGIN_ESCAPE = 3,
+       OR_MARGIN_BOUNDARY = 4, OR_MARGIN_TYPE = 5, OR_MARGIN_CUTOFF = 6 };
+typedef struct {
+    int32_t end;          /* OR_END_*                                                        */
+    int32_t last_type;    /* last real interaction: 0 photoelectric, 1 Compton, 2 Rayleigh, -1 none */
+    uint32_t steps;       /* Woodcock steps taken                                            */
+    uint32_t idx;         /* voxel of the last real interaction (0xffffffff: none)            */
+    double e_end;         /* keV deposited by the event that ended the history (0 if none)   */
+    double margin;        /* see above                                                       */
+    double margin_loc;
+    int32_t margin_kind;  /* OR_MARGIN_* of `margin`                                         */
+    int32_t pad;
+} or_track;
+int or_track_f64(const or_setup *s, uint64_t h0, uint64_t h1, or_track *out);
+int or_track_f32(const or_setup *s, uint64_t h0, uint64_t h1, or_track *out);
+
 /* inspection of the set-up (node values as stored; f32 values widened) */
 int or_setup_sizes(const or_setup *s, int *n_e, int *n_zeta, int *n_mat);
 void or_setup_tables(const or_setup *s, double *mu_cum /* n_mat*n_e*3 */, double *mu_max /* n_e */);

@@ -68,6 +68,20 @@ COUNT_KEYS = ("pe", "compton", "rayleigh", "fictitious", "escaped", "missed", "c
               "aborted", "steps")
 
 
+class OrTrack(C.Structure):
+    _fields_ = [("end", C.c_int32), ("last_type", C.c_int32), ("steps", C.c_uint32), ("idx", C.c_uint32),
+                ("e_end", C.c_double), ("margin", C.c_double), ("margin_loc", C.c_double),
+                ("margin_kind", C.c_int32), ("pad", C.c_int32)]
+
+
+# numpy view of or_track records
+TRACK_DTYPE = np.dtype([("end", np.int32), ("last_type", np.int32), ("steps", np.uint32), ("idx", np.uint32),
+                        ("e_end", np.float64), ("margin", np.float64), ("margin_loc", np.float64),
+                        ("margin_kind", np.int32), ("pad", np.int32)])
+END_NAMES = ("pe", "cutoff", "escaped", "missed", "terminated", "aborted")
+MARGIN_NAMES = ("none", "accept", "entry", "escape", "boundary", "type", "cutoff")
+
+
 def _declare(L):
     P = C.c_void_p
     dp = C.POINTER(C.c_double)
@@ -94,6 +108,8 @@ def _declare(L):
     L.or_setup_destroy.argtypes = [P]
     for n in ("or_transport_f64", "or_transport_f32"):
         getattr(L, n).argtypes = [P, C.c_uint64, C.c_uint64, dp, C.POINTER(OrCounts)]
+    for n in ("or_track_f64", "or_track_f32"):
+        getattr(L, n).argtypes = [P, C.c_uint64, C.c_uint64, C.c_void_p]
     L.or_setup_sizes.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.or_setup_tables.argtypes = [P, dp, dp]
     L.or_setup_surfaces.argtypes = [P, dp, dp]
@@ -402,6 +418,28 @@ class Setup:
             counts[k] = float(sum(getattr(c, k) for c in cnts))
         return edep, counts
 
+
+    def track(self, h0: int, h1: int, threads: int = 1) -> np.ndarray:
+        """Per-history records of histories [h0, h1) (TRACK_DTYPE): how each ended,
+        its steps, the voxel and type of its last real interaction, the energy of
+        the event that ended it and, in binary64, its decision margins."""
+        assert TRACK_DTYPE.itemsize == C.sizeof(OrTrack)
+        out = np.zeros(h1 - h0, dtype=TRACK_DTYPE)
+        fn = lib().or_track_f64 if self.precision == 64 else lib().or_track_f32
+        threads = max(1, min(int(threads), max(1, (h1 - h0) // 64)))
+        edges = np.linspace(h0, h1, threads + 1).astype(np.int64)
+
+        def work(i):
+            a, b = int(edges[i]), int(edges[i + 1])
+            if a < b and fn(self.handle, a, b, out[a - h0:].ctypes.data) != 0:
+                raise ValueError("oracle transport rejected its arguments")
+
+        if threads == 1:
+            work(0)
+        else:
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(work, range(threads)))
+        return out
 
     def transport_ranges(self, ranges, threads: int = 1):
         """Transport a list of history ranges [(h0, h1), ...] on `threads` threads,

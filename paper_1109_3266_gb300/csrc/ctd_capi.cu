@@ -373,10 +373,13 @@ int finish_stats(Phantom &P, int nb, cudaStream_t s)
 
 // One transport launch over local histories [lb, le) of a batch starting at global h_base.
 int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uint64_t h_base, uint64_t lb,
-              uint64_t le, double *tally, size_t ev_index)
+              uint64_t le, double *tally, size_t ev_index, uint4 *trace, uint64_t trace_h0, uint64_t trace_n)
 {
     ctd::LaunchParams L;
     std::memset(&L, 0, sizeof(L));
+    L.trace = trace;
+    L.trace_h0 = trace_h0;
+    L.trace_n = trace_n;
     fill_shared(P, L.sh);
     q.pref = P.pref.p + which_size * (q.nbins + 1);
     q.h_base = h_base;
@@ -954,6 +957,54 @@ int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t s
     CKS(ctd::launch_sum(P->edep.p, nv, P->partials.p + 5 * kRsdParts, kRsdParts, P->result.p + 3, ctx->stream));
     if ((rc = collect(ctx, *P, launches, t0))) return rc;
     P->stats.histories = h_end - h_begin;
+    P->stats.n_batches = n_batches;
+    return CTD_OK;
+}
+
+int ctd_trace_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches,
+                    uint64_t h_begin, uint64_t h_end, ctd_track *out)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!out && h_end > h_begin) return fail(CTD_EINVAL, "null output pointer");
+    if (n_batches < 1 || static_cast<uint64_t>(n_batches) > n_histories)
+        return fail(CTD_EINVAL, "need 1 <= n_batches <= n_histories");
+    if (h_begin > h_end || h_end > n_histories) return fail(CTD_EINVAL, "history range outside [0, n_histories]");
+    const uint64_t n = h_end - h_begin;
+    if (n > kMaxTrace) return fail(CTD_EINVAL, "at most %llu histories per trace", static_cast<unsigned long long>(kMaxTrace));
+    if ((rc = busy(P))) return rc;
+    const double t0 = now_s();
+    if ((rc = prepare_run(ctx, *P, n_histories, n_batches))) return rc;
+    DevBuf<uint4> rec;
+    if ((rc = rec.ensure(n))) return rc;
+    const size_t nv = P->nvox;
+    CK(cudaMemsetAsync(rec.p, 0, (n ? n : 1) * sizeof(uint4), ctx->stream));
+    CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+    P->have_result = false;
+    ctd::RequestDesc T;
+    fill_request(*P, seed, T);
+    const uint64_t n_lo = n_histories / n_batches, rem = n_histories % n_batches;
+    uint64_t h = 0;
+    size_t launches = 0;
+    for (int b = 0; b < n_batches; ++b) {
+        const uint64_t nb = static_cast<uint64_t>(b) < rem ? n_lo + 1 : n_lo;
+        const uint64_t lo = h_begin > h ? h_begin : h, hi = h_end < h + nb ? h_end : h + nb;
+        if (lo < hi) {
+            if ((rc = transport(ctx, *P, T, static_cast<uint64_t>(b) < rem ? 0 : 1, h, lo - h, hi - h, P->edep.p,
+                                launches, rec.p, h_begin, n)))
+                return rc;
+            ++launches;
+        }
+        h += nb;
+    }
+    CK(cudaMemsetAsync(P->result.p, 0, 3 * sizeof(double), ctx->stream));
+    CKS(ctd::launch_sum(P->edep.p, nv, P->partials.p + 5 * kRsdParts, kRsdParts, P->result.p + 3, ctx->stream));
+    if (n) CK(cudaMemcpyAsync(out, rec.p, n * sizeof(ctd_track), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((rc = collect(ctx, *P, launches, t0))) return rc;
+    P->stats.histories = n;
     P->stats.n_batches = n_batches;
     return CTD_OK;
 }

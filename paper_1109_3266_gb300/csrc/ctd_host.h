@@ -123,6 +123,7 @@ struct ServeReq {
 
 constexpr int kRsdParts = 1024;   // partial sums of the statistics reductions
 constexpr int kMaxLanes = 64;     // streams for request chains
+constexpr uint64_t kMaxTrace = 1ull << 26;   // histories of one trace call (16 B of device memory each)
 
 }  // namespace host
 }  // namespace ctd
@@ -207,8 +208,10 @@ int launch_one(ctd_ctx *ctx, Phantom &P, const ctd::RequestDesc &q, cudaStream_t
 int finish_stats(Phantom &P, int nb, cudaStream_t s);
 // one transport launch over local histories [lb, le) of a batch starting at h_base,
 // bracketed by timing events 2 ev_index and 2 ev_index + 1
+// (trace: per-history records of histories trace_h0 .. trace_h0 + trace_n - 1, or nullptr)
 int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uint64_t h_base, uint64_t lb,
-              uint64_t le, double *tally, size_t ev_index);
+              uint64_t le, double *tally, size_t ev_index, uint4 *trace = nullptr, uint64_t trace_h0 = 0,
+              uint64_t trace_n = 0);
 double now_s();
 int transport_time(ctd_ctx *ctx, size_t n_launch, double &t);
 // counts and results of several phantoms read back through pinned staging

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/ctd.h"
 
 namespace ctd {
@@ -156,7 +158,17 @@ struct LaunchParams {
     int n_req;
     int chunk;                   // histories a warp claims at a time
     int flight_cap;              // Woodcock flights a lane takes before yielding to the warp
+    // per-history records of a trace launch (single request; nullptr otherwise):
+    // record i is history trace_h0 + i, for i < trace_n
+    uint4 *trace;
+    uint64_t trace_h0, trace_n;
 };
+
+// Per-history record of a trace launch (16 bytes): x = end code + 1 in bits 0-7
+// (0: the history never ended) and the last real interaction's type + 1 in bits
+// 8-15 (0: none); y = Woodcock steps; z = voxel of the last real interaction;
+// w = binary32 bits of the energy the ending event deposited (keV).
+enum { kEndPe = 0, kEndCutoff, kEndEscaped, kEndMissed, kEndTerminated, kEndAborted };
 
 // launches (ctd_transport.cu / ctd_stats.cu)
 int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream);

@@ -96,6 +96,32 @@ struct LaneCounts {
     __device__ __forceinline__ void escaped(float e) { me->e_escaped += kev_fixed(e); }
 };
 
+// Per-history records of a trace launch (kTrace instantiations only): each
+// history writes its own record, so no two lanes write the same one.
+struct Tracer {
+    uint4 *rec;
+    uint64_t h0, n;
+    // the last real interaction: its type and voxel
+    __device__ __forceinline__ void last(uint64_t h, int type, uint32_t idx) const
+    {
+        const uint64_t i = h - h0;
+        if (i < n) {
+            rec[i].x = (rec[i].x & 0xffu) | (static_cast<uint32_t>(type + 1) << 8);
+            rec[i].z = idx;
+        }
+    }
+    // how the history ended, its steps and the energy the ending event deposited
+    __device__ __forceinline__ void end(uint64_t h, int code, uint32_t steps, float e) const
+    {
+        const uint64_t i = h - h0;
+        if (i < n) {
+            rec[i].x = (rec[i].x & 0xff00u) | static_cast<uint32_t>(code + 1);
+            rec[i].y = steps;
+            rec[i].w = __float_as_uint(e);
+        }
+    }
+};
+
 // A warp's counts added to a request's totals: warp sums, one atomic per
 // counter (energies as 128-bit fixed-point totals).  Leaves the counts cleared.
 __device__ __forceinline__ void flush_warp(DeviceCounts *dst, LaneCounts &c, int lane)
@@ -151,9 +177,9 @@ __device__ __forceinline__ int bin_search(const RequestDesc &q, uint64_t local)
 // Source photon of local history `local` (global index h) of request q;
 // `bin` is a lower bound of its 1 keV interval.  Returns true if the photon
 // enters the phantom.
-template <bool kKeys, bool kFluence>
+template <bool kKeys, bool kFluence, bool kTrace>
 __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_t local, int bin, Photon &ph,
-                                       LaneCounts &cnt)
+                                       LaneCounts &cnt, const Tracer &tr)
 {
     while (bin < q.nbins - 1 && __ldg(&q.pref[bin + 1]) <= local) ++bin;
     const U4 b0 = draw<kKeys>(q, h, 0, kStreamSource);
@@ -205,6 +231,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     if (!accepted) {
         cnt.event(kCntAborted);
         cnt.escaped(e);
+        if (kTrace) tr.end(h, kEndAborted, 0, 0.0f);
         return false;
     }
     const float inv = 1.0f / sqrtf(qq);
@@ -236,6 +263,7 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     if (!(tn < tf) || !(tf > 0.0f)) {
         cnt.event(kCntMissed);
         cnt.escaped(e);
+        if (kTrace) tr.end(h, kEndMissed, 0, 0.0f);
         return false;
     }
     if (tn < 0.0f) tn = 0.0f;
@@ -325,13 +353,16 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
 
 // A real interaction: local deposition, C/R-surface polar angle, rotation.
 // Returns false when the history has ended.
+template <bool kTrace>
 __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDesc &q, const float *__restrict__ s_mm,
-                                         Photon &ph, const Hit &hit, LaneCounts &cnt)
+                                         Photon &ph, const Hit &hit, LaneCounts &cnt, const Tracer &tr)
 {
+    if (kTrace) tr.last(ph.h, hit.type, hit.idx);
     if (hit.type == 0) {
         // photoelectric absorption: the electron deposits E here
         cnt.event(kCntPe);
         deposit(q.tally, hit.idx, ph.e);
+        if (kTrace) tr.end(ph.h, kEndPe, ph.step, ph.e);
         return false;
     }
     const float *S = hit.type == 1
@@ -346,13 +377,16 @@ __device__ __forceinline__ bool interact(const SharedTables &sh, const RequestDe
         if (ep < static_cast<float>(sh.e_min)) {
             cnt.event(kCntCutoff);
             deposit(q.tally, hit.idx, ph.e);
+            if (kTrace) tr.end(ph.h, kEndCutoff, ph.step, ph.e);
             return false;
         }
         deposit(q.tally, hit.idx, ph.e - ep);
+        if (kTrace) tr.end(ph.h, kEndTerminated, ph.step, ph.e - ep);   // kept if the history ends here
         ph.e = ep;
         set_energy(ph, sh, s_mm);
     } else {
         cnt.event(kCntRayleigh);
+        if (kTrace) tr.end(ph.h, kEndTerminated, ph.step, 0.0f);
     }
     if (q.mode == CTD_MODE_MAX_REAL && ++cnt.me->nreal >= static_cast<uint32_t>(q.max_real)) {
         cnt.event(kCntTerminated);
@@ -387,10 +421,14 @@ constexpr size_t kWarpBytes = kQueueBytes + sizeof(WarpPool) + 32 * sizeof(LaneS
 
 // All histories [q.local_begin, q.local_end) of one request, claimed by warps
 // from q.work in runs of `chunk`.  Returns when the warp has no photon left.
-template <bool kKeys, bool kFluence>
+template <bool kKeys, bool kFluence, bool kTrace>
 __device__ __forceinline__ void run_request(const LaunchParams &P, const RequestDesc &q, const float4 *s_tab,
                                             const float *s_mm, const Queue &Q, int lane, LaneCounts &cnt)
 {
+    Tracer tr;
+    tr.rec = P.trace;
+    tr.h0 = P.trace_h0;
+    tr.n = kTrace ? P.trace_n : 0;
     const unsigned lt_mask = (1u << lane) - 1u;
     Photon ph;
     bool alive = false;
@@ -427,7 +465,7 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
                 bool ok = false;
                 if (lane < take) {
                     const uint64_t local = pool_next + lane;
-                    ok = source<kKeys, kFluence>(q, q.h_base + local, local, pool_bin, np, cnt);
+                    ok = source<kKeys, kFluence, kTrace>(q, q.h_base + local, local, pool_bin, np, cnt, tr);
                 }
                 const unsigned okm = __ballot_sync(kFull, ok);
                 if (ok) {
@@ -488,6 +526,7 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
             if (lim == 0) {
                 cnt.event(kCntAborted);
                 cnt.escaped(ph.e);
+                if (kTrace) tr.end(ph.h, kEndAborted, ph.step, 0.0f);
                 alive = false;
             } else {
                 Hit hit;
@@ -498,9 +537,10 @@ __device__ __forceinline__ void run_request(const LaunchParams &P, const Request
                 if (f == kEscaped) {
                     cnt.event(kCntEscaped);
                     cnt.escaped(ph.e);
+                    if (kTrace) tr.end(ph.h, kEndEscaped, ph.step, 0.0f);
                     alive = false;
                 } else if (f == kReal) {
-                    alive = interact(P.sh, q, s_mm, ph, hit, cnt);
+                    alive = interact<kTrace>(P.sh, q, s_mm, ph, hit, cnt, tr);
                 }
             }
         }
@@ -521,8 +561,9 @@ __device__ __forceinline__ void load_tables(const RequestDesc &q, int n_e, float
 // one, so that one request's tail overlaps the next one's start.
 // kForm: 0 one request without a fluence map, 1 one request with a fluence map
 // (the map's source path is compiled only into this form, so that it does not
-// cost the open-field form registers), 2 several requests (maps checked per request)
-template <int kMaxThreads, int kMinBlocks, int kForm>
+// cost the open-field form registers), 2 several requests (maps checked per request).
+// kTrace (single-request forms): also write each history's record to P.trace.
+template <int kMaxThreads, int kMinBlocks, int kForm, bool kTrace = false>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(const LaunchParams P)
 {
     extern __shared__ float4 smem[];
@@ -545,7 +586,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
     if (!kMulti) {
         load_tables(P.one, n_e, s_tab, s_mm);
         __syncthreads();
-        run_request<true, kForm == 1>(P, P.one, s_tab, s_mm, Q, lane, cnt);
+        run_request<true, kForm == 1, kTrace>(P, P.one, s_tab, s_mm, Q, lane, cnt);
         flush_warp(P.one.counts, cnt, lane);
         return;
     }
@@ -578,7 +619,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
         __syncthreads();
         load_tables(q, n_e, s_tab, s_mm);
         __syncthreads();
-        run_request<false, true>(P, q, s_tab, s_mm, Q, lane, cnt);
+        run_request<false, true, false>(P, q, s_tab, s_mm, Q, lane, cnt);
         flush_warp(q.counts, cnt, lane);
         __syncthreads();
         // the same request is exhausted now; continue the walk from it
@@ -616,10 +657,10 @@ __global__ void eval_math_kernel(int fn, const float *x, float *out, size_t n)
     }
 }
 
-template <int kMaxThreads, int kMinBlocks, int kForm>
+template <int kMaxThreads, int kMinBlocks, int kForm, bool kTrace = false>
 int launch_t(const LaunchParams &p, int grid, int block, size_t smem, cudaStream_t stream)
 {
-    auto *k = transport_kernel<kMaxThreads, kMinBlocks, kForm>;
+    auto *k = transport_kernel<kMaxThreads, kMinBlocks, kForm, kTrace>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
             return CTD_ECUDA;
@@ -659,6 +700,15 @@ int launch_transport(const LaunchParams &p, int grid, int block, int threads_per
         return CTD_EINVAL;
     }
     const size_t smem = transport_smem_bytes(p, block);
+    if (p.trace) {
+        // trace launches (validation): one instantiation per source form, at 64 registers
+        if (p.n_req > 0) {
+            set_error("trace launches take one request");
+            return CTD_EINVAL;
+        }
+        return p.one.fl_n > 0 ? launch_t<256, 4, 1, true>(p, grid, block, smem, s)
+                              : launch_t<256, 4, 0, true>(p, grid, block, smem, s);
+    }
     if (p.n_req > 0) return launch_m<2>(p, grid, block, threads_per_sm, smem, s);
     return p.one.fl_n > 0 ? launch_m<1>(p, grid, block, threads_per_sm, smem, s)
                           : launch_m<0>(p, grid, block, threads_per_sm, smem, s);

@@ -111,6 +111,7 @@ def lib():
         L.ctd_set_spectrum.argtypes = [P, C.c_int32, dp, dp, dp, C.c_int]
         L.ctd_run.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int]
         L.ctd_run_range.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]
+        L.ctd_trace_range.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, P]
         L.ctd_get_dose_and_stddev.argtypes = [P, C.c_int32, dp, dp, C.c_size_t, C.POINTER(ctd_run_stats)]
         L.ctd_get_edep.argtypes = [P, C.c_int32, dp, C.c_size_t]
         L.ctd_get_tables.argtypes = [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -276,6 +277,29 @@ def ctd_autotune(ctx, ph, n_probe, seed=1):
 def ctd_run_range(ctx, ph, n_histories, seed, n_batches, h_begin, h_end, clear=True):
     _check(lib().ctd_run_range(ctx, ph, int(n_histories), int(seed), int(n_batches), int(h_begin), int(h_end),
                                int(bool(clear))))
+
+
+# ctd_track records as numpy sees them
+TRACK_DTYPE = np.dtype([("code", np.uint32), ("steps", np.uint32), ("idx", np.uint32), ("e_end_kev", np.float32)])
+END_NAMES = ("pe", "cutoff", "escaped", "missed", "terminated", "aborted")
+
+
+def ctd_trace_range(ctx, ph, n_histories, seed, n_batches, h_begin, h_end):
+    """Per-history records of histories [h_begin, h_end): a structured array with
+    end (0 photoelectric, 1 cutoff, 2 escaped, 3 missed, 4 terminated, 5 aborted,
+    -1 never ended), last_type (0 PE, 1 Compton, 2 Rayleigh, -1 none), steps, idx
+    and e_end (keV)."""
+    raw = np.zeros(int(h_end) - int(h_begin), dtype=TRACK_DTYPE)
+    _check(lib().ctd_trace_range(ctx, ph, int(n_histories), int(seed), int(n_batches), int(h_begin), int(h_end),
+                                 raw.ctypes.data if raw.size else None))
+    out = np.zeros(raw.size, dtype=[("end", np.int32), ("last_type", np.int32), ("steps", np.uint32),
+                                    ("idx", np.uint32), ("e_end", np.float64)])
+    out["end"] = (raw["code"] & 0xff).astype(np.int32) - 1
+    out["last_type"] = ((raw["code"] >> 8) & 0xff).astype(np.int32) - 1
+    out["steps"] = raw["steps"]
+    out["idx"] = raw["idx"]
+    out["e_end"] = raw["e_end_kev"]
+    return out
 
 
 def ctd_get_dose_and_stddev(ctx, ph, nvox, want_arrays=True):

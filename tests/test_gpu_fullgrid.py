@@ -1,0 +1,80 @@
+"""Dose parity with the binary64 oracle on the full grids of the CBCT-water
+(256x256x128 x 0.2 cm, 120 kVp, 360 projections) and head (256x256x160 x
+0.1 cm, half fan, 100 kVp) workloads, at 1e8 histories in 20 batches, so that
+each side's per-voxel batch standard error has 19 degrees of freedom
+(Secs. 2.1 and 2.2.1).
+
+Bar: >= 99 % of the voxels above 10 % of the maximum dose within 3 combined
+standard errors, and the total deposited energy within 0.5 %.  Same seed on
+both sides (the same histories, so the agreement is far inside the bar), plus
+one run at independent seeds, where the 3-sigma test is a statistical one."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1109_3266_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+N_HIST = 100_000_000
+N_BATCHES = 20
+
+
+@pytest.fixture(scope="module")
+def ctd():
+    from paper_1109_3266_gb300 import build, ctd as binding
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(ctd):
+    c = ctd.ctd_create(device=0)
+    yield c
+    ctd.ctd_destroy(c)
+
+
+def within_3sigma(dose, sd, ref, ref_sd):
+    m = ref > 0.1 * ref.max()
+    z = np.abs(dose[m] - ref[m]) / np.sqrt(sd[m] ** 2 + ref_sd[m] ** 2 + 1e-300)
+    return float(np.mean(z < 3.0)), int(m.sum()), float(np.median(z))
+
+
+def physics(p, **kw):
+    return I.scaled(p, physics=dataclasses.replace(p.physics, **kw))
+
+
+CASES = {
+    "cbct_water": lambda: I.cbct_water(n_hist=N_HIST, n_batches=N_BATCHES),
+    "head": lambda: I.head(n_hist=N_HIST, n_batches=N_BATCHES),
+    "head_wh_iaa": lambda: physics(I.head(n_hist=N_HIST, n_batches=N_BATCHES), compton="wh", rayleigh="iaa"),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_full_grid_dose_matches_binary64_oracle(ctd, ctx, oracle, name):
+    p = CASES[name]()
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    ctd.ctd_destroy_phantom(ctx, h)
+    r = oracle.run(p, precision=64)
+    frac, nmask, zmed = within_3sigma(dose, sd, r.dose, r.std)
+    assert nmask > 10_000 and frac >= 0.99, (frac, nmask, zmed)
+    e64 = r.counts["e_deposited"]
+    assert abs(st["e_deposited_kev"] - e64) <= 0.005 * e64, (st["e_deposited_kev"], e64)
+    # energy bookkeeping on the device
+    assert abs(st["e_deposited_kev"] + st["e_escaped_kev"] - st["e_emitted_kev"]) <= 1e-9 * st["e_emitted_kev"]
+
+
+def test_full_grid_independent_seeds(ctd, ctx, oracle):
+    p = CASES["cbct_water"]()
+    dose, sd, st, h = ctd.run_problem(ctx, p)
+    ctd.ctd_destroy_phantom(ctx, h)
+    r = oracle.run(I.scaled(p, seed=991), precision=64)
+    frac, nmask, zmed = within_3sigma(dose, sd, r.dose, r.std)
+    assert nmask > 10_000 and frac >= 0.99, (frac, nmask, zmed)
+    # median |z| of two independent estimates is about 0.67 (half-normal); same-path runs sit near 0
+    assert 0.5 < zmed < 0.85, zmed
+    eg = st["e_deposited_kev"] / st["e_emitted_kev"]
+    e64 = r.counts["e_deposited"] / r.counts["e_emitted"]
+    assert abs(eg - e64) <= 0.005 * e64

@@ -325,10 +325,10 @@ int or_allocate(uint64_t n, int nbins, const double *w, uint64_t *out)
     if (nbins <= 0) return -1;
     double total = 0.0;
     for (int j = 0; j < nbins; ++j) {
-        if (!(w[j] >= 0.0)) return -1;
+        if (!(w[j] >= 0.0) || !isfinite(w[j])) return -1;
         total += w[j];
     }
-    if (!(total > 0.0)) return -1;
+    if (!(total > 0.0) || !isfinite(total)) return -1;
     double *frac = (double *)malloc(sizeof(double) * (size_t)nbins);
     if (!frac) return -1;
     uint64_t given = 0;

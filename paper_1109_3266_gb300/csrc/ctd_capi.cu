@@ -860,7 +860,7 @@ int ctd_allocate_histories(uint64_t n, int nbins, const double *w, uint64_t *out
     if (!w || !out || nbins < 1) return fail(CTD_EINVAL, "need weights, output and nbins >= 1");
     const std::vector<double> wv(w, w + nbins);
     std::vector<uint64_t> o;
-    if (!ctd::allocate(n, wv, o)) return fail(CTD_EINVAL, "weights must be >= 0 and not all zero");
+    if (!ctd::allocate(n, wv, o)) return fail(CTD_EINVAL, "weights must be finite, >= 0, not all zero, with a finite sum");
     std::copy(o.begin(), o.end(), out);
     return CTD_OK;
 }

@@ -292,47 +292,49 @@ bool alias_build(int n, const double *f, uint32_t *thr, int32_t *alias)
 
 bool allocate(uint64_t n, const std::vector<double> &w, std::vector<uint64_t> &out)
 {
-    const int nb = static_cast<int>(w.size());
-    if (nb <= 0) return false;
+    // Largest remainder (Sec. 2.2.5): quota n w_j / W, its floor to every bin, then one
+    // more to the bins of largest fractional part (ties to the lower bin, none to
+    // empty bins) until the counts add up to n.  Weights must be finite, >= 0, and
+    // sum to a finite positive W.
+    const size_t nb = w.size();
+    if (nb == 0) return false;
     double total = 0.0;
     for (double x : w) {
-        if (!(x >= 0.0)) return false;
+        if (!(x >= 0.0) || !std::isfinite(x)) return false;
         total += x;
     }
-    if (!(total > 0.0)) return false;
+    if (!(total > 0.0) || !std::isfinite(total)) return false;
     out.assign(nb, 0);
     std::vector<double> frac(nb);
     uint64_t given = 0;
-    for (int j = 0; j < nb; ++j) {
+    for (size_t j = 0; j < nb; ++j) {
         const double q = static_cast<double>(n) * w[j] / total;
         const double f = std::floor(q);
         out[j] = static_cast<uint64_t>(f);
         frac[j] = q - f;
         given += out[j];
     }
-    // remainder: largest fractional part first, ties to the lower bin, none to empty bins
-    while (given < n) {
-        int pick = -1;
-        for (int j = 0; j < nb; ++j) {
-            if (w[j] <= 0.0) continue;
-            if (pick < 0 || frac[j] > frac[pick]) pick = j;
+    if (given < n) {
+        // bins of positive weight by decreasing fraction, lower bin first among equals
+        std::vector<size_t> order;
+        for (size_t j = 0; j < nb; ++j)
+            if (w[j] > 0.0) order.push_back(j);
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return frac[a] > frac[b]; });
+        for (size_t i = 0; i < order.size() && given < n; ++i, ++given) ++out[order[i]];
+        // rounding of the quotas could in principle leave more than one per bin: the
+        // rest goes to the lowest bin of positive weight
+        if (given < n) {
+            out[order.front()] += n - given;
+            given = n;
         }
-        if (pick < 0) break;
-        out[pick] += 1;
-        frac[pick] = -1.0;
-        ++given;
-    }
-    // rounding of q can push the floors past n: take back from the smallest fractions
-    while (given > n) {
-        int pick = -1;
-        for (int j = nb - 1; j >= 0; --j) {
-            if (out[j] == 0) continue;
-            if (pick < 0 || frac[j] < frac[pick]) pick = j;
-        }
-        if (pick < 0) break;
-        out[pick] -= 1;
-        frac[pick] = 2.0;
-        --given;
+    } else if (given > n) {
+        // rounding pushed the floors past n: one back from each bin of smallest
+        // fraction among those holding any, the higher bin first among equals
+        std::vector<size_t> order;
+        for (size_t j = nb; j-- > 0;)
+            if (out[j] > 0) order.push_back(j);
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return frac[a] < frac[b]; });
+        for (size_t i = 0; i < order.size() && given > n; ++i, --given) --out[order[i]];
     }
     return given == n;
 }

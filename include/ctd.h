@@ -453,9 +453,12 @@ int ctd_probe_memory(ctd_ctx *ctx, int kind, uint64_t n_slots, uint64_t n_ops, d
  * device.  It allocates nothing: its partial sums live in a fixed 160 KB
  * device array inside the library, which every GPU that loads the library
  * holds until exit, so nvox may not exceed 67,108,864 (CTD_EINVAL beyond).
- * The first call on each device looks up that array's device address; make
- * it before any stream capture.  All calls share the array: a call overwrites
- * every partial it reads, but calls that overlap on the GPU race on it. */
+ * Each call made outside stream capture looks up that array's device address
+ * on the current device (so a device reset between calls is harmless); a call
+ * made during capture uses the address its device's last call found, so make
+ * the first call on each device before any stream capture.  All calls share
+ * the array: a call overwrites every partial it reads, but calls that overlap
+ * on the GPU race on it. */
 int ctd_avg_rsd_noalloc(const double *dose_dev, const double *stddev_dev, const float *density_dev, size_t nvox,
                         double *result_dev, void *stream);
 

@@ -2,10 +2,11 @@
 paper_1109_3266_gb300/_build/libctd.so.
 
 Every translation unit is compiled in parallel with
-    nvcc -gencode arch=compute_103a,code=sm_103a -lineinfo -O3 --fmad=false
-and host code with -ffp-contract=off, so that the binary32 transport rounds
-each multiply and add separately and the host-built tables do not depend on
-the host compiler's FMA contraction.
+    nvcc -gencode arch=compute_103a,code=sm_103a -lineinfo -O3
+the transport kernels with --use_fast_math (hardware reciprocal, square root,
+logarithm and sincos, contracted multiply-adds; binary64 is unaffected), the
+other kernels with --fmad=false, and host code with -ffp-contract=off, so that
+the host-built tables do not depend on the host compiler's FMA contraction.
 """
 import os
 import shutil
@@ -20,6 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["ctd_capi.cu", "ctd_forms.cu", "ctd_tune.cu", "ctd_transport.cu", "ctd_stats.cu", "ctd_physics.cpp",
            "ctd_noalloc.cu", "ctd_probe.cu"]
 HEADERS = ["ctd_internal.h", "ctd_host.h", "ctd_device.cuh"]
+FAST_MATH = {"ctd_transport.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_FLAGS = "-fPIC,-ffp-contract=off,-fno-fast-math,-O2"
 
@@ -41,7 +43,8 @@ def _stale() -> bool:
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "--fmad=false", "-std=c++17", "-I", INCLUDE,
+    fp = ["--use_fast_math"] if src in FAST_MATH else ["--fmad=false"]
+    cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", *fp, "-std=c++17", "-I", INCLUDE,
            "-Xcompiler", HOST_FLAGS, "-c", os.path.join(SRC, src), "-o", obj, *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -139,11 +139,20 @@ int ctd_avg_rsd_noalloc(const double *dose_dev, const double *stddev_dev, const 
         cudaGetLastError();
         return na_fail(CTD_ECUDA, "no usable current CUDA device");
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The scratch array's device address, looked up with the device current.  Outside
+    // stream capture it is looked up on every call (a device reset reloads the module
+    // and moves the array); during capture the address of this device's last lookup
+    // is used.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;   // unknown: take the cached address
+    }
     double *scratch;
     {
-        // once per device, with that device current: the scratch array's device address
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_rsd_scratch);
             if (e != cudaSuccess || !p) {
@@ -155,7 +164,6 @@ int ctd_avg_rsd_noalloc(const double *dose_dev, const double *stddev_dev, const 
         scratch = g_scratch_ptr[dev];
     }
     const int nblocks = static_cast<int>((nvox + kVoxPerBlock - 1) / kVoxPerBlock);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     na_dmax_kernel<<<nblocks, kThreads, 0, s>>>(dose_dev, density_dev, nvox, scratch);
     na_dmax_final_kernel<<<1, 32, 0, s>>>(nblocks, scratch);
     na_rsd_kernel<<<nblocks, kThreads, 0, s>>>(dose_dev, stddev_dev, density_dev, nvox, scratch);

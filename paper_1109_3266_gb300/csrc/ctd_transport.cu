@@ -189,7 +189,9 @@ __device__ __forceinline__ bool source(const RequestDesc &q, uint64_t h, uint64_
     float cb = 1.0f, sb = 0.0f, zs = 0.0f;
     if (q.src_kind == CTD_SRC_ARC) {
         if (q.continuous) {
-            sincos_turns(__fmaf_rn(q.awt, uni(b0.y), q.a0t), cb, sb);
+            // the angle in turns, reduced to [0, 1) (arcs may span several turns)
+            const float turns = __fmaf_rn(q.awt, uni(b0.y), q.a0t);
+            sincos_turns(turns - floorf(turns), cb, sb);
             zs = __fmaf_rn(q.hdz, uni(b0.y), q.hz0);
         } else {
             const uint32_t k =

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from paper_1109_3266_gb300 import inputs as I
+from gpu_checks import histories_match_binary64
 
 pytestmark = pytest.mark.gpu
 
@@ -206,13 +207,7 @@ def test_batched_full_size_requests(ctd, oracle):
             assert np.allclose(ctd.ctd_get_dose_and_stddev(c, hs[r], p.phantom.nvox)[0], doses[r], rtol=1e-9, atol=0)
     for r in (1, 62):
         p = reqs[r]
-        s32 = oracle.Setup(p, 32)
-        for a, b in ((0, 3000), (p.n_hist - 3000, p.n_hist)):
-            ctd.ctd_run_range(c, hs[r], p.n_hist, p.seed, 10, a, b, clear=True)
-            st = ctd.ctd_get_dose_and_stddev(c, hs[r], 0, want_arrays=False)[2]
-            _, oc = s32.transport(a, b, threads=8)
-            diff = {k: (st[k], oc[k]) for k in CK if st[k] != oc[k]}
-            assert not diff, (r, a, diff)
+        histories_match_binary64(ctd, c, hs[r], p, oracle, ranges=[(0, 3000), (p.n_hist - 3000, p.n_hist)])
     ctd.ctd_destroy(c)
 
 

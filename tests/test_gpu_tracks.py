@@ -113,7 +113,7 @@ def test_full_size_ranges_history_by_history(ctd, ctx, oracle, name, mode):
     refs = oracle_tracks(oracle, p, ranges)
     for dev, ref in zip(devs, refs):
         if mode == "primary":
-            assert_consistent(dev, ref, max_flagged_frac=0.35)
+            assert_consistent(dev, ref)
         else:
             s = compare(dev, ref)
             assert s["never_ended"] == 0 and s["mismatches"] <= 5e-3 * s["histories"], s

@@ -36,7 +36,7 @@ def compare(run32, ref64):
     }
 
 
-def assert_consistent(run32, ref64, max_flagged_frac=0.25):
+def assert_consistent(run32, ref64, max_flagged_frac=0.05):
     s = compare(run32, ref64)
     assert s["never_ended"] == 0, s
     assert s["unflagged_mismatches"] == 0, s

@@ -1,5 +1,6 @@
 #!/usr/bin/env python3
-"""Benchmark of the dose engine: photon histories per second on one GB300.
+"""Benchmark of the dose engine on one GB300: photon histories per second,
+seconds to 1 % avg RSD, and the served form's p50/p99 latency.
 
 A step is one complete dose calculation of the workload through the C ABI:
 source sampling, Woodcock transport, interactions and tallies for every
@@ -8,17 +9,29 @@ history in N_b batches, the batch folds and the avg-RSD reduction.  Its inputs
 writing a 256 MB buffer, outside the timed events.
 
 Default workload: the CBCT water phantom, 256x256x128 voxels of 0.2 cm,
-120 kVp, 360 projections, 1e9 histories in 10 batches.
+120 kVp, 360 projections, 1e9 histories in 10 batches.  The same JSON line
+also carries, each measured in this run:
+  head      the head phantom (256x256x160 x 0.1 cm, 100 kVp half fan, 2e9
+            histories): histories/s, seconds to 1 % avg RSD, roofline;
+  batched   64 uneven requests (64^3-256^3 water and head, 80-140 kVp, 1e7-1e9
+            histories): request chains in one CUDA graph and one shared launch
+            per batch, against the same requests run one after another;
+  served    a Poisson stream of head requests, each stopped at 1 % avg RSD:
+            p50/p99 latency and histories/s, continuous batching against one
+            request at a time;
+  error_vs_fp64_oracle  the device against the binary64 oracle on the CPU
+            baseline's sample (the same histories on both sides).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--legs ...]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
-Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
-replica (own seed); value = all histories / max-over-ranks time.
+Prints one JSON line (rank 0).  Under torchrun the ranks share one problem of
+N x 1e9 histories, each rank transporting its share of every batch, with one
+binary64 sum of each batch's tally across ranks (NCCL) before the fold;
+value = all histories / max-over-ranks time.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -31,19 +44,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "photon histories/sec (sec-to-1% avg RSD beside it)"
+METRIC = "photon histories/sec and sec-to-1% avg RSD on 1 GB300; served p50/p99 latency"
 UNIT = "histories/s"
 SM_COUNT = 152
 LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes issue per SM clock
+FLUSH_BYTES = 256 * 1024 * 1024
 
-
-# Transport-kernel figures from one ncu capture of one launch of the same workload
-# (profiles/transport_kernel_*_full.md): lane instructions per history
-# (smsp__inst_executed x thread-per-instruction ratio / histories) and DRAM
-# bytes per launch (dram__bytes_read + dram__bytes_write).
+# Transport-kernel figures from one ncu capture (--set full, --clock-control none)
+# of one launch of the same workload: lane instructions per history
+# (smsp__thread_inst_executed / histories) and DRAM bytes per launch
+# (dram__bytes_read + dram__bytes_write); they are not measured in this run.
 KERNEL_PROFILE = {
-    "cbct_water": {"lane_inst_per_history": 2603.0, "dram_bytes_per_launch": 9.16e9, "histories_per_launch": 1e8},
-    "head": {"lane_inst_per_history": 3128.0, "dram_bytes_per_launch": 13.42e9, "histories_per_launch": 2e8},
+    "cbct_water": {"lane_inst_per_history": None, "dram_bytes_per_launch": None, "histories_per_launch": 1e8,
+                   "capture": None},
+    "head": {"lane_inst_per_history": None, "dram_bytes_per_launch": None, "histories_per_launch": 2e8,
+             "capture": None},
 }
 
 
@@ -55,7 +70,7 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload(name, compton="kn", rayleigh="gauss"):
+def workload(name, compton="kn", rayleigh="gauss", n_hist=None):
     """The named workload; compton "wh" switches it to the Waller-Hartree model,
     rayleigh "iaa" to the independent-atom form factor of its materials' elements."""
     import dataclasses
@@ -68,26 +83,21 @@ def workload(name, compton="kn", rayleigh="gauss"):
     p = makers[name]()
     if compton != "kn" or rayleigh != "gauss":
         p = I.scaled(p, physics=dataclasses.replace(p.physics, compton=compton, rayleigh=rayleigh))
+    if n_hist is not None:
+        p = I.scaled(p, n_hist=n_hist)
     return p
 
 
 class Clocks:
-    """nvidia-smi clock and throttle sampling during the timed region."""
+    """nvidia-smi clock and throttle sampling; summaries over marked windows."""
 
     def __init__(self, index=0):
         self.index = index
         self.proc = None
         self.lines = []
-        self.window = None
 
-    def start_window(self):
-        """Samples from here on count (the sampler itself may start earlier, so that
-        its own start-up does not fall into the timed region)."""
-        self.window = [len(self.lines), None]
-
-    def stop_window(self):
-        if self.window is not None:
-            self.window[1] = len(self.lines)
+    def mark(self):
+        return len(self.lines)
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -114,16 +124,14 @@ class Clocks:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            self.proc = None
 
-    def summary(self):
+    def summary(self, a=0, b=None):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        lines = self.lines
-        if self.window is not None:
-            a, b = self.window
-            lines = self.lines[a:b] if b is not None else self.lines[a:]
-            if not lines:   # a window shorter than one sample: the nearest sample
-                lines = self.lines[max(0, a - 1):a + 1]
+        lines = self.lines[a:b] if b is not None else self.lines[a:]
+        if not lines:   # a window shorter than one sample: the nearest sample
+            lines = self.lines[max(0, a - 1):a + 1]
         for l in lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
@@ -177,11 +185,19 @@ def sum_over_ranks(x, world, device=None):
     return float(t.item())
 
 
-# --------------------------------------------------------------------------- CPU oracle leg
-def oracle_rate(p, seconds, threads, n_ranges=64):
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample(p, seconds, threads, n_ranges=64, keep=False):
     """Histories/s of the binary64 oracle as it stands on a bounded sample of the
     workload: n_ranges equal history ranges spread evenly through the first batch,
-    so that the sample covers the whole spectrum (histories run in 1 keV bin order)."""
+    so that the sample covers the whole spectrum (histories run in 1 keV bin order).
+    Returns (rate, histories, seconds, ranges, deposits, counts) of the last sample."""
     from oracle import oracle as O
     s = O.Setup(p, 64)
     batch = p.n_hist // p.n_batches
@@ -190,30 +206,23 @@ def oracle_rate(p, seconds, threads, n_ranges=64):
         per = max(1, n // n_ranges)
         ranges = [((batch * k) // n_ranges, min((batch * k) // n_ranges + per, p.n_hist)) for k in range(n_ranges)]
         t0 = time.perf_counter()
-        s.transport_ranges(ranges, threads)
-        return per * n_ranges, time.perf_counter() - t0
+        edep, c = s.transport_ranges(ranges, threads)
+        return per * n_ranges, time.perf_counter() - t0, ranges, edep, c
 
     n = 64 * n_ranges
     while True:
-        done, dt = sample(n)
+        done, dt, ranges, edep, c = sample(n)
         if dt > 0.5 or n >= batch:
             break
         n *= 4
     # size the sample from the probe's rate, then once more from the sample's own
     # rate if the first estimate (small samples pay thread start-up) fell short
     n = int(max(n_ranges, min(batch, done / max(dt, 1e-6) * seconds)))
-    done, dt = sample(n)
+    done, dt, ranges, edep, c = sample(n)
     if dt < 0.6 * seconds and n < batch:
         n = int(max(n_ranges, min(batch, done / max(dt, 1e-6) * seconds)))
-        done, dt = sample(n)
-    return done / dt, done, dt, None
-
-
-def cpu_cores():
-    try:
-        return len(os.sched_getaffinity(0))
-    except AttributeError:
-        return os.cpu_count() or 1
+        done, dt, ranges, edep, c = sample(n)
+    return done / dt, done, dt, ranges, (edep if keep else None), c
 
 
 def run_reference(args):
@@ -222,11 +231,13 @@ def run_reference(args):
         return
     p = workload(args.workload, args.compton, args.rayleigh)
     threads = cpu_cores()
+    # each step a bounded sample, so that the whole run ends within a few minutes
+    per_step = max(2.0, min(args.ref_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_rate(p, 0.5, threads)
+        oracle_sample(p, 0.5, threads)
     rates, ns = [], []
     for _ in range(args.steps):
-        r, n, dt, _ = oracle_rate(p, args.ref_seconds, threads)
+        r, n, dt, _, _, _ = oracle_sample(p, per_step, threads)
         rates.append(r)
         ns.append(n)
     value = float(np.mean(rates))
@@ -243,83 +254,134 @@ def run_reference(args):
     }), flush=True)
 
 
-# --------------------------------------------------------------------------- GPU leg
-def run_ours(args):
+# --------------------------------------------------------------------------- measurement pieces
+def timed_runs(ctd, ctx, h, p, seed, steps, warmup, ramp_s, stream, flush, sync, clk=None):
+    """An untimed clock ramp (runs for ramp_s seconds, so that an idle GPU has reached
+    its clocks), exactly `warmup` warm-up runs, then `steps` runs timed with CUDA
+    events on the launching stream, L2 flushed between them outside the events."""
     import torch
-
-    from paper_1109_3266_gb300 import ctd
-
-    rank, world = dist_init(args.gpus)
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    p = workload(args.workload, args.compton, args.rayleigh)
-    seed = p.seed + 7919 * rank
-    nvox = p.phantom.nvox
-    ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
-                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap)
-    h = ctd.load_problem(ctx, p)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     def step():
         ctd.ctd_run(ctx, h, p.n_hist, seed, p.n_batches)
 
-    # the clock sampler starts before the warm-up, so that its start-up is not timed;
-    # the warm-up runs at least its W steps and at least 2 s, so that an idle GPU has
-    # ramped its clocks up before the timed region
-    clk = Clocks(local).__enter__()
-    t_warm = time.perf_counter()
-    warmup_done = 0
-    while warmup_done < args.warmup or (time.perf_counter() - t_warm < 2.0 and warmup_done < 100):
+    t0, ramp = time.perf_counter(), 0
+    while time.perf_counter() - t0 < ramp_s and ramp < 200:
+        step()
+        ramp += 1
+    ramp_t = time.perf_counter() - t0
+    for _ in range(warmup):
         step()
         flush.zero_()
-        torch.cuda.synchronize()
-        warmup_done += 1
-    torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     t_transport, launches, stats = 0.0, 0, None
-    clk.start_window()
-    for i in range(args.steps):
+    a = clk.mark() if clk else 0
+    for i in range(steps):
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        _, _, stats = ctd.ctd_get_dose_and_stddev(ctx, h, nvox, want_arrays=False)
+        _, _, stats = ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)
         t_transport += stats["t_transport_s"]
         launches += stats["transport_launches"]
         flush.zero_()
     torch.cuda.synchronize()
-    clk.stop_window()
-    clk.__exit__(None, None, None)
-    barrier(world)
+    b = clk.mark() if clk else 0
+    t_dev = sum(x.elapsed_time(y) for x, y in ev) * 1e-3
+    return {"t_dev": t_dev, "t_transport": t_transport, "launches": launches, "stats": stats,
+            "ramp": {"seconds": ramp_t, "runs": ramp}, "clocks": clk.summary(a, b) if clk else None}
+
+
+def rsd_stopped(ctd, ctx, h, p, seed, rsd, sec_run):
+    """Seconds to 1 % avg RSD, measured with the RSD-stopped served form: batches of a
+    tenth of the extrapolated need N (RSD / 1 %)^2, stopped at 1 % after >= 10 batches."""
+    import torch
+    n_1 = p.n_hist * (rsd / 0.01) ** 2
+    B = int(max(1e6, n_1 / 10))
     torch.cuda.synchronize()
-    t_dev = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
-    t_max = max_over_ranks(t_dev, world, dev)
-    hist_total = sum_over_ranks(float(p.n_hist * args.steps), world, dev)
-    value = hist_total / t_max
+    t0 = time.perf_counter()
+    rid = ctd.ctd_submit(ctx, h, B, 0.01, seed + 1, n_histories_max=int(40 * B))
+    st = ctd.ctd_wait(ctx, rid, 600.0)
+    return {"seconds": time.perf_counter() - t0, "histories": st["histories"], "batches": st["batches"],
+            "avg_rsd": st["avg_rsd"], "batch_histories": B,
+            "extrapolated_seconds": sec_run * (rsd / 0.01) ** 2}
 
-    # sec-to-1% avg RSD: N scales as RSD^-2 at fixed variance per history (extrapolated),
-    # and measured by the RSD-stopped served form: batches of a tenth of the extrapolated
-    # count, stopped at 1 % after at least 10 batches
-    rsd = stats["avg_rsd"]
-    sec_run = t_dev / args.steps
-    sec_to_1 = sec_run * (rsd / 0.01) ** 2
-    measured_1 = None
-    if args.rsd_stop and rank == 0:
-        n_1 = p.n_hist * (rsd / 0.01) ** 2
-        B = int(max(1e6, n_1 / 10))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rid = ctd.ctd_submit(ctx, h, B, 0.01, seed + 1, n_histories_max=int(40 * B))
-        st1 = ctd.ctd_wait(ctx, rid, 600.0)
-        measured_1 = {"seconds": time.perf_counter() - t0, "histories": st1["histories"], "batches": st1["batches"],
-                      "avg_rsd": st1["avg_rsd"], "batch_histories": B}
 
-    # end to end through the public API with host buffers: phantom upload, set-up,
-    # run and the read-back of dose and stddev, every step
-    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+def memory_probes(ctd, ctx, nvox):
+    """Memory ceilings measured on this GPU by the library's probes over as many slots
+    as the phantom has voxels: binary64 reductions into random tally slots, random
+    voxel (material + density) gathers, random 4-byte gathers."""
+    n_ops = 1 << 31
+    return {"l2_red_per_s": ctd.ctd_probe_memory(ctx, ctd.PROBE_L2_RED, nvox, n_ops),
+            "voxel_gather_per_s": ctd.ctd_probe_memory(ctx, ctd.PROBE_VOXEL, nvox, n_ops),
+            "gather4_per_s": ctd.ctd_probe_memory(ctx, ctd.PROBE_GATHER4, nvox, n_ops),
+            "probe": f"{n_ops} operations on uniform random slots of {nvox} voxels "
+                     f"({nvox * 8 / 1e6:.0f} MB binary64 tally, {nvox * 5 / 1e6:.0f} MB voxels), "
+                     f"mean of 3 launches after 1"}
+
+
+def roofline(p, run, peaks, peak_kind, probes, prof):
+    """The transport kernel against its ceilings.  frac: the algorithmic bytes of a
+    history -- 5 B per Woodcock step (material byte + binary32 density) and 8 B per
+    deposit (a binary64 reduction) -- over one launch's histories and its average
+    launch time, against the measured HBM copy bandwidth.  Beside it the L2-reduction
+    and voxel-gather fractions of the probes' ceilings, and the SM-issue fraction."""
+    st = run["stats"]
+    n = st["histories"]
+    launches = max(run["launches"], 1)
+    t_launch = run["t_transport"] / launches
+    hist_launch = n / st["transport_launches"]
+    steps_h = st["steps"] / n
+    dep_h = (st["pe"] + st["compton"]) / n
+    bytes_h = 5.0 * steps_h + 8.0 * dep_h
+    achieved = bytes_h * hist_launch / t_launch / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
+    out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+           "traffic": traffic * hist_launch / prof["histories_per_launch"] if traffic else None,
+           "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+           "kernel": "transport_kernel", "launches": run["launches"], "avg_launch_ms": 1e3 * t_launch,
+           "histories_per_launch": hist_launch, "bytes_per_history": bytes_h,
+           "steps_per_history": steps_h, "deposits_per_history": dep_h,
+           "algorithmic_bytes_per_launch": bytes_h * hist_launch}
+    hist_s = hist_launch / t_launch
+    if probes:
+        out["l2_reduction"] = {"achieved_per_s": hist_s * dep_h, "peak_per_s": probes["l2_red_per_s"],
+                               "frac": hist_s * dep_h / probes["l2_red_per_s"]}
+        out["voxel_gather"] = {"achieved_per_s": hist_s * steps_h, "peak_per_s": probes["voxel_gather_per_s"],
+                               "frac": hist_s * steps_h / probes["voxel_gather_per_s"]}
+        out["probe"] = probes["probe"]
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    ipeak = SM_COUNT * LANES_PER_SM_CLK * mhz * 1e6 / 1e12
+    lih = prof.get("lane_inst_per_history") if prof else None
+    out["issue"] = {"lane_inst_per_history": lih, "achieved_t_per_s": hist_s * lih / 1e12 if lih else None,
+                    "peak_t_per_s": ipeak, "frac": hist_s * lih / 1e12 / ipeak if lih else None,
+                    "peak_source": f"{SM_COUNT} SM x {LANES_PER_SM_CLK} lanes x {mhz:.0f} MHz",
+                    "source": (prof or {}).get("capture")}
+    return out
+
+
+def error_vs_oracle(ctd, ctx, h, p, ranges, o_edep, o_counts):
+    """The device over the oracle's sample (the same histories): relative error of the
+    total deposit, of each voxel's deposit above 10 % of the maximum, and of the counts."""
+    for i, (a, b) in enumerate(ranges):
+        ctd.ctd_run_range(ctx, h, p.n_hist, p.seed, p.n_batches, a, b, clear=(i == 0))
+    _, _, st = ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)
+    ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
+    m = o_edep > 0.1 * o_edep.max()
+    rel = np.abs(ed[m] - o_edep[m]) / o_edep[m]
+    counts = {k: (st[k] - o_counts[k]) / max(o_counts[k], 1) for k in ("pe", "compton", "rayleigh", "fictitious",
+                                                                         "escaped", "missed")}
+    return {"histories": int(sum(b - a for a, b in ranges)), "sample": "the CPU baseline's sample, same histories",
+            "total_edep_rel": float((st["e_deposited_kev"] - o_counts["e_deposited"]) / o_counts["e_deposited"]),
+            "voxel_edep_rel_median": float(np.median(rel)), "voxel_edep_rel_p99": float(np.percentile(rel, 99)),
+            "voxel_edep_rel_max": float(rel.max()), "voxels": int(m.sum()), "count_rel": counts}
+
+
+def e2e_rate(ctd, ctx, p, seed, steps, world, dev):
+    """The same metric end to end through the public API with host buffers: phantom
+    upload from pinned memory, set-up, run, read-back of dose and stddev, release."""
+    import torch
+    nvox = p.phantom.nvox
     mat_h = torch.from_numpy(np.ascontiguousarray(p.phantom.mat).ravel()).pin_memory().numpy()
     rho_h = torch.from_numpy(np.ascontiguousarray(p.phantom.rho).ravel()).pin_memory().numpy()
     dose_h = torch.empty(nvox, dtype=torch.float64).pin_memory().numpy()
@@ -329,7 +391,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(steps):
         ph = p.phantom
         h2 = ctd.ctd_create_phantom(ctx, ph.nx, ph.ny, ph.nz, ph.dx, ph.dy, ph.dz, mat_h, rho_h, ph.materials)
         s = p.source
@@ -347,98 +409,50 @@ def run_ours(args):
         ctd.ctd_run(ctx, h2, p.n_hist, seed, p.n_batches)
         ctd._check(L.ctd_get_dose_and_stddev(ctx, h2, ctd._dp(dose_h), ctd._dp(sd_h), nvox, ctd.C.byref(st)))
         ctd.ctd_destroy_phantom(ctx, h2)
-    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e_value = sum_over_ranks(float(p.n_hist * e2e_steps), world, dev) / t_e2e
-    h2d = nvox * (1 + 4) + 3 * 8 * len(p.spectrum.w)
-    d2h = nvox * 16
+    t = max_over_ranks(time.perf_counter() - t0, world, dev)
+    return {"value": sum_over_ranks(float(p.n_hist * steps), world, dev) / t, "unit": UNIT,
+            "h2d_bytes_per_step": nvox * (1 + 4) + 3 * 8 * len(p.spectrum.w), "d2h_bytes_per_step": nvox * 16,
+            "steps": steps}
 
-    # roofline of the transport kernel: lane-instructions per history (KERNEL_PROFILE, from
-    # the ncu capture) over the SM issue ceiling 152 SM x 128 lanes x clock
-    peaks, peak_kind = load_peaks()
-    ck = clk.summary()
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = SM_COUNT * LANES_PER_SM_CLK * mhz * 1e6 / 1e12        # tera lane-instructions / s
-    # the lane-instruction count was measured for the Klein-Nishina model
-    prof = KERNEL_PROFILE.get(p.name, {}) if args.compton == "kn" and args.rayleigh == "gauss" else {}
-    inst_per_hist = args.inst_per_history or prof.get("lane_inst_per_history")
-    achieved = p.n_hist * args.steps * inst_per_hist / t_transport / 1e12 if inst_per_hist else None
-    traffic = args.traffic_per_launch or prof.get("dram_bytes_per_launch")
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-inst/s",
-            "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "lane_inst_per_history": inst_per_hist,
-            "kernel": "transport_kernel", "launches": launches,
-            "avg_launch_ms": 1e3 * t_transport / max(launches, 1),
-            "peak_source": f"{SM_COUNT} SM x {LANES_PER_SM_CLK} lanes x {mhz:.0f} MHz ({peak_kind} max clock)"}
-    # memory-side view: algorithmic bytes per history, counted live from this run's steps and deposits
-    steps_per_hist = stats["steps"] / p.n_hist
-    deposits_per_hist = (stats["pe"] + stats["compton"]) / p.n_hist
-    bytes_per_hist = steps_per_hist * 5.0 + deposits_per_hist * 16.0
-    roof["memory_side"] = {"bytes_per_history": bytes_per_hist,
-                           "achieved_gbs": p.n_hist * args.steps * bytes_per_hist / t_transport / 1e9,
-                           "peak_gbs": peaks.get("hbm_gbs"),
-                           "atomics_per_s": p.n_hist * args.steps * deposits_per_hist / t_transport,
-                           "steps_per_history": steps_per_hist, "deposits_per_history": deposits_per_hist}
-    if not args.no_probe:
-        # memory ceilings measured on this GPU by the library's probes, over the same
-        # number of slots as the phantom: binary64 reductions into random tally slots
-        # and random voxel (material + density) gathers
-        n_ops = 1 << 31
-        red = ctd.ctd_probe_memory(ctx, ctd.PROBE_L2_RED, nvox, n_ops)
-        vox = ctd.ctd_probe_memory(ctx, ctd.PROBE_VOXEL, nvox, n_ops)
-        g4 = ctd.ctd_probe_memory(ctx, ctd.PROBE_GATHER4, nvox, n_ops)
-        ms = roof["memory_side"]
-        steps_per_s = p.n_hist * args.steps * steps_per_hist / t_transport
-        ms.update({"l2_red_peak_per_s": red, "atomic_frac": ms["atomics_per_s"] / red,
-                   "voxel_gather_peak_per_s": vox, "steps_per_s": steps_per_s, "gather_frac": steps_per_s / vox,
-                   "gather4_peak_per_s": g4,
-                   "probe": f"{n_ops} operations on uniform random slots of {nvox} voxels "
-                            f"({nvox * 8 / 1e6:.0f} MB binary64 tally, {nvox * 5 / 1e6:.0f} MB voxels), "
-                            f"mean of 3 launches after 1"})
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = cpu_cores()
-        r, n, dt, _ = oracle_rate(p, args.ref_seconds, threads)
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"binary64 oracle, {n} histories of {p.name} in 64 equal ranges spread through batch 0 "
-                         f"(all 1 keV bins), {dt:.1f} s, {threads} threads"}
-
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": warmup_done, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": p.name, "voxels": [p.phantom.nx, p.phantom.ny, p.phantom.nz],
-                       "voxel_cm": p.phantom.dx, "histories_per_step": p.n_hist, "batches": p.n_batches,
-                       "kvp": 120 if p.name.startswith("cbct_water") else 100 if p.name == "head" else None,
-                       "parallelism": f"replicas{world}",
-                       "l2": "flushed between steps (256 MB write outside timed events)",
-                       "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk,
-                       "flight_cap": args.flight_cap, "compton": args.compton, "rayleigh": args.rayleigh},
-            "sec_to_1pct_avg_rsd": measured_1["seconds"] if measured_1 else sec_to_1,
-            "sec_to_1pct_avg_rsd_extrapolated": sec_to_1, "rsd_stopped_run": measured_1,
-            "avg_rsd": rsd, "paper_sigma_bar": stats["paper_sigma_bar"],
-            # Sec. 3.1's simulation efficiency 1 / (sigma_bar^2 T), T the device time of one run
-            "paper_efficiency_per_s": (1.0 / (stats["paper_sigma_bar"] ** 2 * sec_run)
-                                       if stats["paper_sigma_bar"] > 0 else None),
-            "clocks": ck,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
-            "gpu_launches": launches + 17 * args.steps,
-            "roofline": roof,
-            "cpu_baseline": cpu,
-        }), flush=True)
+# --------------------------------------------------------------------------- legs
+def leg_head(ctd, args, stream, flush, peaks, peak_kind, clk):
+    """The head workload: histories/s over a few timed runs, seconds to 1 %, roofline,
+    error against the oracle on a short sample."""
+    import torch
+    p = workload("head", args.compton, args.rayleigh)
+    ctx = ctd.ctd_create(device=0, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
+                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap)
+    h = ctd.load_problem(ctx, p)
+    run = timed_runs(ctd, ctx, h, p, p.seed, args.head_steps, 2, 0.0, stream, flush, torch.cuda.synchronize, clk)
+    st = run["stats"]
+    sec_run = run["t_dev"] / args.head_steps
+    out = {"workload": "head", "voxels": [p.phantom.nx, p.phantom.ny, p.phantom.nz], "voxel_cm": p.phantom.dx,
+           "histories_per_step": p.n_hist, "steps": args.head_steps, "value": p.n_hist * args.head_steps / run["t_dev"],
+           "unit": UNIT, "ms_per_step": 1e3 * sec_run, "avg_rsd": st["avg_rsd"], "clocks": run["clocks"]}
+    out["sec_to_1pct_avg_rsd_extrapolated"] = sec_run * (st["avg_rsd"] / 0.01) ** 2
+    if args.rsd_stop:
+        r = rsd_stopped(ctd, ctx, h, p, p.seed, st["avg_rsd"], sec_run)
+        out["sec_to_1pct_avg_rsd"] = r["seconds"]
+        out["rsd_stopped_run"] = r
+    probes = None if args.no_probe else memory_probes(ctd, ctx, p.phantom.nvox)
+    out["roofline"] = roofline(p, run, peaks, peak_kind, probes, KERNEL_PROFILE.get("head"))
+    if not args.no_cpu_baseline:
+        _, _, _, ranges, edep, c = oracle_sample(p, 3.0, cpu_cores(), keep=True)
+        out["error_vs_fp64_oracle"] = error_vs_oracle(ctd, ctx, h, p, ranges, edep, c)
+    out["gpu_launches"] = run["launches"] + 17 * args.head_steps
+    ctd.ctd_destroy_phantom(ctx, h)
     ctd.ctd_destroy(ctx)
+    return out
 
 
-# --------------------------------------------------------------------------- batched form
-def run_batched(args):
-    """64 uneven requests: all in shared launches (batched form) against the same
-    requests one after another (plain single-request form)."""
+def leg_batched(ctd, args, clk):
+    """Uneven requests: request chains in one CUDA graph and one shared launch per
+    batch (batched form) against the same requests one ctd_run after another (plain
+    single-request form)."""
     import torch
 
-    from paper_1109_3266_gb300 import ctd, inputs as I
-
+    from paper_1109_3266_gb300 import inputs as I
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     sides = tuple(range(64, args.max_side + 1, 32))
@@ -472,121 +486,253 @@ def run_batched(args):
 
     timed(batched, 1)
     timed(lambda: batched(1), 1)
-    with Clocks(0) as clk:
-        tb = timed(batched, args.steps)
-        ts = timed(lambda: batched(1), max(1, args.steps // 2))
-        tp = timed(plain, max(1, args.steps // 2))
+    a = clk.mark()
+    tb = timed(batched, args.batched_reps)
+    ts = timed(lambda: batched(1), args.batched_reps)
+    tp = timed(plain, args.batched_reps)
+    b = clk.mark()
     rsd = [ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)[2]["avg_rsd"] for h in hs]
-    vb = n_total / float(np.mean(tb))
-    vs = n_total / float(np.mean(ts))
-    vp = n_total / float(np.mean(tp))
-    print(json.dumps({
-        "metric": "photon histories/sec, batched form vs plain single-request form", "value": vb, "unit": UNIT,
-        "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * float(np.mean(tb)),
-        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "batched", "requests": len(reqs), "histories_per_step": n_total, "batches": nb,
-                   "sides": sorted({p.meta["side"] for p in reqs}), "hist_range": [args.hist_lo, args.hist_hi],
-                   "launches": "one chain of single-request launches per request, one CUDA graph"},
-        "plain_value": vp, "plain_ms_per_step": 1e3 * float(np.mean(tp)), "speedup_vs_plain": vb / vp,
-        "shared_launch_value": vs, "shared_launch_speedup_vs_plain": vs / vp,
-        "avg_rsd_range": [float(min(rsd)), float(max(rsd))], "clocks": clk.summary(),
-    }), flush=True)
+    vb, vs, vp = (n_total / float(np.mean(t)) for t in (tb, ts, tp))
     for c, hl in zip(ctxs, hss):
         for h in hl:
             ctd.ctd_destroy_phantom(c, h)
         ctd.ctd_destroy(c)
+    return {"workload": "batched", "requests": len(reqs), "histories_per_step": n_total, "batches": nb,
+            "sides": sorted({p.meta["side"] for p in reqs}), "hist_range": [args.hist_lo, args.hist_hi],
+            "reps": args.batched_reps, "chains_value": vb, "shared_launch_value": vs, "plain_value": vp,
+            "unit": UNIT, "chains_speedup_vs_plain": vb / vp, "shared_launch_speedup_vs_plain": vs / vp,
+            "chains_ms": 1e3 * float(np.mean(tb)), "shared_launch_ms": 1e3 * float(np.mean(ts)),
+            "plain_ms": 1e3 * float(np.mean(tp)), "avg_rsd_range": [float(min(rsd)), float(max(rsd))],
+            "launches": "chains: one chain of single-request launches per request on its own stream, one CUDA "
+                        "graph; shared: one multi-request launch per batch", "clocks": clk.summary(a, b)}
 
 
-# --------------------------------------------------------------------------- served form
-def run_served(args):
+def leg_served(ctd, args, clk):
     """Poisson stream of head requests, each stopped at 1 % avg RSD: continuous
-    batching against one request at a time (the plain single-request form)."""
+    batching (every request on its own stream) against one request at a time."""
     import torch
 
-    from paper_1109_3266_gb300 import ctd, inputs as I, serve
-
+    from paper_1109_3266_gb300 import inputs as I, serve
     torch.cuda.set_device(0)
     d = args.served_voxel_cm
     nx, ny, nz = int(round(25.6 / d)), int(round(25.6 / d)), int(round(16.0 / d))
     pool = [I.head_phantom(nx, ny, nz, d, seed=3 + k) for k in range(args.pool)]
-    arrivals = I.served_arrivals(args.n_requests, args.rate, seed=5)
+    arrivals = I.served_arrivals(args.served_requests, args.rate, seed=5)
 
     def make(seed):
         return I.head_request(pool[seed % len(pool)], seed)
 
     out = {}
-    for label, max_active in (("continuous", 0), ("one_at_a_time", 1)):
+    for label, max_active, budget in (("continuous", 0, args.round_histories), ("one_at_a_time", 1, 0.0)):
         ctx = ctd.ctd_create(device=0, multi_blocks_per_sm=args.multi_blocks_per_sm, serve_max_active=max_active,
-                             shared_launch=args.shared_launch, serve_round_histories=args.round_histories)
+                             shared_launch=args.shared_launch, serve_round_histories=budget)
         # warm-up: one request alone
         serve.serve(ctx, [(0.0, 4999)], make, args.batch_histories, 0.01, n_histories_max=40 * args.batch_histories)
-        with Clocks(0) as clk:
-            reqs, wall = serve.serve(ctx, arrivals, make, args.batch_histories, 0.01,
-                                     n_histories_max=40 * args.batch_histories, time_limit_s=args.time_limit)
+        a = clk.mark()
+        reqs, wall = serve.serve(ctx, arrivals, make, args.batch_histories, 0.01,
+                                 n_histories_max=40 * args.batch_histories, time_limit_s=args.time_limit)
+        b = clk.mark()
         done = [r for r in reqs if np.isfinite(r.latency)]
         hist = sum(r.histories for r in done)
         out[label] = dict(serve.latency_summary(reqs), histories_per_s=hist / wall, wall_s=wall,
                           submitted=len(reqs), mean_batches=float(np.mean([r.batches for r in done])) if done else None,
                           mean_histories=float(np.mean([r.histories for r in done])) if done else None,
-                          clocks=clk.summary())
+                          round_histories=budget or 1e8, clocks=clk.summary(a, b))
         ctd.ctd_destroy(ctx)
     c, o = out["continuous"], out["one_at_a_time"]
-    print(json.dumps({
-        "metric": "served p50/p99 latency (s) and histories/sec at 1% avg RSD", "value": c["histories_per_s"],
-        "unit": UNIT, "p50_s": c["p50_s"], "p99_s": c["p99_s"], "n_gpus": 1, "higher_is_better": True,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "served", "phantom": [nx, ny, nz], "voxel_cm": d, "rate_per_s": args.rate,
-                   "requests": args.n_requests, "batch_histories": args.batch_histories, "rsd_target": 0.01,
-                   "min_batches": 10, "phantom_pool": args.pool, "time_limit_s": args.time_limit,
-                   "launches": "shared multi-request launch" if args.shared_launch else "one stream per request",
-                   "round_histories": args.round_histories or 1e8},
-        "continuous": c, "one_at_a_time": o,
-        "throughput_vs_one_at_a_time": (c["histories_per_s"] / o["histories_per_s"]) if o["histories_per_s"] else None,
-    }), flush=True)
+    return {"workload": "served", "phantom": [nx, ny, nz], "voxel_cm": d, "rate_per_s": args.rate,
+            "requests": args.served_requests, "batch_histories": args.batch_histories, "rsd_target": 0.01,
+            "min_batches": 10, "phantom_pool": args.pool, "p50_s": c["p50_s"], "p99_s": c["p99_s"],
+            "value": c["histories_per_s"], "unit": UNIT,
+            "launches": "shared multi-request launch" if args.shared_launch else "one stream per request",
+            "continuous": c, "one_at_a_time": o,
+            "throughput_vs_one_at_a_time": (c["histories_per_s"] / o["histories_per_s"]) if o["histories_per_s"]
+            else None,
+            "stand_in": f"heads of {d} cm voxels instead of the 0.1 cm ones: one 0.1 cm head needs about 1e11 "
+                        "histories to reach 1 % (about 15 s of this GPU), so 4 requests/s would be about 60x over "
+                        "its capacity and every latency would be queueing"}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+
+    from paper_1109_3266_gb300 import ctd
+
+    rank, world = dist_init(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    peaks, peak_kind = load_peaks()
+    # the clock sampler starts before any GPU work, so that its start-up is not timed
+    clk = Clocks(local).__enter__()
+
+    def sync():
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+
+    if world > 1:
+        from paper_1109_3266_gb300 import shard
+        p = workload(args.workload, args.compton, args.rayleigh, n_hist=1_000_000_000 * world)
+        ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
+                             threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap)
+        h = ctd.load_problem(ctx, p)
+        reduce = shard.nccl_allreduce(dev)
+        for _ in range(args.warmup):
+            shard.run_sharded(ctd, ctx, h, p.n_hist, p.seed, p.n_batches, rank, world, reduce, dev,
+                              nvox=p.phantom.nvox)
+            flush.zero_()
+        sync()
+        a = clk.mark()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            st = shard.run_sharded(ctd, ctx, h, p.n_hist, p.seed, p.n_batches, rank, world, reduce, dev)
+            ev[i][1].record(stream)
+            flush.zero_()
+        sync()
+        b = clk.mark()
+        t_dev = sum(x.elapsed_time(y) for x, y in ev) * 1e-3
+        t_max = max_over_ranks(t_dev, world, dev)
+        if rank == 0:
+            print(json.dumps({
+                "metric": METRIC, "value": p.n_hist * args.steps / t_max, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": p.name, "histories_per_step": p.n_hist, "batches": p.n_batches,
+                           "parallelism": f"history shards x{world}, one binary64 all-reduce of each batch tally",
+                           "l2": "flushed between steps (256 MB write outside timed events)"},
+                "avg_rsd": st["avg_rsd"], "clocks": clk.summary(a, b),
+                "gpu_launches": None,
+            }), flush=True)
+        clk.__exit__(None, None, None)
+        ctd.ctd_destroy(ctx)
+        return
+
+    p = workload(args.workload, args.compton, args.rayleigh)
+    nvox = p.phantom.nvox
+    ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
+                         threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap)
+    h = ctd.load_problem(ctx, p)
+    run = timed_runs(ctd, ctx, h, p, p.seed, args.steps, args.warmup, args.ramp_seconds, stream, flush, sync, clk)
+    st = run["stats"]
+    t_dev = run["t_dev"]
+    value = p.n_hist * args.steps / t_dev
+    sec_run = t_dev / args.steps
+    rsd = st["avg_rsd"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sec_run, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": p.name, "voxels": [p.phantom.nx, p.phantom.ny, p.phantom.nz],
+                   "voxel_cm": p.phantom.dx, "histories_per_step": p.n_hist, "batches": p.n_batches,
+                   "kvp": 120 if p.name.startswith("cbct_water") else 100 if p.name == "head" else None,
+                   "parallelism": "one GPU",
+                   "l2": "flushed between steps (256 MB write outside timed events)",
+                   "blocks_per_sm": args.blocks_per_sm, "threads": args.threads, "chunk": args.chunk,
+                   "flight_cap": args.flight_cap, "compton": args.compton, "rayleigh": args.rayleigh},
+        "clock_ramp": run["ramp"], "avg_rsd": rsd, "paper_sigma_bar": st["paper_sigma_bar"],
+        "sec_to_1pct_avg_rsd_extrapolated": sec_run * (rsd / 0.01) ** 2,
+        # Sec. 3.1's simulation efficiency 1 / (sigma_bar^2 T), T the device time of one run
+        "paper_efficiency_per_s": (1.0 / (st["paper_sigma_bar"] ** 2 * sec_run) if st["paper_sigma_bar"] > 0
+                                   else None),
+        "clocks": run["clocks"],
+    }
+    if args.rsd_stop:
+        r = rsd_stopped(ctd, ctx, h, p, p.seed, rsd, sec_run)
+        line["sec_to_1pct_avg_rsd"] = r["seconds"]
+        line["rsd_stopped_run"] = r
+    else:
+        line["sec_to_1pct_avg_rsd"] = line["sec_to_1pct_avg_rsd_extrapolated"]
+    line["e2e"] = e2e_rate(ctd, ctx, p, p.seed, max(1, min(args.e2e_steps, args.steps)), world, dev)
+    probes = None if args.no_probe else memory_probes(ctd, ctx, nvox)
+    prof = KERNEL_PROFILE.get(p.name) if args.compton == "kn" and args.rayleigh == "gauss" else None
+    line["roofline"] = roofline(p, run, peaks, peak_kind, probes, prof)
+    line["gpu_launches"] = run["launches"] + 17 * args.steps
+    if not args.no_cpu_baseline:
+        threads = cpu_cores()
+        r, n, dt, ranges, edep, c = oracle_sample(p, args.ref_seconds, threads, keep=True)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"binary64 oracle, {n} histories of {p.name} in 64 equal ranges spread "
+                                          f"through batch 0 (all 1 keV bins), {dt:.1f} s, {threads} threads"}
+        line["error_vs_fp64_oracle"] = error_vs_oracle(ctd, ctx, h, p, ranges, edep, c)
+    else:
+        line["cpu_baseline"] = None
+    ctd.ctd_destroy_phantom(ctx, h)
+    ctd.ctd_destroy(ctx)
+    legs = args.legs.split(",") if args.legs else []
+    if "head" in legs:
+        line["head"] = leg_head(ctd, args, stream, flush, peaks, peak_kind, clk)
+    if "batched" in legs:
+        line["batched"] = leg_batched(ctd, args, clk)
+    if "served" in legs:
+        line["served"] = leg_served(ctd, args, clk)
+    clk.__exit__(None, None, None)
+    print(json.dumps(line), flush=True)
+
+
+def run_form(args):
+    """--workload batched / served: the leg on its own, as its own JSON line."""
+    from paper_1109_3266_gb300 import ctd
+    with Clocks(0) as clk:
+        out = leg_batched(ctd, args, clk) if args.workload == "batched" else leg_served(ctd, args, clk)
+    out.update({"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic"})
+    if args.workload == "batched":
+        out["value"] = out["chains_value"]
+    print(json.dumps(out), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cbct_water")
+    ap.add_argument("--legs", default=None,
+                    help="comma list of head,batched,served (default: all three for cbct_water, none otherwise; "
+                         "'' for none)")
+    ap.add_argument("--ramp-seconds", type=float, default=2.0, help="untimed runs before the warm-up")
+    ap.add_argument("--head-steps", type=int, default=4)
+    ap.add_argument("--batched-reps", type=int, default=2)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--flight-cap", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the memory-ceiling probes")
     ap.add_argument("--rsd-stop", type=int, default=1, help="measure sec-to-1%% with the RSD-stopped form")
-    ap.add_argument("--inst-per-history", type=float, default=0.0)
     ap.add_argument("--n-requests", type=int, default=64)
     ap.add_argument("--max-side", type=int, default=256)
+    ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--pool", type=int, default=4)
-    ap.add_argument("--served-voxel-cm", type=float, default=0.1)
-    ap.add_argument("--batch-histories", type=int, default=int(9e9))
-    ap.add_argument("--time-limit", type=float, default=None)
+    ap.add_argument("--served-voxel-cm", type=float, default=0.5)
+    ap.add_argument("--batch-histories", type=int, default=80_000_000)
+    ap.add_argument("--time-limit", type=float, default=120.0)
     ap.add_argument("--multi-blocks-per-sm", type=int, default=0)
     ap.add_argument("--shared-launch", type=int, default=0, help="served form: one shared multi-request launch")
-    ap.add_argument("--round-histories", type=float, default=0.0,
-                    help="served form: histories one round may hold before admission stops (0: 1e8)")
+    ap.add_argument("--round-histories", type=float, default=1e9,
+                    help="served form: histories of one batch of every running request admission keeps within")
     ap.add_argument("--compton", default="kn", choices=["kn", "wh"],
                     help="Compton model: free-electron Klein-Nishina or Waller-Hartree")
     ap.add_argument("--rayleigh", default="gauss", choices=["gauss", "iaa"],
                     help="Rayleigh form factor: analytic exp(-q^2/q0^2) or independent-atom of the elements")
     ap.add_argument("--hist-lo", type=float, default=1e7)
     ap.add_argument("--hist-hi", type=float, default=1e9)
-    ap.add_argument("--traffic-per-launch", type=float, default=None)
     args = ap.parse_args()
+    if args.legs is None:
+        args.legs = "head,batched,served" if args.workload == "cbct_water" else ""
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batched":
-        run_batched(args)
-    elif args.workload == "served":
-        run_served(args)
+    elif args.workload in ("batched", "served"):
+        run_form(args)
     else:
         run_ours(args)
 

@@ -266,6 +266,36 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
 int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches,
                   uint64_t h_begin, uint64_t h_end, int clear);
 
+/* Sharded run: one problem of n_histories in n_batches batches split among
+ * several GPUs (Sec. 4: histories distributed among GPUs that run without
+ * interfering), each rank with its own context and copy of the phantom.
+ * Within every batch, rank r of W transports the local histories
+ * [floor(n_b r / W), floor(n_b (r + 1) / W)) of the batch's n_b, with the same
+ * random numbers any other partition gives them; the ranks then sum their
+ * partial batch tallies (binary64, a collective of the caller's choice) and
+ * each folds the sum, so every rank holds the same batch statistics as a
+ * single-GPU ctd_run, up to the order of binary64 additions.
+ *   ctd_shard_begin: start the run on phantom ph (clears its sums and counts).
+ *   ctd_shard_batch: transport local histories [local_begin, local_end) of batch
+ *       `batch` and add their deposits (keV) to tally_dev, nvox device doubles
+ *       the caller owns (asynchronously, on the context's stream).
+ *   ctd_shard_fold: fold the summed batch tally tally_dev into the statistics
+ *       (Sec. 2.2.1) and leave tally_dev zeroed for the next batch (asynchronous).
+ *   ctd_shard_counts: this rank's counts (10: photoelectric, Compton, Rayleigh,
+ *       fictitious, escaped, missed, cutoff, terminated, aborted, steps) and
+ *       energies (2: emitted, escaped keV), to be summed over the ranks.
+ *   ctd_shard_finish: mean dose, standard error and the precision measures of
+ *       the folded batches, with the ranks' summed counts and energies as the
+ *       run's stats; ctd_get_dose_and_stddev then reads the result.
+ * Errors: CTD_ENOTFOUND, CTD_EINVAL (no run begun, batch or range out of range,
+ * null buffers), CTD_EBUSY. */
+int ctd_shard_begin(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches);
+int ctd_shard_batch(ctd_ctx *ctx, ctd_phantom ph, int batch, uint64_t local_begin, uint64_t local_end,
+                    double *tally_dev);
+int ctd_shard_fold(ctd_ctx *ctx, ctd_phantom ph, int batch, double *tally_dev);
+int ctd_shard_counts(ctd_ctx *ctx, ctd_phantom ph, uint64_t *counts, double *energies);
+int ctd_shard_finish(ctd_ctx *ctx, ctd_phantom ph, const uint64_t *counts, const double *energies);
+
 /* Per-history records for validation (the primary-only comparison of the
  * interaction choice, Sec. 2.1, and of the source, Secs. 2.2.4-2.2.6, history
  * by history).  Runs histories [h_begin, h_end) of the n_histories/n_batches
@@ -317,12 +347,20 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
  * random numbers keyed by seed until, after at least min_batches batches, its
  * avg RSD is <= rsd_target, or until n_histories_max histories have run.
  * Requests wait in a queue until admitted, first in, first out (free device
- * memory above the context's reserve, serve_reserve_bytes, fewer than serve_max_active
- * running, one round within serve_round_histories); each call of ctd_serve_step
- * admits what fits, runs one batch of every running request (each on its own
- * stream, or with shared_launch = 1 in one shared launch, which needs every
- * request on one node grid), folds them, updates the statistics and retires
- * finished requests.
+ * memory above the context's reserve, serve_reserve_bytes, fewer than
+ * serve_max_active running (at most 64 with shared_launch = 0), one batch of
+ * every running request within serve_round_histories).
+ * With shared_launch = 0 every running request advances on its own stream,
+ * independently of the others: each call of ctd_serve_step takes in the
+ * batches that have finished on the GPU (a batch counts only then), retires
+ * requests that reached their stop and requests cancelled, admits what fits
+ * and launches the next batch (transport, fold and, from min_batches on, the
+ * statistics) of every running request with nothing on the GPU.  It does not
+ * wait for the GPU, so requests submitted while others run start at the next
+ * call.  With shared_launch = 1 each call runs one round, one batch of every
+ * running request in one shared launch (every request on one node grid), and
+ * waits for it; a round whose launches fail counts for no request and marks
+ * them CTD_REQ_FAILED.
  * A finished request's result equals ctd_run(phantom, k * batch_histories,
  * seed, k) for its k batches (up to the order of binary64 additions), alone or
  * mixed with others, and is read with ctd_get_dose_and_stddev.  A phantom
@@ -357,15 +395,16 @@ typedef struct {
 } ctd_req_status;
 
 int ctd_submit(ctd_ctx *ctx, ctd_phantom ph, const ctd_request *req, ctd_req_id *out);
-/* One round of the served form; *n_active (may be NULL) is the number of
- * requests still queued or running afterwards. */
+/* One step of the served form (above); *n_active (may be NULL) is the number
+ * of requests still queued or running afterwards. */
 int ctd_serve_step(ctd_ctx *ctx, int *n_active);
 int ctd_poll(ctd_ctx *ctx, ctd_req_id id, ctd_req_status *out);
 /* Drive ctd_serve_step until request id has finished or timeout_s seconds have
  * passed (CTD_ETIMEOUT); out may be NULL. */
 int ctd_wait(ctd_ctx *ctx, ctd_req_id id, double timeout_s, ctd_req_status *out);
-/* A queued request is dropped at once, a running one at the next round;
- * either ends as CTD_REQ_CANCELLED. */
+/* A queued request is dropped at once, a running one at the next
+ * ctd_serve_step (after its batch on the GPU, if any, has finished); either
+ * ends as CTD_REQ_CANCELLED. */
 int ctd_cancel(ctd_ctx *ctx, ctd_req_id id);
 
 /* Autotuner: launch-shape search for the single-request transport kernel.

@@ -430,8 +430,9 @@ int transport_time(ctd_ctx *ctx, size_t n_launch, double &t)
 // Counts, energies and precision figures of several phantoms read back in one
 // go (copies into pinned staging, one synchronisation).
 int collect_many(ctd_ctx *ctx, Phantom *const *ps, int n, size_t n_launch, double t0_wall,
-                 const double *t0_each)
+                 const double *t0_each, cudaStream_t stream)
 {
+    const cudaStream_t cs = stream ? stream : ctx->stream;
     if (static_cast<size_t>(n) > ctx->staged_n) {
         if (ctx->staged) cudaFreeHost(ctx->staged);
         ctx->staged = nullptr;
@@ -444,11 +445,11 @@ int collect_many(ctd_ctx *ctx, Phantom *const *ps, int n, size_t n_launch, doubl
     }
     for (int i = 0; i < n; ++i) {
         CK(cudaMemcpyAsync(&ctx->staged[i].c, ps[i]->counts.p, sizeof(ctd::DeviceCounts), cudaMemcpyDeviceToHost,
-                           ctx->stream));
+                           cs));
         CK(cudaMemcpyAsync(ctx->staged[i].res, ps[i]->result.p, sizeof(ctx->staged[i].res), cudaMemcpyDeviceToHost,
-                           ctx->stream));
+                           cs));
     }
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(cs));
     const double t_now = now_s();
     double t_transport;
     int rc;
@@ -540,6 +541,7 @@ int ctd_destroy(ctd_ctx *ctx)
     if (!ctx) return CTD_OK;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (auto l : ctx->lanes) cudaStreamSynchronize(l);
     ctx->phantoms.clear();
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     for (auto e : ctx->events) cudaEventDestroy(e);
@@ -547,6 +549,8 @@ int ctd_destroy(ctd_ctx *ctx)
     for (auto l : ctx->lanes) cudaStreamDestroy(l);
     for (auto e : ctx->lane_done) cudaEventDestroy(e);
     if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
+    for (auto e : ctx->serve_ev) cudaEventDestroy(e);
+    if (ctx->serve_res) cudaFreeHost(ctx->serve_res);
     if (ctx->staged) cudaFreeHost(ctx->staged);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -958,6 +962,125 @@ int ctd_run_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t s
     if ((rc = collect(ctx, *P, launches, t0))) return rc;
     P->stats.histories = h_end - h_begin;
     P->stats.n_batches = n_batches;
+    return CTD_OK;
+}
+
+int ctd_shard_begin(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, int n_batches)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (n_batches < 2 || static_cast<uint64_t>(n_batches) > n_histories)
+        return fail(CTD_EINVAL, "need 2 <= n_batches <= n_histories");
+    if ((rc = busy(P))) return rc;
+    if ((rc = prepare_run(ctx, *P, n_histories, n_batches))) return rc;
+    const size_t nv = P->nvox;
+    CK(cudaMemsetAsync(P->sum_d.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+    P->have_result = false;
+    P->shard_n = n_histories;
+    P->shard_nb = n_batches;
+    P->shard_seed = seed;
+    P->shard_t0 = now_s();
+    return CTD_OK;
+}
+
+// batch b of the sharded run: its size, which allocation it uses, its first history
+static void shard_batch_of(const Phantom &P, int b, uint64_t &size, int &which, uint64_t &h0)
+{
+    const uint64_t n_lo = P.shard_n / P.shard_nb, rem = P.shard_n % P.shard_nb;
+    const uint64_t ub = static_cast<uint64_t>(b);
+    size = ub < rem ? n_lo + 1 : n_lo;
+    which = ub < rem ? 0 : 1;
+    h0 = ub * n_lo + (ub < rem ? ub : rem);
+}
+
+int ctd_shard_batch(ctd_ctx *ctx, ctd_phantom ph, int batch, uint64_t local_begin, uint64_t local_end,
+                    double *tally_dev)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (P->shard_nb == 0) return fail(CTD_EINVAL, "no sharded run begun on phantom %d", ph);
+    if (batch < 0 || batch >= P->shard_nb) return fail(CTD_EINVAL, "batch %d outside [0, %d)", batch, P->shard_nb);
+    if (!tally_dev) return fail(CTD_EINVAL, "null tally buffer");
+    uint64_t size, h0;
+    int which;
+    shard_batch_of(*P, batch, size, which, h0);
+    if (local_begin > local_end || local_end > size)
+        return fail(CTD_EINVAL, "history range outside batch %d of %llu histories", batch,
+                    static_cast<unsigned long long>(size));
+    if (local_begin == local_end) return CTD_OK;
+    ctd::RequestDesc T;
+    fill_request(*P, P->shard_seed, T);
+    return transport(ctx, *P, T, which, h0, local_begin, local_end, tally_dev, static_cast<size_t>(batch));
+}
+
+int ctd_shard_fold(ctd_ctx *ctx, ctd_phantom ph, int batch, double *tally_dev)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (P->shard_nb == 0) return fail(CTD_EINVAL, "no sharded run begun on phantom %d", ph);
+    if (batch < 0 || batch >= P->shard_nb) return fail(CTD_EINVAL, "batch %d outside [0, %d)", batch, P->shard_nb);
+    if (!tally_dev) return fail(CTD_EINVAL, "null tally buffer");
+    uint64_t size, h0;
+    int which;
+    shard_batch_of(*P, batch, size, which, h0);
+    // d = E / (m n_b) with m = rho V / 1000 kg
+    const double scale = ctd::kKevToJ * 1000.0 / (P->dx * P->dy * P->dz * static_cast<double>(size));
+    CKS(ctd::launch_fold(tally_dev, P->rho.p, P->sum_d.p, P->sum_d2.p, P->edep.p, P->nvox, scale, ctx->stream));
+    return CTD_OK;
+}
+
+int ctd_shard_counts(ctd_ctx *ctx, ctd_phantom ph, uint64_t *counts, double *energies)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (!counts || !energies) return fail(CTD_EINVAL, "null output");
+    ctd::DeviceCounts c;
+    CK(cudaMemcpyAsync(&c, P->counts.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 10; ++i) counts[i] = c.n[i];
+    energies[0] = ctd::fixed_kev(c.e_fix[0], c.e_fix[1]);
+    energies[1] = ctd::fixed_kev(c.e_fix[2], c.e_fix[3]);
+    return CTD_OK;
+}
+
+int ctd_shard_finish(ctd_ctx *ctx, ctd_phantom ph, const uint64_t *counts, const double *energies)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    Phantom *P = find(ctx, ph);
+    if (!P) return fail(CTD_ENOTFOUND, "unknown phantom %d", ph);
+    if (P->shard_nb == 0) return fail(CTD_EINVAL, "no sharded run begun on phantom %d", ph);
+    if (!counts || !energies) return fail(CTD_EINVAL, "null totals");
+    CKS(finish_stats(*P, P->shard_nb, ctx->stream));
+    if ((rc = collect(ctx, *P, 0, P->shard_t0))) return rc;
+    ctd_run_stats &s = P->stats;
+    s.pe = counts[ctd::kCntPe];
+    s.compton = counts[ctd::kCntCompton];
+    s.rayleigh = counts[ctd::kCntRayleigh];
+    s.fictitious = counts[ctd::kCntFict];
+    s.escaped = counts[ctd::kCntEscaped];
+    s.missed = counts[ctd::kCntMissed];
+    s.cutoff = counts[ctd::kCntCutoff];
+    s.terminated = counts[ctd::kCntTerminated];
+    s.aborted = counts[ctd::kCntAborted];
+    s.steps = counts[ctd::kCntSteps];
+    s.e_emitted_kev = energies[0];
+    s.e_escaped_kev = energies[1];
+    s.histories = P->shard_n;
+    s.n_batches = P->shard_nb;
+    P->have_result = true;
+    P->shard_nb = 0;
     return CTD_OK;
 }
 

@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <array>
 #include <cstring>
+#include <chrono>
 #include <functional>
+#include <thread>
 
 #include "ctd_host.h"
 
@@ -223,17 +225,50 @@ namespace {
 
 double elapsed_since(double t) { return now_s() - t; }
 
-// Admit queued requests in order while memory and slots allow.
-int admit(ctd_ctx *ctx)
+// Lanes, their events and pinned result slots for served request chains, made
+// once per context.
+int ensure_serve_lanes(ctd_ctx *ctx)
+{
+    int rc;
+    if ((rc = ensure_lanes(ctx, kMaxLanes))) return rc;
+    if (ctx->lane_owner.empty()) ctx->lane_owner.assign(kMaxLanes, 0);
+    while (ctx->serve_ev.size() < static_cast<size_t>(kMaxLanes)) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->serve_ev.push_back(e);
+    }
+    if (!ctx->serve_res) {
+        if (cudaMallocHost(reinterpret_cast<void **>(&ctx->serve_res), kMaxLanes * 4 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->serve_res = nullptr;
+            return fail(CTD_ENOMEM, "cudaMallocHost failed");
+        }
+    }
+    return ctx->serve_work.ensure(kMaxLanes);
+}
+
+int free_lane(ctd_ctx *ctx)
+{
+    for (int i = 0; i < static_cast<int>(ctx->lane_owner.size()); ++i)
+        if (ctx->lane_owner[i] == 0) return i;
+    return -1;
+}
+
+// Admit queued requests in order while memory and slots allow.  Request chains
+// (chains = true) also need a free lane; a request's buffers are cleared on the
+// stream it will run on.
+int admit(ctd_ctx *ctx, bool chains)
 {
     double round = 0.0;
     for (int64_t id : ctx->active) round += static_cast<double>(ctx->sreqs[id].req.batch_histories);
     while (!ctx->pending.empty() && static_cast<int>(ctx->active.size()) < ctx->max_active) {
         ServeReq &R = ctx->sreqs[ctx->pending.front()];
-        // first in, first out: a request joins the running set only while one round of
+        // first in, first out: a request joins the running set only while one batch of
         // every running request stays within the round budget (one request always may)
         const double b = static_cast<double>(R.req.batch_histories);
         if (!ctx->active.empty() && round + b > ctx->round_histories) break;
+        const int lane_i = chains ? free_lane(ctx) : -1;
+        if (chains && lane_i < 0) break;
         Phantom *P = find(ctx, R.ph);
         if (!P) {
             R.state = CTD_REQ_FAILED;
@@ -252,15 +287,20 @@ int admit(ctd_ctx *ctx)
             ctx->pending.erase(ctx->pending.begin());
             continue;
         }
+        const cudaStream_t s = chains ? ctx->lanes[lane_i] : ctx->stream;
         const size_t nv = P->nvox;
-        CK(cudaMemsetAsync(P->tally.p, 0, nv * sizeof(double), ctx->stream));
-        CK(cudaMemsetAsync(P->sum_d.p, 0, nv * sizeof(double), ctx->stream));
-        CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), ctx->stream));
-        CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
-        CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), ctx->stream));
+        CK(cudaMemsetAsync(P->tally.p, 0, nv * sizeof(double), s));
+        CK(cudaMemsetAsync(P->sum_d.p, 0, nv * sizeof(double), s));
+        CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), s));
+        CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), s));
+        CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), s));
         P->have_result = false;
         R.state = CTD_REQ_RUNNING;
         R.t_start = now_s();
+        if (chains) {
+            R.lane = lane_i;
+            ctx->lane_owner[lane_i] = R.id;
+        }
         round += b;
         ctx->active.push_back(R.id);
         ctx->pending.erase(ctx->pending.begin());
@@ -272,13 +312,277 @@ void retire(ctd_ctx *ctx, ServeReq &R, int state)
 {
     R.state = state;
     R.t_done = now_s();
+    R.in_flight = false;
     Phantom *P = find(ctx, R.ph);
     if (P) P->busy_req = 0;
+    if (R.lane >= 0) {
+        ctx->lane_owner[R.lane] = 0;
+        R.lane = -1;
+    }
     for (size_t i = 0; i < ctx->active.size(); ++i)
         if (ctx->active[i] == R.id) {
             ctx->active.erase(ctx->active.begin() + i);
             break;
         }
+}
+
+// The next batch of a running request on its own lane: transport, fold and, from
+// min_batches on, the statistics of the stop test with their copy to the lane's
+// pinned slot; the lane's event marks its end.
+int launch_batch(ctd_ctx *ctx, ServeReq &R, Phantom &P)
+{
+    const cudaStream_t s = ctx->lanes[R.lane];
+    const uint64_t B = R.req.batch_histories;
+    ctd::RequestDesc q;
+    fill_request(P, R.req.seed, q);
+    q.work = ctx->serve_work.p + R.lane;
+    q.pref = P.pref.p + 1 * (q.nbins + 1);    // batches of exactly B histories
+    q.h_base = static_cast<uint64_t>(R.batches) * B;
+    q.local_begin = 0;
+    q.local_end = B;
+    q.tally = P.tally.p;
+    CK(cudaMemsetAsync(q.work, 0, sizeof(unsigned long long), s));
+    CKS(launch_one(ctx, P, q, s));
+    const double scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
+    CKS(ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, scale, s));
+    R.checked = R.batches + 1 >= R.req.min_batches;
+    if (R.checked) {
+        CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, R.batches + 1, P.dose.p, P.sd.p, P.nvox, s));
+        CKS(ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, s));
+        CK(cudaMemcpyAsync(ctx->serve_res + 4 * R.lane, P.result.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaEventRecord(ctx->serve_ev[R.lane], s));
+    R.in_flight = true;
+    return CTD_OK;
+}
+
+// A request that reached its target or its history cap: total deposit, results
+// read back on its lane, then retired.
+int finish_request(ctd_ctx *ctx, ServeReq &R, Phantom &P)
+{
+    const cudaStream_t s = ctx->lanes[R.lane];
+    CKS(ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, s));
+    Phantom *ps[1] = {&P};
+    const double t0[1] = {R.t_start};
+    int rc;
+    if ((rc = collect_many(ctx, ps, 1, 0, 0.0, t0, s))) return rc;
+    P.stats.histories = R.histories;
+    P.stats.n_batches = R.batches;
+    P.have_result = true;
+    retire(ctx, R, CTD_REQ_DONE);
+    return CTD_OK;
+}
+
+bool reached_stop(const ServeReq &R)
+{
+    const bool hit = R.req.rsd_target > 0.0 && R.avg_rsd > 0.0 && R.avg_rsd <= R.req.rsd_target;
+    const bool cap = R.req.n_histories_max && R.histories >= R.req.n_histories_max;
+    return hit || cap;
+}
+
+// Request chains (shared_launch = 0): every running request advances on its own
+// lane independently of the others.  One call takes in the batches that have
+// finished, retires cancelled and finished requests, admits queued ones and
+// launches the next batch of every request with nothing on the GPU; it does not
+// wait for the GPU, except for the batch in flight of a cancelled request.
+// *progress: whether anything was taken in, retired, admitted or launched.
+int serve_chains(ctd_ctx *ctx, bool *progress)
+{
+    int rc;
+    if ((rc = ensure_serve_lanes(ctx))) return rc;
+    bool moved = false;
+    const std::vector<int64_t> act = ctx->active;
+    for (int64_t id : act) {
+        ServeReq &R = ctx->sreqs[id];
+        if (!R.in_flight) continue;
+        const cudaError_t q = R.cancel ? cudaEventSynchronize(ctx->serve_ev[R.lane])
+                                       : cudaEventQuery(ctx->serve_ev[R.lane]);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) {
+            retire(ctx, R, CTD_REQ_FAILED);
+            return fail(CTD_ECUDA, "served request %lld: %s", static_cast<long long>(id), cudaGetErrorString(q));
+        }
+        moved = true;
+        // the batch is done: only now does it count
+        R.in_flight = false;
+        R.batches += 1;
+        R.histories += R.req.batch_histories;
+        if (R.checked) {
+            R.avg_rsd = ctx->serve_res[4 * R.lane];
+            R.sigma_bar = ctx->serve_res[4 * R.lane + 1];
+        }
+        if (!R.cancel && R.checked && reached_stop(R)) {
+            Phantom *P = find(ctx, R.ph);
+            if (!P) {
+                retire(ctx, R, CTD_REQ_FAILED);
+                continue;
+            }
+            if ((rc = finish_request(ctx, R, *P))) {
+                retire(ctx, R, CTD_REQ_FAILED);
+                return rc;
+            }
+        }
+    }
+    // cancellations take effect once nothing of the request is on the GPU
+    for (size_t i = 0; i < ctx->active.size();) {
+        ServeReq &R = ctx->sreqs[ctx->active[i]];
+        if (R.cancel && !R.in_flight) {
+            retire(ctx, R, CTD_REQ_CANCELLED);
+            moved = true;
+        } else {
+            ++i;
+        }
+    }
+    const size_t before = ctx->active.size();
+    if ((rc = admit(ctx, true))) return rc;
+    moved = moved || ctx->active.size() != before;
+    for (int64_t id : std::vector<int64_t>(ctx->active)) {
+        ServeReq &R = ctx->sreqs[id];
+        if (R.in_flight) continue;
+        Phantom *P = find(ctx, R.ph);
+        if (!P || (rc = launch_batch(ctx, R, *P))) {
+            retire(ctx, R, CTD_REQ_FAILED);
+            if (!P) continue;
+            return rc;
+        }
+        moved = true;
+    }
+    *progress = moved;
+    return CTD_OK;
+}
+
+// Shared launches (shared_launch = 1): one round, one batch of every running
+// request in one multi-request launch, waited for.
+int serve_round(ctd_ctx *ctx)
+{
+    int rc;
+    for (size_t i = 0; i < ctx->active.size();) {
+        ServeReq &R = ctx->sreqs[ctx->active[i]];
+        if (R.cancel) retire(ctx, R, CTD_REQ_CANCELLED);
+        else ++i;
+    }
+    if ((rc = admit(ctx, false))) return rc;
+    const int n = static_cast<int>(ctx->active.size());
+    if (n == 0) return CTD_OK;
+    std::vector<Phantom *> ps(n);
+    for (int i = 0; i < n; ++i) ps[i] = find(ctx, ctx->sreqs[ctx->active[i]].ph);
+    for (int i = 1; i < n; ++i) {
+        const ctd_physics &a = ps[0]->phys, &b = ps[i]->phys;
+        if (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta) {
+            retire(ctx, ctx->sreqs[ctx->active[i]], CTD_REQ_FAILED);
+            return fail(CTD_EINVAL, "served requests must share one node grid");
+        }
+    }
+    int max_n_mat = 0;
+    for (int i = 0; i < n; ++i) max_n_mat = std::max(max_n_mat, static_cast<int>(ps[i]->mats.size()));
+    if ((rc = ctx->u_work.ensure(n))) return rc;
+    std::vector<ctd::RequestDesc> descs(n);
+    std::vector<uint64_t> tiles(n + 1, 0);
+    std::vector<ctd::FoldDesc> folds(n);
+    std::vector<int> checked;
+    for (int i = 0; i < n; ++i) {
+        ServeReq &R = ctx->sreqs[ctx->active[i]];
+        Phantom &P = *ps[i];
+        const uint64_t B = R.req.batch_histories;
+        ctd::RequestDesc &q = descs[i];
+        fill_request(P, R.req.seed, q);
+        q.work = ctx->u_work.p + i;
+        q.pref = P.pref.p + 1 * (q.nbins + 1);    // batches of exactly B histories
+        q.h_base = static_cast<uint64_t>(R.batches) * B;
+        q.local_begin = 0;
+        q.local_end = B;
+        q.tally = P.tally.p;
+        tiles[i + 1] = tiles[i] + (P.nvox + ctd::kFoldTile - 1) / ctd::kFoldTile;
+        ctd::FoldDesc &f = folds[i];
+        f.tally = P.tally.p;
+        f.rho = P.rho.p;
+        f.sum_d = P.sum_d.p;
+        f.sum_d2 = P.sum_d2.p;
+        f.edep = P.edep.p;
+        f.nvox = P.nvox;
+        f.scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
+        // those past min_batches after this round also get their statistics
+        if (R.batches + 1 >= R.req.min_batches) checked.push_back(i);
+    }
+    // a round whose launches fail counts for no request: their batches stay as they were
+    auto failed = [&](int code) {
+        for (int64_t id : std::vector<int64_t>(ctx->active)) retire(ctx, ctx->sreqs[id], CTD_REQ_FAILED);
+        return code;
+    };
+    if ((rc = ctx->u_reqs.ensure(n)) || (rc = ctx->u_folds.ensure(n)) || (rc = ctx->u_tiles.ensure(n + 1)))
+        return failed(rc);
+    if (cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), n * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->u_folds.p, folds.data(), n * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->u_work.p, 0, n * sizeof(unsigned long long), ctx->stream) != cudaSuccess)
+        return failed(fail(CTD_ECUDA, "served round: copying the request table failed"));
+    ctd::LaunchParams L;
+    std::memset(&L, 0, sizeof(L));
+    fill_shared(*ps[0], L.sh);
+    L.sh.max_n_mat = max_n_mat;
+    L.reqs = ctx->u_reqs.p;
+    L.n_req = n;
+    L.chunk = ctx->chunk;
+    L.flight_cap = ctx->flight_cap;
+    const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
+    if ((rc = ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, ctx->stream)) ||
+        (rc = ctd::launch_fold_multi(ctx->u_folds.p, ctx->u_tiles.p, n, tiles[n], ctx->stream)))
+        return failed(rc);
+    for (int i : checked) {
+        Phantom &P = *ps[i];
+        const int nb = ctx->sreqs[ctx->active[i]].batches + 1;
+        if ((rc = ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, nb, P.dose.p, P.sd.p, P.nvox, ctx->stream)) ||
+            (rc = ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p,
+                                  ctx->stream)))
+            return failed(rc);
+    }
+    std::vector<std::array<double, 3>> res(checked.size());
+    for (size_t c = 0; c < checked.size(); ++c)
+        if (cudaMemcpyAsync(res[c].data(), ps[checked[c]]->result.p, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream) != cudaSuccess)
+            return failed(fail(CTD_ECUDA, "served round: reading the statistics failed"));
+    const cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    if (se != cudaSuccess) return failed(fail(CTD_ECUDA, "served round: %s", cudaGetErrorString(se)));
+    // the round is done: now its batch counts for every running request
+    for (int i = 0; i < n; ++i) {
+        ServeReq &R = ctx->sreqs[ctx->active[i]];
+        R.batches += 1;
+        R.histories += R.req.batch_histories;
+    }
+    std::vector<int64_t> finished;
+    for (size_t c = 0; c < checked.size(); ++c) {
+        ServeReq &R = ctx->sreqs[ctx->active[checked[c]]];
+        R.avg_rsd = res[c][0];
+        R.sigma_bar = res[c][1];
+        if (reached_stop(R)) finished.push_back(R.id);
+    }
+    std::vector<Phantom *> fp;
+    std::vector<double> ft;
+    for (int64_t id : finished) {
+        ServeReq &R = ctx->sreqs[id];
+        Phantom &P = *find(ctx, R.ph);
+        CKS(ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, ctx->stream));
+        fp.push_back(&P);
+        ft.push_back(R.t_start);
+    }
+    if (!fp.empty() && (rc = collect_many(ctx, fp.data(), static_cast<int>(fp.size()), 0, 0.0, ft.data()))) return rc;
+    for (size_t i = 0; i < finished.size(); ++i) {
+        ServeReq &R = ctx->sreqs[finished[i]];
+        fp[i]->stats.histories = R.histories;
+        fp[i]->stats.n_batches = R.batches;
+        fp[i]->have_result = true;
+        retire(ctx, R, CTD_REQ_DONE);
+    }
+    return CTD_OK;
+}
+
+int serve_pump(ctd_ctx *ctx, bool *progress)
+{
+    *progress = true;
+    return ctx->shared_launch ? serve_round(ctx) : serve_chains(ctx, progress);
 }
 
 }  // namespace
@@ -315,145 +619,10 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
 {
     int rc;
     if ((rc = use_device(ctx))) return rc;
-    // cancellations take effect at round boundaries
-    for (size_t i = 0; i < ctx->active.size();) {
-        ServeReq &R = ctx->sreqs[ctx->active[i]];
-        if (R.cancel) retire(ctx, R, CTD_REQ_CANCELLED);
-        else ++i;
-    }
-    if ((rc = admit(ctx))) return rc;
-    const int n = static_cast<int>(ctx->active.size());
-    if (n == 0) {
-        if (n_active) *n_active = static_cast<int>(ctx->pending.size());
-        return CTD_OK;
-    }
-    std::vector<Phantom *> ps(n);
-    for (int i = 0; i < n; ++i) ps[i] = find(ctx, ctx->sreqs[ctx->active[i]].ph);
-    for (int i = 1; i < n && ctx->shared_launch; ++i) {
-        const ctd_physics &a = ps[0]->phys, &b = ps[i]->phys;
-        if (a.e_min_kev != b.e_min_kev || a.e_max_kev != b.e_max_kev || a.n_zeta != b.n_zeta) {
-            retire(ctx, ctx->sreqs[ctx->active[i]], CTD_REQ_FAILED);
-            return fail(CTD_EINVAL, "served requests must share one node grid");
-        }
-    }
-    int max_n_mat = 0;
-    for (int i = 0; i < n; ++i) max_n_mat = std::max(max_n_mat, static_cast<int>(ps[i]->mats.size()));
-    int rc2;
-    if ((rc2 = ctx->u_work.ensure(n))) return rc2;
-    std::vector<ctd::RequestDesc> descs(n);
-    std::vector<uint64_t> tiles(n + 1, 0);
-    std::vector<ctd::FoldDesc> folds(n);
-    for (int i = 0; i < n; ++i) {
-        ServeReq &R = ctx->sreqs[ctx->active[i]];
-        Phantom &P = *ps[i];
-        const uint64_t B = R.req.batch_histories;
-        ctd::RequestDesc &q = descs[i];
-        fill_request(P, R.req.seed, q);
-        q.work = ctx->u_work.p + i;
-        q.pref = P.pref.p + 1 * (q.nbins + 1);    // batches of exactly B histories
-        q.h_base = static_cast<uint64_t>(R.batches) * B;
-        q.local_begin = 0;
-        q.local_end = B;
-        q.tally = P.tally.p;
-        tiles[i + 1] = tiles[i] + (P.nvox + ctd::kFoldTile - 1) / ctd::kFoldTile;
-        ctd::FoldDesc &f = folds[i];
-        f.tally = P.tally.p;
-        f.rho = P.rho.p;
-        f.sum_d = P.sum_d.p;
-        f.sum_d2 = P.sum_d2.p;
-        f.edep = P.edep.p;
-        f.nvox = P.nvox;
-        f.scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
-    }
-    // one batch of every running request; those past min_batches also get their
-    // statistics for the stopping test
-    std::vector<int> checked;
-    for (int i = 0; i < n; ++i) {
-        ServeReq &R = ctx->sreqs[ctx->active[i]];
-        R.batches += 1;
-        R.histories += R.req.batch_histories;
-        if (R.batches >= R.req.min_batches) checked.push_back(i);
-    }
-    auto stats = [&](int i, cudaStream_t s) {
-        Phantom &P = *ps[i];
-        const int nb = ctx->sreqs[ctx->active[i]].batches;
-        int e = ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, nb, P.dose.p, P.sd.p, P.nvox, s);
-        if (e == CTD_OK) e = ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, s);
-        return e;
-    };
-    if (!ctx->shared_launch) {
-        // each request on its own stream: transport, fold, statistics
-        if ((rc = ensure_lanes(ctx, n))) return rc;
-        CK(cudaMemsetAsync(ctx->u_work.p, 0, n * sizeof(unsigned long long), ctx->stream));
-        if ((rc = fork_lanes(ctx, ctx->stream, n))) return rc;
-        size_t c = 0;
-        for (int i = 0; i < n; ++i) {
-            Phantom &P = *ps[i];
-            const cudaStream_t s = lane(ctx, i);
-            CKS(launch_one(ctx, P, descs[i], s));
-            CKS(ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, folds[i].scale, s));
-            if (c < checked.size() && checked[c] == i) {
-                CKS(stats(i, s));
-                ++c;
-            }
-        }
-        if ((rc = join_lanes(ctx, ctx->stream, n))) return rc;
-    } else {
-        if ((rc = ctx->u_reqs.ensure(n)) || (rc = ctx->u_folds.ensure(n)) || (rc = ctx->u_tiles.ensure(n + 1)))
-            return rc;
-        CK(cudaMemcpyAsync(ctx->u_reqs.p, descs.data(), n * sizeof(ctd::RequestDesc), cudaMemcpyHostToDevice,
-                           ctx->stream));
-        CK(cudaMemcpyAsync(ctx->u_folds.p, folds.data(), n * sizeof(ctd::FoldDesc), cudaMemcpyHostToDevice,
-                           ctx->stream));
-        CK(cudaMemcpyAsync(ctx->u_tiles.p, tiles.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
-                           ctx->stream));
-        CK(cudaMemsetAsync(ctx->u_work.p, 0, n * sizeof(unsigned long long), ctx->stream));
-        ctd::LaunchParams L;
-        std::memset(&L, 0, sizeof(L));
-        fill_shared(*ps[0], L.sh);
-        L.sh.max_n_mat = max_n_mat;
-        L.reqs = ctx->u_reqs.p;
-        L.n_req = n;
-        L.chunk = ctx->chunk;
-        L.flight_cap = ctx->flight_cap;
-        const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;
-        CKS(ctd::launch_transport(L, mgrid, ctx->threads, ctx->threads * ctx->multi_blocks_per_sm, ctx->stream));
-        CKS(ctd::launch_fold_multi(ctx->u_folds.p, ctx->u_tiles.p, n, tiles[n], ctx->stream));
-        for (int i : checked) CKS(stats(i, ctx->stream));
-    }
-    std::vector<std::array<double, 3>> res(checked.size());
-    for (size_t c = 0; c < checked.size(); ++c)
-        CK(cudaMemcpyAsync(res[c].data(), ps[checked[c]]->result.p, 3 * sizeof(double), cudaMemcpyDeviceToHost,
-                           ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    std::vector<int64_t> finished;
-    for (size_t c = 0; c < checked.size(); ++c) {
-        ServeReq &R = ctx->sreqs[ctx->active[checked[c]]];
-        R.avg_rsd = res[c][0];
-        R.sigma_bar = res[c][1];
-        const bool hit = R.req.rsd_target > 0.0 && R.avg_rsd > 0.0 && R.avg_rsd <= R.req.rsd_target;
-        const bool cap = R.req.n_histories_max && R.histories >= R.req.n_histories_max;
-        if (hit || cap) finished.push_back(R.id);
-    }
-    std::vector<Phantom *> fp;
-    std::vector<double> ft;
-    for (int64_t id : finished) {
-        ServeReq &R = ctx->sreqs[id];
-        Phantom &P = *find(ctx, R.ph);
-        CKS(ctd::launch_sum(P.edep.p, P.nvox, P.partials.p + 5 * kRsdParts, kRsdParts, P.result.p + 3, ctx->stream));
-        fp.push_back(&P);
-        ft.push_back(R.t_start);
-    }
-    if (!fp.empty() && (rc = collect_many(ctx, fp.data(), static_cast<int>(fp.size()), 0, 0.0, ft.data()))) return rc;
-    for (size_t i = 0; i < finished.size(); ++i) {
-        ServeReq &R = ctx->sreqs[finished[i]];
-        fp[i]->stats.histories = R.histories;
-        fp[i]->stats.n_batches = R.batches;
-        fp[i]->have_result = true;
-        retire(ctx, R, CTD_REQ_DONE);
-    }
+    bool progress;
+    rc = serve_pump(ctx, &progress);
     if (n_active) *n_active = static_cast<int>(ctx->active.size() + ctx->pending.size());
-    return CTD_OK;
+    return rc;
 }
 
 int ctd_poll(ctd_ctx *ctx, ctd_req_id id, ctd_req_status *out)
@@ -490,10 +659,13 @@ int ctd_wait(ctd_ctx *ctx, ctd_req_id id, double timeout_s, ctd_req_status *out)
             return fail(CTD_ETIMEOUT, "request %lld not finished after %.3f s", static_cast<long long>(id), timeout_s);
         }
         const size_t before = ctx->active.size();
-        if ((rc = ctd_serve_step(ctx, nullptr))) return rc;
+        bool progress = false;
+        if ((rc = use_device(ctx)) || (rc = serve_pump(ctx, &progress))) return rc;
         if (before == 0 && ctx->active.empty() && ctx->sreqs[id].state == CTD_REQ_QUEUED)
             return fail(CTD_ENOMEM, "request %lld cannot be admitted: not enough free device memory",
                         static_cast<long long>(id));
+        // every batch is on the GPU: look again shortly instead of spinning
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     const ServeReq &R = ctx->sreqs[id];
     if (out) ctd_poll(ctx, id, out);

@@ -102,6 +102,10 @@ struct Phantom {
     std::vector<int32_t> h_alias;
     DevBuf<uint32_t> fl_thr;
     DevBuf<int32_t> fl_alias;
+    // a sharded run in progress (ctd_shard_*): its history count, batches and seed
+    uint64_t shard_n = 0, shard_seed = 0;
+    int shard_nb = 0;
+    double shard_t0 = 0.0;
 };
 
 struct Staged {
@@ -119,6 +123,10 @@ struct ServeReq {
     double avg_rsd = 0.0, sigma_bar = 0.0;
     double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
     bool cancel = false;
+    // request chains (shared_launch = 0): the stream slot the request runs on, and
+    // whether a batch of it is on the GPU (with its statistics for the stop test)
+    int lane = -1;
+    bool in_flight = false, checked = false;
 };
 
 constexpr int kRsdParts = 1024;   // partial sums of the statistics reductions
@@ -172,6 +180,13 @@ struct ctd_ctx {
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> lane_done;
     cudaEvent_t fork_event = nullptr;
+    // served request chains: the request holding each lane (0: free), an event per lane
+    // marking the end of its batch in flight, and pinned slots [lane][4] the batch's
+    // avg RSD, sigma_bar and D_max come back to
+    std::vector<int64_t> lane_owner;
+    std::vector<cudaEvent_t> serve_ev;
+    double *serve_res = nullptr;
+    ctd::host::DevBuf<unsigned long long> serve_work;   // claim counter per lane
 };
 
 namespace ctd {
@@ -216,7 +231,7 @@ double now_s();
 int transport_time(ctd_ctx *ctx, size_t n_launch, double &t);
 // counts and results of several phantoms read back through pinned staging
 int collect_many(ctd_ctx *ctx, Phantom *const *ps, int n, size_t n_launch, double t0_wall,
-                 const double *t0_each = nullptr);
+                 const double *t0_each = nullptr, cudaStream_t stream = nullptr);
 int collect(ctd_ctx *ctx, Phantom &P, size_t n_launch, double t0_wall);
 
 }  // namespace host

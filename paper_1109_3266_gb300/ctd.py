@@ -112,6 +112,11 @@ def lib():
         L.ctd_run.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int]
         L.ctd_run_range.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]
         L.ctd_trace_range.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, P]
+        L.ctd_shard_begin.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int]
+        L.ctd_shard_batch.argtypes = [P, C.c_int32, C.c_int, C.c_uint64, C.c_uint64, P]
+        L.ctd_shard_fold.argtypes = [P, C.c_int32, C.c_int, P]
+        L.ctd_shard_counts.argtypes = [P, C.c_int32, C.POINTER(C.c_uint64), dp]
+        L.ctd_shard_finish.argtypes = [P, C.c_int32, C.POINTER(C.c_uint64), dp]
         L.ctd_get_dose_and_stddev.argtypes = [P, C.c_int32, dp, dp, C.c_size_t, C.POINTER(ctd_run_stats)]
         L.ctd_get_edep.argtypes = [P, C.c_int32, dp, C.c_size_t]
         L.ctd_get_tables.argtypes = [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -277,6 +282,35 @@ def ctd_autotune(ctx, ph, n_probe, seed=1):
 def ctd_run_range(ctx, ph, n_histories, seed, n_batches, h_begin, h_end, clear=True):
     _check(lib().ctd_run_range(ctx, ph, int(n_histories), int(seed), int(n_batches), int(h_begin), int(h_end),
                                int(bool(clear))))
+
+
+def ctd_shard_begin(ctx, ph, n_histories, seed, n_batches):
+    _check(lib().ctd_shard_begin(ctx, ph, int(n_histories), int(seed), int(n_batches)))
+
+
+def ctd_shard_batch(ctx, ph, batch, local_begin, local_end, tally_dev):
+    """Add local histories [local_begin, local_end) of `batch` to the device buffer at
+    address tally_dev (nvox doubles, e.g. a torch tensor's data_ptr())."""
+    _check(lib().ctd_shard_batch(ctx, ph, int(batch), int(local_begin), int(local_end), int(tally_dev)))
+
+
+def ctd_shard_fold(ctx, ph, batch, tally_dev):
+    """Fold the summed batch tally at device address tally_dev; leaves it zeroed."""
+    _check(lib().ctd_shard_fold(ctx, ph, int(batch), int(tally_dev)))
+
+
+def ctd_shard_counts(ctx, ph):
+    """This rank's counts (10 uint64) and emitted/escaped energies (2 doubles)."""
+    c = np.zeros(10, dtype=np.uint64)
+    e = np.zeros(2, dtype=np.float64)
+    _check(lib().ctd_shard_counts(ctx, ph, c.ctypes.data_as(C.POINTER(C.c_uint64)), _dp(e)))
+    return c, e
+
+
+def ctd_shard_finish(ctx, ph, counts, energies):
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    _check(lib().ctd_shard_finish(ctx, ph, c.ctypes.data_as(C.POINTER(C.c_uint64)), _dp(e)))
 
 
 # ctd_track records as numpy sees them

@@ -1,12 +1,15 @@
 """Request loop of the served form (continuous batching).
 
 Requests arrive at given times; at each turn of the loop the requests that
-have arrived are created on the device and submitted, one round of the
-library's scheduler runs (admission by free device memory, one batch of every
-running request in one shared launch, statistics, retirement at the target avg
-RSD), and finished requests are read back and their phantoms released.  The
-scheduling and every step of the transport run in the CUDA library; this
-module only drives it and keeps the clock.
+have arrived are created on the device and submitted, and the library's
+scheduler is stepped once: it takes in the batches that have finished on the
+GPU, retires requests at their target avg RSD, admits queued requests by free
+device memory and launches the next batch of every running request, each on
+its own stream (with the context's shared_launch option, one round of every
+running request in one shared launch instead).  Finished requests are read
+back and their phantoms released.  The scheduling and every step of the
+transport run in the CUDA library; this module only drives it and keeps the
+clock.
 """
 from __future__ import annotations
 
@@ -68,6 +71,7 @@ def serve(ctx, arrivals, make_problem, batch_histories, rsd_target, min_batches=
             continue
         ctd.ctd_serve_step(ctx)
         t_now = time.perf_counter() - t0
+        n_before = len(running)
         for rid in list(running):
             st = ctd.ctd_poll(ctx, rid)
             if st["state"] >= ctd.REQ_DONE:
@@ -81,6 +85,11 @@ def serve(ctx, arrivals, make_problem, batch_histories, rsd_target, min_batches=
                 if keep_results:
                     r.stats = ctd.ctd_get_dose_and_stddev(ctx, r.handle, 0, want_arrays=False)[2]
                 ctd.ctd_destroy_phantom(ctx, r.handle)
+        if len(running) == n_before:
+            # nothing finished: the GPU is busy with every running request's batch
+            wait = 2e-4 if nxt >= len(reqs) else min(2e-4, max(0.0, reqs[nxt].t_arrival - t_now))
+            if wait > 0:
+                time.sleep(wait)
     return reqs, time.perf_counter() - t0
 
 

@@ -155,6 +155,30 @@ def test_served_cancel_timeout_and_queue(ctd, ctx):
         ctd.ctd_poll(ctx, 10 ** 9)
 
 
+def test_served_requests_join_while_others_are_on_the_gpu(ctd):
+    # continuous batching: a request submitted while another's batch is on the GPU is
+    # admitted and its first batch launched at the next step, without waiting for that
+    # batch; the short request finishes while the long one is still running
+    c = ctd.ctd_create(device=0, serve_round_histories=1e12)
+    pa, pb = problems()[0], problems()[3]
+    ha, hb = ctd.load_problem(c, pa), ctd.load_problem(c, pb)
+    a = ctd.ctd_submit(c, ha, 200_000_000, 1e-9, 5, n_histories_max=10 ** 11)
+    ctd.ctd_serve_step(c)                                      # a's first batch goes to the GPU
+    b = ctd.ctd_submit(c, hb, 5_000, 0.5, 6, n_histories_max=200_000)
+    ctd.ctd_serve_step(c)
+    sa, sb = ctd.ctd_poll(c, a), ctd.ctd_poll(c, b)
+    assert sb["state"] == ctd.REQ_RUNNING and sa["batches"] == 0, (sa, sb)
+    assert ctd.ctd_wait(c, b, 120.0)["state"] == ctd.REQ_DONE
+    assert ctd.ctd_poll(c, a)["state"] == ctd.REQ_RUNNING
+    ctd.ctd_cancel(c, a)
+    ctd.ctd_serve_step(c)
+    assert ctd.ctd_poll(c, a)["state"] == ctd.REQ_CANCELLED
+    # b's result is the plain run of its batches
+    st = ctd.ctd_poll(c, b)
+    same(alone(ctd, c, pb, n=st["batches"] * 5_000, nb=st["batches"]), ctd.ctd_get_dose_and_stddev(c, hb, pb.phantom.nvox))
+    ctd.ctd_destroy(c)
+
+
 def test_serve_loop_reports_latency(ctd, ctx):
     from paper_1109_3266_gb300 import serve
 

@@ -55,10 +55,13 @@ FLUSH_BYTES = 256 * 1024 * 1024
 # (smsp__thread_inst_executed / histories) and DRAM bytes per launch
 # (dram__bytes_read + dram__bytes_write); they are not measured in this run.
 KERNEL_PROFILE = {
-    "cbct_water": {"lane_inst_per_history": None, "dram_bytes_per_launch": None, "histories_per_launch": 1e8,
-                   "capture": None},
-    "head": {"lane_inst_per_history": None, "dram_bytes_per_launch": None, "histories_per_launch": 2e8,
-             "capture": None},
+    "cbct_water": {"lane_inst_per_history": 2088.0, "dram_bytes_per_launch": 9.16e9, "histories_per_launch": 1e8,
+                   "capture": "ncu --set full --clock-control none of one transport_kernel<256,4,0,0> launch of 1e8 "
+                              "CBCT-water histories (fast-math kernel): 8.69e9 warp instructions x 24.03 lanes; "
+                              "DRAM 5.63 + 3.54 GB"},
+    "head": {"lane_inst_per_history": 2440.0, "dram_bytes_per_launch": 14.71e9, "histories_per_launch": 2e8,
+             "capture": "ncu --set full --clock-control none of one transport_kernel<256,4,0,0> launch of 2e8 head "
+                        "histories (fast-math kernel): 2.646e10 warp instructions x 18.44 lanes; DRAM 9.54 + 5.17 GB"},
 }
 
 
@@ -369,12 +372,15 @@ def error_vs_oracle(ctd, ctx, h, p, ranges, o_edep, o_counts):
     ed = ctd.ctd_get_edep(ctx, h, p.phantom.nvox)
     m = o_edep > 0.1 * o_edep.max()
     rel = np.abs(ed[m] - o_edep[m]) / o_edep[m]
-    counts = {k: (st[k] - o_counts[k]) / max(o_counts[k], 1) for k in ("pe", "compton", "rayleigh", "fictitious",
-                                                                         "escaped", "missed")}
+    counts = {k: {"device": int(st[k]), "oracle": int(o_counts[k]),
+                  "rel": (st[k] - o_counts[k]) / max(o_counts[k], 1)}
+              for k in ("pe", "compton", "rayleigh", "fictitious", "escaped", "missed")}
     return {"histories": int(sum(b - a for a, b in ranges)), "sample": "the CPU baseline's sample, same histories",
             "total_edep_rel": float((st["e_deposited_kev"] - o_counts["e_deposited"]) / o_counts["e_deposited"]),
             "voxel_edep_rel_median": float(np.median(rel)), "voxel_edep_rel_p99": float(np.percentile(rel, 99)),
-            "voxel_edep_rel_max": float(rel.max()), "voxels": int(m.sum()), "count_rel": counts}
+            "voxel_edep_rel_max": float(rel.max()), "voxels": int(m.sum()), "counts": counts,
+            "note": "the same histories on both sides: the differences are binary32 against binary64 rounding, "
+                    "and a voxel's largest difference is one history that took another path"}
 
 
 def e2e_rate(ctd, ctx, p, seed, steps, world, dev):
@@ -486,21 +492,30 @@ def leg_batched(ctd, args, clk):
 
     timed(batched, 1)
     timed(lambda: batched(1), 1)
+    # the batched form's autotuner on a 5 % probe of the same requests, in a third context
+    ctxs.append(ctd.ctd_create(device=0, stream=stream.cuda_stream))
+    hss.append([ctd.load_problem(ctxs[2], p) for p in reqs])
+    t0 = time.perf_counter()
+    tune = ctd.ctd_autotune_batch(ctxs[2], hss[2], [p.n_hist for p in reqs], [p.seed for p in reqs], nb, 0.05)
+    tune["seconds"] = time.perf_counter() - t0
+    timed(lambda: batched(2), 1)
     a = clk.mark()
     tb = timed(batched, args.batched_reps)
     ts = timed(lambda: batched(1), args.batched_reps)
+    tt = timed(lambda: batched(2), args.batched_reps)
     tp = timed(plain, args.batched_reps)
     b = clk.mark()
     rsd = [ctd.ctd_get_dose_and_stddev(ctx, h, 0, want_arrays=False)[2]["avg_rsd"] for h in hs]
-    vb, vs, vp = (n_total / float(np.mean(t)) for t in (tb, ts, tp))
+    vb, vs, vt, vp = (n_total / float(np.mean(t)) for t in (tb, ts, tt, tp))
     for c, hl in zip(ctxs, hss):
         for h in hl:
             ctd.ctd_destroy_phantom(c, h)
         ctd.ctd_destroy(c)
     return {"workload": "batched", "requests": len(reqs), "histories_per_step": n_total, "batches": nb,
             "sides": sorted({p.meta["side"] for p in reqs}), "hist_range": [args.hist_lo, args.hist_hi],
-            "reps": args.batched_reps, "chains_value": vb, "shared_launch_value": vs, "plain_value": vp,
-            "unit": UNIT, "chains_speedup_vs_plain": vb / vp, "shared_launch_speedup_vs_plain": vs / vp,
+            "reps": args.batched_reps, "chains_value": vb, "shared_launch_value": vs, "autotuned_value": vt,
+            "plain_value": vp, "unit": UNIT, "chains_speedup_vs_plain": vb / vp,
+            "shared_launch_speedup_vs_plain": vs / vp, "autotuned_speedup_vs_plain": vt / vp, "autotuner": tune,
             "chains_ms": 1e3 * float(np.mean(tb)), "shared_launch_ms": 1e3 * float(np.mean(ts)),
             "plain_ms": 1e3 * float(np.mean(tp)), "avg_rsd_range": [float(min(rsd)), float(max(rsd))],
             "launches": "chains: one chain of single-request launches per request on its own stream, one CUDA "

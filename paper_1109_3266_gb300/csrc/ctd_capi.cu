@@ -542,6 +542,7 @@ int ctd_destroy(ctd_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (auto l : ctx->lanes) cudaStreamSynchronize(l);
+    for (auto l : ctx->serve_hi) cudaStreamSynchronize(l);
     ctx->phantoms.clear();
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     for (auto e : ctx->events) cudaEventDestroy(e);
@@ -550,6 +551,7 @@ int ctd_destroy(ctd_ctx *ctx)
     for (auto e : ctx->lane_done) cudaEventDestroy(e);
     if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
     for (auto e : ctx->serve_ev) cudaEventDestroy(e);
+    for (auto l : ctx->serve_hi) cudaStreamDestroy(l);
     if (ctx->serve_res) cudaFreeHost(ctx->serve_res);
     if (ctx->staged) cudaFreeHost(ctx->staged);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

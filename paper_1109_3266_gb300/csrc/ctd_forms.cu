@@ -232,6 +232,15 @@ int ensure_serve_lanes(ctd_ctx *ctx)
     int rc;
     if ((rc = ensure_lanes(ctx, kMaxLanes))) return rc;
     if (ctx->lane_owner.empty()) ctx->lane_owner.assign(kMaxLanes, 0);
+    if (ctx->serve_hi.empty()) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        for (int i = 0; i < kMaxLanes; ++i) {
+            cudaStream_t st;
+            CK(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest));
+            ctx->serve_hi.push_back(st);
+        }
+    }
     while (ctx->serve_ev.size() < static_cast<size_t>(kMaxLanes)) {
         cudaEvent_t e;
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -329,9 +338,14 @@ void retire(ctd_ctx *ctx, ServeReq &R, int state)
 // The next batch of a running request on its own lane: transport, fold and, from
 // min_batches on, the statistics of the stop test with their copy to the lane's
 // pinned slot; the lane's event marks its end.
-int launch_batch(ctd_ctx *ctx, ServeReq &R, Phantom &P)
+int launch_batch(ctd_ctx *ctx, ServeReq &R, Phantom &P, bool first_in_line)
 {
-    const cudaStream_t s = ctx->lanes[R.lane];
+    // the oldest running request's batches go to its lane's high-priority stream, so that
+    // its blocks are dispatched first and younger requests fill the SMs its batches leave
+    // idle; a batch starts only after the request's previous one has finished (the host
+    // saw its event), so switching streams keeps the order.  The first batch stays on the
+    // lane's own stream, behind the buffers' clearing.
+    const cudaStream_t s = first_in_line && R.batches > 0 ? ctx->serve_hi[R.lane] : ctx->lanes[R.lane];
     const uint64_t B = R.req.batch_histories;
     ctd::RequestDesc q;
     fill_request(P, R.req.seed, q);
@@ -436,11 +450,12 @@ int serve_chains(ctd_ctx *ctx, bool *progress)
     const size_t before = ctx->active.size();
     if ((rc = admit(ctx, true))) return rc;
     moved = moved || ctx->active.size() != before;
+    const int64_t oldest = ctx->active.empty() ? 0 : ctx->active.front();   // admitted first in, first out
     for (int64_t id : std::vector<int64_t>(ctx->active)) {
         ServeReq &R = ctx->sreqs[id];
         if (R.in_flight) continue;
         Phantom *P = find(ctx, R.ph);
-        if (!P || (rc = launch_batch(ctx, R, *P))) {
+        if (!P || (rc = launch_batch(ctx, R, *P, id == oldest))) {
             retire(ctx, R, CTD_REQ_FAILED);
             if (!P) continue;
             return rc;

@@ -184,6 +184,7 @@ struct ctd_ctx {
     // marking the end of its batch in flight, and pinned slots [lane][4] the batch's
     // avg RSD, sigma_bar and D_max come back to
     std::vector<int64_t> lane_owner;
+    std::vector<cudaStream_t> serve_hi;   // per lane, a stream of the device's greatest priority
     std::vector<cudaEvent_t> serve_ev;
     double *serve_res = nullptr;
     ctd::host::DevBuf<unsigned long long> serve_work;   // claim counter per lane

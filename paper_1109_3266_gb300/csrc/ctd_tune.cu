@@ -1,6 +1,6 @@
-// ctd_tune.cu -- the launch-shape search for the single-request transport
-// kernel (ctd_autotune) and the memory-ceiling probes (ctd_probe_memory) of
-// the C ABI in include/ctd.h.
+// ctd_tune.cu -- the launch-shape searches for the single-request transport
+// kernel (ctd_autotune) and for the batched form (ctd_autotune_batch), and the
+// memory-ceiling probes (ctd_probe_memory) of the C ABI in include/ctd.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -157,6 +157,103 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
         out->n_tried = static_cast<int>(shapes.size());
         out->histories_per_s = static_cast<double>(n2) / best;
         out->baseline_per_s = static_cast<double>(n2) / base;
+        out->shared_launch = ctx->shared_launch;
+        out->multi_blocks_per_sm = ctx->multi_blocks_per_sm;
+    }
+    return CTD_OK;
+}
+
+int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const uint64_t *n_histories,
+                       const uint64_t *seeds, int n_batches, double probe_fraction, ctd_tune_result *out)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    if (n_req <= 0 || !phantoms || !n_histories || !seeds) return fail(CTD_EINVAL, "bad request arrays");
+    if (n_batches < 2) return fail(CTD_EINVAL, "need n_batches >= 2");
+    if (!(probe_fraction > 0.0 && probe_fraction <= 1.0)) return fail(CTD_EINVAL, "probe_fraction in (0, 1]");
+    // the probe: every request with a fraction of its histories (at least one per batch)
+    std::vector<uint64_t> nh(n_req);
+    uint64_t total = 0;
+    for (int r = 0; r < n_req; ++r) {
+        const double x = static_cast<double>(n_histories[r]) * probe_fraction;
+        nh[r] = std::max<uint64_t>(static_cast<uint64_t>(n_batches), static_cast<uint64_t>(x));
+        total += nh[r];
+    }
+    struct Shape {
+        int shared, threads, bps, mbps, chunk, cap;
+    };
+    const Shape old{ctx->shared_launch, ctx->threads, ctx->blocks_per_sm, ctx->multi_blocks_per_sm, ctx->chunk,
+                    ctx->flight_cap};
+    std::vector<Shape> shapes{old};
+    // request chains: block shape and residency of each request's launches; shared
+    // launches: blocks per SM of the multi-request kernel; both: claim size (how many
+    // histories a warp takes into its photon queue at a time) and flight cap (how many
+    // Woodcock flights a lane runs before its warp regroups at the queue)
+    const int chains[3][2] = {{256, 4}, {256, 3}, {128, 8}};
+    for (const auto &b : chains)
+        for (int chunk : {256, 1024})
+            for (int cap : {2, 4})
+                shapes.push_back({0, b[0], b[1], old.mbps, chunk, cap});
+    for (int mbps : {2, 3, 4})
+        for (int chunk : {256, 1024})
+            for (int cap : {2, 4})
+                shapes.push_back({1, 256, old.bps, mbps, chunk, cap});
+    auto apply = [&](const Shape &s) {
+        ctx->shared_launch = s.shared;
+        ctx->threads = s.threads;
+        ctx->blocks_per_sm = s.bps;
+        ctx->multi_blocks_per_sm = s.mbps;
+        ctx->chunk = s.chunk;
+        ctx->flight_cap = s.cap;
+    };
+    // best of two timed batched calls (the first call of a shape records its graph)
+    auto time_shape = [&](const Shape &s, double &t_min) -> int {
+        apply(s);
+        t_min = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            const double t0 = now_s();
+            int e;
+            if ((e = ctd_run_batch(ctx, n_req, phantoms, nh.data(), seeds, n_batches))) return e;
+            if (rep > 0) t_min = std::min(t_min, now_s() - t0);
+        }
+        return CTD_OK;
+    };
+    double best = 1e300, base = 0.0;
+    Shape pick = old;
+    for (size_t k = 0; k < shapes.size(); ++k) {
+        // one node grid per shared launch: shapes the requests cannot share are skipped
+        if (shapes[k].shared && k > 0) {
+            bool same = true;
+            const Phantom *P0 = find(ctx, phantoms[0]);
+            for (int r = 1; r < n_req && same && P0; ++r) {
+                const Phantom *P = find(ctx, phantoms[r]);
+                same = P && P->phys.e_min_kev == P0->phys.e_min_kev && P->phys.e_max_kev == P0->phys.e_max_kev &&
+                       P->phys.n_zeta == P0->phys.n_zeta;
+            }
+            if (!same) continue;
+        }
+        double t;
+        if ((rc = time_shape(shapes[k], t))) {
+            apply(old);
+            return rc;
+        }
+        if (k == 0) base = t;
+        if (t < best) {
+            best = t;
+            pick = shapes[k];
+        }
+    }
+    apply(pick);
+    if (out) {
+        out->threads_per_block = pick.threads;
+        out->blocks_per_sm = pick.bps;
+        out->chunk = pick.chunk;
+        out->flight_cap = pick.cap;
+        out->n_tried = static_cast<int>(shapes.size());
+        out->histories_per_s = static_cast<double>(total) / best;
+        out->baseline_per_s = static_cast<double>(total) / base;
+        out->shared_launch = pick.shared;
+        out->multi_blocks_per_sm = pick.mbps;
     }
     return CTD_OK;
 }

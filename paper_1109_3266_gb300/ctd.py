@@ -82,7 +82,8 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(5)
 
 class ctd_tune_result(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int), ("n_tried", C.c_int),
-                ("histories_per_s", C.c_double), ("baseline_per_s", C.c_double), ("threads_per_block", C.c_int)]
+                ("histories_per_s", C.c_double), ("baseline_per_s", C.c_double), ("threads_per_block", C.c_int),
+                ("shared_launch", C.c_int), ("multi_blocks_per_sm", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -132,6 +133,8 @@ def lib():
         L.ctd_wait.argtypes = [P, C.c_int64, C.c_double, C.POINTER(ctd_req_status)]
         L.ctd_cancel.argtypes = [P, C.c_int64]
         L.ctd_autotune.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.POINTER(ctd_tune_result)]
+        L.ctd_autotune_batch.argtypes = [P, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_uint64),
+                                         C.POINTER(C.c_uint64), C.c_int, C.c_double, C.POINTER(ctd_tune_result)]
         L.ctd_probe_memory.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, dp]
         L.ctd_set_fluence.argtypes = [P, C.c_int32, C.c_int, C.c_int, dp]
         L.ctd_spectrum_kramers.argtypes = [C.c_int, C.c_double, C.c_int, dp, dp, dp, C.POINTER(C.c_int)]
@@ -276,6 +279,18 @@ def ctd_autotune(ctx, ph, n_probe, seed=1):
     """Pick the fastest launch shape for this phantom's problem; returns the choice."""
     r = ctd_tune_result()
     _check(lib().ctd_autotune(ctx, ph, int(n_probe), int(seed), C.byref(r)))
+    return r.as_dict()
+
+
+def ctd_autotune_batch(ctx, phantoms, n_histories, seeds, n_batches, probe_fraction=0.05):
+    """Pick the batched form's launch design and shape for these requests (kept in the
+    context); returns the choice."""
+    n = len(phantoms)
+    ph = (C.c_int32 * n)(*phantoms)
+    nh = (C.c_uint64 * n)(*[int(x) for x in n_histories])
+    sd = (C.c_uint64 * n)(*[int(x) for x in seeds])
+    r = ctd_tune_result()
+    _check(lib().ctd_autotune_batch(ctx, n, ph, nh, sd, int(n_batches), float(probe_fraction), C.byref(r)))
     return r.as_dict()
 
 

@@ -164,7 +164,7 @@ def test_served_requests_join_while_others_are_on_the_gpu(ctd):
     ha, hb = ctd.load_problem(c, pa), ctd.load_problem(c, pb)
     a = ctd.ctd_submit(c, ha, 200_000_000, 1e-9, 5, n_histories_max=10 ** 11)
     ctd.ctd_serve_step(c)                                      # a's first batch goes to the GPU
-    b = ctd.ctd_submit(c, hb, 5_000, 0.5, 6, n_histories_max=200_000)
+    b = ctd.ctd_submit(c, hb, 5_000, 0.5, pb.seed, n_histories_max=200_000)
     ctd.ctd_serve_step(c)
     sa, sb = ctd.ctd_poll(c, a), ctd.ctd_poll(c, b)
     assert sb["state"] == ctd.REQ_RUNNING and sa["batches"] == 0, (sa, sb)
@@ -232,6 +232,23 @@ def test_batched_full_size_requests(ctd, oracle):
     for r in (1, 62):
         p = reqs[r]
         histories_match_binary64(ctd, c, hs[r], p, oracle, ranges=[(0, 3000), (p.n_hist - 3000, p.n_hist)])
+    ctd.ctd_destroy(c)
+
+
+def test_batched_autotuner_picks_a_shape_and_results_do_not_depend_on_it(ctd, ctx):
+    ps = problems()
+    ref = [alone(ctd, ctx, p) for p in ps]
+    c = ctd.ctd_create(device=0)
+    hs = [ctd.load_problem(c, p) for p in ps]
+    r = ctd.ctd_autotune_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10, probe_fraction=0.2)
+    assert r["n_tried"] == 25 and r["histories_per_s"] > 0 and r["baseline_per_s"] > 0
+    assert r["shared_launch"] in (0, 1) and r["chunk"] in (256, 1024) and r["flight_cap"] in (2, 4)
+    # the context keeps the choice; the full requests give what they give alone
+    ctd.ctd_run_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
+    for p, h, rr in zip(ps, hs, ref):
+        same(rr, ctd.ctd_get_dose_and_stddev(c, h, p.phantom.nvox))
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_autotune_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10, probe_fraction=0.0)
     ctd.ctd_destroy(c)
 
 

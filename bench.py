@@ -496,7 +496,7 @@ def leg_batched(ctd, args, clk):
     ctxs.append(ctd.ctd_create(device=0, stream=stream.cuda_stream))
     hss.append([ctd.load_problem(ctxs[2], p) for p in reqs])
     t0 = time.perf_counter()
-    tune = ctd.ctd_autotune_batch(ctxs[2], hss[2], [p.n_hist for p in reqs], [p.seed for p in reqs], nb, 0.05)
+    tune = ctd.ctd_autotune_batch(ctxs[2], hss[2], [p.n_hist for p in reqs], [p.seed for p in reqs], nb, 0.04)
     tune["seconds"] = time.perf_counter() - t0
     timed(lambda: batched(2), 1)
     a = clk.mark()

@@ -434,16 +434,17 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
 /* Autotuner of the batched form (the paper has no counterpart).  It times
  * ctd_run_batch of the given requests, each with probe_fraction of its histories
  * (at least one per batch), best of two calls after one that records the graph,
- * over: request chains with blocks of 256 threads at 4 or 3 per SM or of 128 at 8
+ * over the shapes below; then the three fastest and the context's own shape
+ * again with five times the fraction (at most all of it).  The shapes: request chains with blocks of 256 threads at 4 or 3 per SM or of 128 at 8
  * per SM; shared multi-request launches at 2, 3 or 4 blocks per SM; claims of
  * 256 or 1024 histories (how many a warp takes into its photon queue at a time);
  * flight caps of 2 or 4 (how many Woodcock flights a lane runs before its warp
  * regroups at the queue); and the context's own shape (25 in all; shared
  * shapes are skipped when the requests do not share one node grid).  The
- * fastest is kept in the context (shared_launch, threads_per_block,
- * blocks_per_sm, multi_blocks_per_sm, chunk, flight_cap) and returned in out
- * (histories_per_s on the probe; baseline_per_s of the context's previous
- * shape).  Results do not depend on the shape (up to the order of binary64
+ * fastest on the longer probe is kept in the context (shared_launch,
+ * threads_per_block, blocks_per_sm, multi_blocks_per_sm, chunk, flight_cap) and
+ * returned in out (histories_per_s on the longer probe; baseline_per_s of the
+ * context's previous shape there; n_tried, the shapes of the first pass).  Results do not depend on the shape (up to the order of binary64
  * additions).  The requests' phantoms end holding the last probe's results. */
 int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const uint64_t *n_histories,
                        const uint64_t *seeds, int n_batches, double probe_fraction, ctd_tune_result *out);

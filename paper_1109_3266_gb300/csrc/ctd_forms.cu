@@ -225,6 +225,8 @@ namespace {
 
 double elapsed_since(double t) { return now_s() - t; }
 
+constexpr int kServeSlices = 8;   // launches per batch of a served request that is not the oldest
+
 // Lanes, their events and pinned result slots for served request chains, made
 // once per context.
 int ensure_serve_lanes(ctd_ctx *ctx)
@@ -352,11 +354,18 @@ int launch_batch(ctd_ctx *ctx, ServeReq &R, Phantom &P, bool first_in_line)
     q.work = ctx->serve_work.p + R.lane;
     q.pref = P.pref.p + 1 * (q.nbins + 1);    // batches of exactly B histories
     q.h_base = static_cast<uint64_t>(R.batches) * B;
-    q.local_begin = 0;
-    q.local_end = B;
     q.tally = P.tally.p;
-    CK(cudaMemsetAsync(q.work, 0, sizeof(unsigned long long), s));
-    CKS(launch_one(ctx, P, q, s));
+    // the other requests' batches go out as kServeSlices launches of consecutive history
+    // ranges: their persistent blocks give the SMs back between slices, so the oldest
+    // request's next batch waits at most one slice for them
+    const int slices = first_in_line ? 1 : kServeSlices;
+    for (int i = 0; i < slices; ++i) {
+        q.local_begin = B * static_cast<uint64_t>(i) / slices;
+        q.local_end = B * static_cast<uint64_t>(i + 1) / slices;
+        if (q.local_begin == q.local_end) continue;
+        CK(cudaMemsetAsync(q.work, 0, sizeof(unsigned long long), s));
+        CKS(launch_one(ctx, P, q, s));
+    }
     const double scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
     CKS(ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, scale, s));
     R.checked = R.batches + 1 >= R.req.min_batches;

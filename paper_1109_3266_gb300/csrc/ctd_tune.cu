@@ -218,8 +218,7 @@ int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, con
         }
         return CTD_OK;
     };
-    double best = 1e300, base = 0.0;
-    Shape pick = old;
+    std::vector<std::pair<double, size_t>> t1;
     for (size_t k = 0; k < shapes.size(); ++k) {
         // one node grid per shared launch: shapes the requests cannot share are skipped
         if (shapes[k].shared && k > 0) {
@@ -237,6 +236,29 @@ int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, con
             apply(old);
             return rc;
         }
+        t1.push_back({t, k});
+    }
+    // second pass: the three fastest and the context's own shape on probes five times
+    // longer (short probes overrate shapes that drain a launch's tail sooner)
+    std::sort(t1.begin(), t1.end());
+    std::vector<size_t> finalists{0};
+    for (size_t r = 0; r < t1.size() && finalists.size() < 4; ++r)
+        if (t1[r].second != 0) finalists.push_back(t1[r].second);
+    const double f2 = std::min(1.0, 5.0 * probe_fraction);
+    total = 0;
+    for (int r = 0; r < n_req; ++r) {
+        const double x = static_cast<double>(n_histories[r]) * f2;
+        nh[r] = std::max<uint64_t>(static_cast<uint64_t>(n_batches), static_cast<uint64_t>(x));
+        total += nh[r];
+    }
+    double best = 1e300, base = 0.0;
+    Shape pick = old;
+    for (size_t k : finalists) {
+        double t;
+        if ((rc = time_shape(shapes[k], t))) {
+            apply(old);
+            return rc;
+        }
         if (k == 0) base = t;
         if (t < best) {
             best = t;
@@ -249,7 +271,7 @@ int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, con
         out->blocks_per_sm = pick.bps;
         out->chunk = pick.chunk;
         out->flight_cap = pick.cap;
-        out->n_tried = static_cast<int>(shapes.size());
+        out->n_tried = static_cast<int>(t1.size());
         out->histories_per_s = static_cast<double>(total) / best;
         out->baseline_per_s = static_cast<double>(total) / base;
         out->shared_launch = pick.shared;

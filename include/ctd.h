@@ -197,6 +197,21 @@ int ctd_set_fluence(ctd_ctx *ctx, ctd_phantom ph, int n_u, int n_v, const double
  * (either pointer may be NULL; *n = 0 without a map). */
 int ctd_get_fluence_table(ctd_ctx *ctx, ctd_phantom ph, int *n, uint32_t *thr, int32_t *alias);
 
+/* The paper's Metropolis-Hastings beamlet sampler (Sec. 2.2.4, Algorithm A1) on
+ * the device, as the paper runs it: `chains` independent chains, one per GPU
+ * thread.  Chain c takes particles [floor(n/chains) c + min(c, n mod chains), ...)
+ * of n (the first n mod chains chains one more) and starts at beamlet i0;
+ * particle i draws a trial beamlet J = floor(x n_f / 2^32) and zeta =
+ * (2 (y >> 9) + 1) 2^-24 from the words x, y of Philox block (i, 0, stream 4)
+ * under seed, and moves to J if zeta < f_J / f_last (binary64), else stays.
+ * counts[n_f] (host) receives how often each beamlet was visited.  The transport
+ * draws beamlets from the alias table instead (ctd_set_fluence): a chain makes a
+ * photon's beamlet depend on the particles before it in its thread.  1 <= n_f <=
+ * 2^24 intensities f >= 0 (host), 0 <= i0 < n_f, 1 <= chains <= 2^32, else
+ * CTD_EINVAL.  Allocates device memory for the call. */
+int ctd_mh_beamlets(ctd_ctx *ctx, int n_f, const double *f, int i0, uint64_t n, uint64_t seed, uint64_t chains,
+                    uint64_t *counts);
+
 /* Spectrum (Sec. 2.2.5): nbins intervals [e_lo[j], e_hi[j]] keV (e_lo == e_hi
  * is a line) with weights w[j] >= 0, sum > 0, inside [e_min, e_max] of the
  * physics.  Each batch's histories are split over the bins by largest

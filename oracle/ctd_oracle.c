@@ -524,6 +524,29 @@ void or_mh_counts(int n_f, const double *f, int i0, uint64_t n, uint64_t seed, u
     }
 }
 
+/* Algorithm A1 as the paper runs it on a GPU: one chain per thread.  Chain c of
+ * `chains` takes particles [n c / chains, n (c + 1) / chains), starts at beamlet
+ * i0 and draws particle i from Philox block (i, 0, stream 4), as the single chain
+ * does; the counts of all chains are summed.  chains = 1 is or_mh_counts. */
+void or_mh_chains(int n_f, const double *f, int i0, uint64_t n, uint64_t seed, uint64_t chains, uint64_t *counts)
+{
+    for (int i = 0; i < n_f; ++i) counts[i] = 0;
+    for (uint64_t c = 0; c < chains; ++c) {
+        uint64_t lo = (n / chains) * c + (c < n % chains ? c : n % chains);
+        uint64_t len = n / chains + (c < n % chains ? 1 : 0);
+        int last = i0;
+        for (uint64_t i = lo; i < lo + len; ++i) {
+            uint32_t b[4];
+            or_block(seed, i, 0, OR_STREAM_MH, b);
+            int j = (int)(((uint64_t)b[0] * (uint64_t)(uint32_t)n_f) >> 32);
+            double zeta = or_uniform(b[1]);
+            int cur = zeta < f[j] / f[last] ? j : last;
+            counts[cur]++;
+            last = cur;
+        }
+    }
+}
+
 /* ===================================================================== */
 /* Set-up: tables, majorant, surfaces, batch and bin offsets.            */
 /* ===================================================================== */

@@ -15,10 +15,11 @@
  *
  * Every function exists in two precisions built from one source:
  *   *_f64 : the method in IEEE binary64 with the C library's log/sin/cos/sqrt;
- *   *_f32 : the method in the paper's single precision (Sec. 2.2.7 item 1), with
- *           a fixed operation order and the single-precision log and sincos
- *           defined in ctd_oracle.c, so that integer decisions (interaction
- *           type, voxel index, escape) are taken in binary32.
+ *   *_f32 : a second restatement in the paper's single precision (Sec. 2.2.7
+ *           item 1), with the single-precision log and sincos defined in
+ *           ctd_oracle.c, so that integer decisions (interaction type, voxel
+ *           index, escape) are taken in binary32; the CPU tests compare it with
+ *           *_f64 history by history under the decision margins below.
  * Integer-only helpers (Philox, allocation) have one version.
  */
 #ifndef CTD_ORACLE_H
@@ -214,6 +215,10 @@ void or_alias_counts(int n_f, const uint32_t *thr, const int32_t *alias, uint64_
  * (Algorithm A1) started at beamlet i0: trial J uniform, kept if zeta < f_J /
  * f_last (particle i: Philox block (i, 0, stream 4) under seed). */
 void or_mh_counts(int n_f, const double *f, int i0, uint64_t n, uint64_t seed, uint64_t *counts);
+/* The same with one chain per GPU thread, as the paper runs A1: chain c of `chains`
+ * takes particles [n c / chains, n (c + 1) / chains) (the first n mod chains
+ * chains one more), each starting at i0; counts summed over the chains. */
+void or_mh_chains(int n_f, const double *f, int i0, uint64_t n, uint64_t seed, uint64_t chains, uint64_t *counts);
 
 /* the direction rotation on its own, for invariant checks */
 void or_rotate_f64(double *u, double mu, double t_phi);

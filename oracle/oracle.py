@@ -127,6 +127,7 @@ def _declare(L):
     L.or_alias_counts.argtypes = [C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_int32), C.c_uint64, C.c_uint64,
                                   C.POINTER(C.c_uint64)]
     L.or_mh_counts.argtypes = [C.c_int, dp, C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_uint64)]
+    L.or_mh_chains.argtypes = [C.c_int, dp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(C.c_uint64)]
     L.or_rotate_f64.argtypes = [dp, C.c_double, C.c_double]
     L.or_rotate_f32.argtypes = [C.POINTER(C.c_float), C.c_float, C.c_float]
 
@@ -279,6 +280,14 @@ def mh_counts(f, n, seed, i0=0):
     f = np.ascontiguousarray(f, dtype=np.float64).ravel()
     out = np.zeros(f.size, dtype=np.uint64)
     lib().or_mh_counts(f.size, _ptr(f, C.c_double), i0, n, seed, _ptr(out, C.c_uint64))
+    return out
+
+
+def mh_chains(f, n, seed, chains, i0=0):
+    """Beamlet counts of Algorithm A1 run as `chains` chains (one per GPU thread)."""
+    f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+    out = np.zeros(f.size, dtype=np.uint64)
+    lib().or_mh_chains(f.size, _ptr(f, C.c_double), i0, n, seed, chains, _ptr(out, C.c_uint64))
     return out
 
 

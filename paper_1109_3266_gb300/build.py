@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libctd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["ctd_capi.cu", "ctd_forms.cu", "ctd_tune.cu", "ctd_transport.cu", "ctd_stats.cu", "ctd_physics.cpp",
-           "ctd_noalloc.cu", "ctd_probe.cu"]
+           "ctd_noalloc.cu", "ctd_probe.cu", "ctd_fluence.cu"]
 HEADERS = ["ctd_internal.h", "ctd_host.h", "ctd_device.cuh"]
 FAST_MATH = {"ctd_transport.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

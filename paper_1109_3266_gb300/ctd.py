@@ -113,6 +113,8 @@ def lib():
         L.ctd_run.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int]
         L.ctd_run_range.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]
         L.ctd_trace_range.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, P]
+        L.ctd_mh_beamlets.argtypes = [P, C.c_int, dp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64,
+                                      C.POINTER(C.c_uint64)]
         L.ctd_shard_begin.argtypes = [P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int]
         L.ctd_shard_batch.argtypes = [P, C.c_int32, C.c_int, C.c_uint64, C.c_uint64, P]
         L.ctd_shard_fold.argtypes = [P, C.c_int32, C.c_int, P]
@@ -497,6 +499,16 @@ def ctd_set_fluence(ctx, ph, f):
     if f.ndim != 2:
         raise CtdError(1, "fluence map must be [n_v][n_u]")
     _check(lib().ctd_set_fluence(ctx, ph, f.shape[1], f.shape[0], _dp(f)))
+
+
+def ctd_mh_beamlets(ctx, f, n, seed, chains, i0=0):
+    """Beamlet visit counts of the paper's Metropolis-Hastings sampler (Algorithm A1) run on
+    the device as `chains` chains, one per thread."""
+    f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+    out = np.zeros(f.size, dtype=np.uint64)
+    _check(lib().ctd_mh_beamlets(ctx, f.size, _dp(f), int(i0), int(n), int(seed), int(chains),
+                                 out.ctypes.data_as(C.POINTER(C.c_uint64))))
+    return out
 
 
 def ctd_get_fluence_table(ctx, ph):

@@ -96,3 +96,32 @@ def test_bowtie_request_batches_with_others(ctd, ctx):
             assert all(st[k] == st2[k] for k in COUNT_KEYS)
             assert np.allclose(d2, dose, rtol=1e-9, atol=0)
         ctd.ctd_destroy(c)
+
+
+@pytest.mark.parametrize("chains", [1, 7, 4096])
+def test_device_mh_chains_equal_oracle(ctd, ctx, oracle, chains):
+    # the paper's Algorithm A1 on the device, one chain per thread: visit counts equal
+    # the oracle's chains exactly (integer draws, the binary64 acceptance ratio)
+    f = I.bowtie_fluence(128, 32, seed=1).ravel()
+    n = 200_000
+    dev = ctd.ctd_mh_beamlets(ctx, f, n, 5, chains, i0=17)
+    assert np.array_equal(dev, oracle.mh_chains(f, n, seed=5, chains=chains, i0=17))
+    with pytest.raises(ctd.CtdError):
+        ctd.ctd_mh_beamlets(ctx, f, n, 5, 0)
+
+
+def test_device_mh_against_the_alias_draw_on_the_fig5_error(ctd, ctx):
+    # Fig. 5(c): e(N) = ||counts/N - p*|| / ||p*|| of the beamlet frequencies.  The alias draw
+    # is a multinomial sample, e(N) = sqrt(sum p(1-p)/N) / ||p|| in expectation; A1 with one
+    # chain per GPU thread (65536 chains, each from beamlet 0) is correlated within a chain
+    # and biased toward its start while chains are short
+    f = I.bowtie_fluence(128, 32, seed=1).ravel()
+    p = f / f.sum()
+    es = []
+    for n in (10 ** 6, 10 ** 7, 10 ** 8):
+        c = ctd.ctd_mh_beamlets(ctx, f, n, 11, 65536, i0=0)
+        e = np.linalg.norm(c / n - p) / np.linalg.norm(p)
+        e_multi = np.sqrt(np.sum(p * (1 - p)) / n) / np.linalg.norm(p)
+        assert e > e_multi
+        es.append(e)
+    assert es[0] > es[1] > es[2]

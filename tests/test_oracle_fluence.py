@@ -106,3 +106,28 @@ def test_thin_absorber_records_the_map(oracle):
         ex = sub_counts.sum(axis=1, keepdims=True) / (sub * sub)
         chi2 = ((sub_counts - ex) ** 2 / ex).sum()
         assert stats.chi2.sf(chi2, f.size * (sub * sub - 1)) > 1e-4
+
+
+def test_mh_chains_one_chain_is_the_single_chain_and_counts_add_up(oracle):
+    f = I.bowtie_fluence(16, 4, seed=2).ravel()
+    for n in (1, 1000, 123_457):
+        assert np.array_equal(oracle.mh_chains(f, n, seed=9, chains=1, i0=5), oracle.mh_counts(f, n, seed=9, i0=5))
+        for chains in (2, 7, 1000):
+            c = oracle.mh_chains(f, n, seed=9, chains=chains, i0=5)
+            assert int(c.sum()) == n
+    # chains of one particle each visit the trial or stay at i0: every trial beamlet whose
+    # intensity is at least i0's is accepted
+    n = 20_000
+    c = oracle.mh_chains(f, n, seed=3, chains=n, i0=5)
+    assert c[5] >= n // f.size
+
+
+def test_mh_chains_converge_like_the_single_chain(oracle):
+    # long chains: the visit frequencies approach f / sum f; one chain per particle
+    # never moves far from i0 and stays biased
+    f = I.bowtie_fluence(32, 8, seed=4).ravel()
+    p = f / f.sum()
+    n = 2_000_000
+    e_long = np.linalg.norm(oracle.mh_chains(f, n, seed=5, chains=16) / n - p) / np.linalg.norm(p)
+    e_short = np.linalg.norm(oracle.mh_chains(f, n, seed=5, chains=n // 4) / n - p) / np.linalg.norm(p)
+    assert e_long < 0.05 and e_short > 2 * e_long

@@ -159,4 +159,8 @@ def test_trace_launch_equals_production_launch(ctd, ctx):
     assert ctd.ctd_trace_range(ctx, h, p.n_hist, p.seed, p.n_batches, 5, 5).size == 0
     with pytest.raises(ctd.CtdError):
         ctd.ctd_trace_range(ctx, h, p.n_hist, p.seed, p.n_batches, 0, p.n_hist + 1)
+    # more records than one call may hold (2^26) are refused before any work
+    with pytest.raises(ctd.CtdError) as e:
+        ctd.ctd_trace_range(ctx, h, 2 ** 30, p.seed, p.n_batches, 0, 2 ** 26 + 1)
+    assert "2^26" in str(e.value) or "67108864" in str(e.value)
     ctd.ctd_destroy_phantom(ctx, h)

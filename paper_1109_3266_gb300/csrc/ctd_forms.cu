@@ -106,22 +106,32 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
         }
         if ((rc = ensure_lanes(ctx, n_req))) return rc;
         if (!event_at(ctx, 0) || !event_at(ctx, 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
-        body = [&](cudaStream_t cs) {
+        // chains are issued largest first, so that the last to finish are short ones
+        // (longest processing time first: the smaller requests fill the tail)
+        std::vector<int> order(n_req);
+        for (int r = 0; r < n_req; ++r) order[r] = r;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return n_histories[a] > n_histories[b]; });
+        put(order.data(), order.size() * sizeof(int));
+        body = [&, order](cudaStream_t cs) {
             if (cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long),
                                 cs) != cudaSuccess ||
                 cudaEventRecordWithFlags(ctx->events[0], cs, cudaEventRecordExternal) != cudaSuccess)
                 return static_cast<int>(CTD_ECUDA);
             int e = fork_lanes(ctx, cs, n_req);
-            for (int r = 0; r < n_req && e == CTD_OK; ++r) {
+            for (int k = 0; k < n_req && e == CTD_OK; ++k) {
+                const int r = order[k];
                 Phantom &P = *ps[r];
+                // the k-th largest request on lane k (mod the lanes)
+                const cudaStream_t ls = lane(ctx, k);
                 for (int b = 0; b < n_batches && e == CTD_OK; ++b) {
-                    const size_t k = static_cast<size_t>(b) * n_req + r;
-                    e = launch_one(ctx, P, descs[k], lane(ctx, r));
+                    const size_t d = static_cast<size_t>(b) * n_req + r;
+                    e = launch_one(ctx, P, descs[d], ls);
                     if (e == CTD_OK)
-                        e = ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, folds[k].scale,
-                                             lane(ctx, r));
+                        e = ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, folds[d].scale,
+                                             ls);
                 }
-                if (e == CTD_OK) e = finish_stats(P, n_batches, lane(ctx, r));
+                if (e == CTD_OK) e = finish_stats(P, n_batches, ls);
             }
             if (e == CTD_OK) e = join_lanes(ctx, cs, n_req);
             if (e == CTD_OK && cudaEventRecordWithFlags(ctx->events[1], cs, cudaEventRecordExternal) != cudaSuccess)

@@ -157,6 +157,7 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
         fill_shared(*ps[0], L.sh);
         L.sh.max_n_mat = max_n_mat;
         L.n_req = n_req;
+        for (int r = 0; r < n_req; ++r) L.any_fluence |= ps[r]->fl_nu > 0;
         L.chunk = ctx->chunk;
         L.flight_cap = ctx->flight_cap;
         put(&L, sizeof(L));
@@ -559,6 +560,7 @@ int serve_round(ctd_ctx *ctx)
     L.sh.max_n_mat = max_n_mat;
     L.reqs = ctx->u_reqs.p;
     L.n_req = n;
+    for (int i = 0; i < n; ++i) L.any_fluence |= ps[i]->fl_nu > 0;
     L.chunk = ctx->chunk;
     L.flight_cap = ctx->flight_cap;
     const int mgrid = ctx->num_sms * ctx->multi_blocks_per_sm;

@@ -158,6 +158,7 @@ struct LaunchParams {
     int n_req;
     int chunk;                   // histories a warp claims at a time
     int flight_cap;              // Woodcock flights a lane takes before yielding to the warp
+    int any_fluence;             // multi-request launches: some request has a fluence map
     // per-history records of a trace launch (single request; nullptr otherwise):
     // record i is history trace_h0 + i, for i < trace_n
     uint4 *trace;

@@ -12,11 +12,11 @@
 // Per-step event counts live in registers, the rest of a lane's counts in its
 // shared-memory slot.
 //
-// One kernel template, three forms: one request without a fluence map, one
+// One kernel template, four forms: one request without a fluence map, one
 // request with one (its source path compiled only there), both with the request
-// in the kernel's parameter space; and many requests at once (blocks walk
-// through a request table, one request at a time, its descriptor and tables in
-// shared memory).
+// in the kernel's parameter space; and many requests at once, without or with
+// maps (blocks walk through a request table, one request at a time, its
+// descriptor and tables in shared memory).
 #include "ctd_device.cuh"
 
 namespace ctd {
@@ -563,7 +563,10 @@ __device__ __forceinline__ void load_tables(const RequestDesc &q, int n_e, float
 // one, so that one request's tail overlaps the next one's start.
 // kForm: 0 one request without a fluence map, 1 one request with a fluence map
 // (the map's source path is compiled only into this form, so that it does not
-// cost the open-field form registers), 2 several requests (maps checked per request).
+// cost the open-field form registers), 2 several requests without maps, 3 several
+// requests of which some have a map (checked per request).  The multi-request
+// forms take each request's Philox round keys from its descriptor in shared
+// memory.
 // kTrace (single-request forms): also write each history's record to P.trace.
 template <int kMaxThreads, int kMinBlocks, int kForm, bool kTrace = false>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(const LaunchParams P)
@@ -584,7 +587,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
     cnt.me = reinterpret_cast<LaneSlot *>(wbase + kQueueBytes + sizeof(WarpPool)) + lane;
     cnt.clear();
 
-    constexpr bool kMulti = kForm == 2;
+    constexpr bool kMulti = kForm >= 2;
     if (!kMulti) {
         load_tables(P.one, n_e, s_tab, s_mm);
         __syncthreads();
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
         __syncthreads();
         load_tables(q, n_e, s_tab, s_mm);
         __syncthreads();
-        run_request<false, true, false>(P, q, s_tab, s_mm, Q, lane, cnt);
+        run_request<true, kForm == 3, false>(P, q, s_tab, s_mm, Q, lane, cnt);
         flush_warp(q.counts, cnt, lane);
         __syncthreads();
         // the same request is exhausted now; continue the walk from it
@@ -711,7 +714,8 @@ int launch_transport(const LaunchParams &p, int grid, int block, int threads_per
         return p.one.fl_n > 0 ? launch_t<256, 4, 1, true>(p, grid, block, smem, s)
                               : launch_t<256, 4, 0, true>(p, grid, block, smem, s);
     }
-    if (p.n_req > 0) return launch_m<2>(p, grid, block, threads_per_sm, smem, s);
+    if (p.n_req > 0) return p.any_fluence ? launch_m<3>(p, grid, block, threads_per_sm, smem, s)
+                                           : launch_m<2>(p, grid, block, threads_per_sm, smem, s);
     return p.one.fl_n > 0 ? launch_m<1>(p, grid, block, threads_per_sm, smem, s)
                           : launch_m<0>(p, grid, block, threads_per_sm, smem, s);
 }

@@ -576,6 +576,7 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     // voxel indices are 32-bit on the device
     if (nvox >= (static_cast<size_t>(1) << 32)) return fail(CTD_EINVAL, "phantom too large (2^32 voxels or more)");
     std::unique_ptr<Phantom> P(new Phantom());
+    P->use_cache(&ctx->buffers);
     P->nx = nx; P->ny = ny; P->nz = nz;
     P->dx = dx; P->dy = dy; P->dz = dz;
     P->nvox = nvox;

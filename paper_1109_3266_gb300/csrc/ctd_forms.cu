@@ -299,6 +299,7 @@ int admit(ctd_ctx *ctx, bool chains)
         }
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
+        free_b += ctx->buffers.cached;   // released buffers the context holds for reuse
         const double need = P->tally.p ? 0.0 : 6.0 * 8.0 * static_cast<double>(P->nvox);
         if (static_cast<double>(free_b) < need + ctx->reserve_bytes) break;
         int rc;

@@ -37,14 +37,46 @@ int fail(int code, const char *fmt, ...);
         }                                                                                                 \
     } while (0)
 
+// Device buffers a context has released and may hand out again: the byte size of
+// each, up to `cap` bytes in all.  A phantom's buffers return here when it is
+// destroyed (after its context's stream is idle), so a phantom of the same size
+// created next takes them without cudaMalloc, and no cudaFree synchronises the
+// device meanwhile.  The context frees what is left when it is destroyed.
+struct BufferCache {
+    std::multimap<size_t, void *> blocks;
+    size_t cached = 0;
+    size_t cap = size_t(4) << 30;
+    void *take(size_t bytes)
+    {
+        auto it = blocks.find(bytes);
+        if (it == blocks.end()) return nullptr;
+        void *p = it->second;
+        blocks.erase(it);
+        cached -= bytes;
+        return p;
+    }
+    bool give(void *p, size_t bytes)
+    {
+        if (cached + bytes > cap) return false;
+        blocks.emplace(bytes, p);
+        cached += bytes;
+        return true;
+    }
+    ~BufferCache()
+    {
+        for (auto &b : blocks) cudaFree(b.second);
+    }
+};
+
 template <class T>
 struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
+    BufferCache *cache = nullptr;   // where released buffers go (nullptr: cudaFree)
     ~DevBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p && !(cache && cache->give(p, n * sizeof(T)))) cudaFree(p);
         p = nullptr;
         n = 0;
     }
@@ -53,6 +85,10 @@ struct DevBuf {
         if (count <= n && p) return CTD_OK;
         release();
         if (count == 0) count = 1;
+        if (cache && (p = static_cast<T *>(cache->take(count * sizeof(T))))) {
+            n = count;
+            return CTD_OK;
+        }
         if (cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T)) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -106,6 +142,18 @@ struct Phantom {
     uint64_t shard_n = 0, shard_seed = 0;
     int shard_nb = 0;
     double shard_t0 = 0.0;
+    // every device buffer of the phantom takes from and returns to cache c
+    void use_cache(BufferCache *c)
+    {
+        for (DevBuf<float> *b : {&rho, &tab, &mm, &cs, &rs, &bins, &proj}) b->cache = c;
+        for (DevBuf<double> *b : {&tally, &sum_d, &sum_d2, &edep, &dose, &sd, &partials, &result}) b->cache = c;
+        mat.cache = c;
+        counts.cache = c;
+        work.cache = c;
+        pref.cache = c;
+        fl_thr.cache = c;
+        fl_alias.cache = c;
+    }
 };
 
 struct Staged {
@@ -146,6 +194,8 @@ struct ctd_ctx {
     int threads = 256;
     int chunk = 256;
     int flight_cap = 4;
+    // released device buffers (declared before the phantoms: it outlives them)
+    ctd::host::BufferCache buffers;
     std::map<int, std::unique_ptr<ctd::host::Phantom>> phantoms;
     int next_id = 1;
     std::vector<cudaEvent_t> events;

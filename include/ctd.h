@@ -114,7 +114,8 @@ typedef enum { CTD_MODE_FULL = 0, CTD_MODE_MAX_REAL = 1 } ctd_mode;
  * compton_model (Sec. 2.2.3): CTD_COMPTON_KN, free-electron Klein-Nishina
  * (Eq. 2 with S = 1; total in closed form, one C surface for all materials);
  * CTD_COMPTON_WH, Waller-Hartree (Eq. 2 with each material's S(q); total by
- * composite Simpson integration of Eq. 2 over 20000 intervals in cos theta,
+ * integration of Eq. 2 over cos theta (16-point Gauss-Legendre on 41 panels of
+ * 1 - cos theta halving toward forward scattering),
  * one C surface per material). */
 typedef enum { CTD_COMPTON_KN = 0, CTD_COMPTON_WH = 1 } ctd_compton_model;
 typedef struct {
@@ -171,7 +172,7 @@ int ctd_set_physics(ctd_ctx *ctx, ctd_phantom ph, const ctd_physics *phys);
  * x = sin(theta/2)/lambda, and a formula unit's F^2 is sum_i count[i] F_Z[i]^2
  * (independent atoms, no interference).  With n_el > 0 the material's Rayleigh
  * total becomes pi r0^2 times the integral over mu of (1 + mu^2) F^2 (composite
- * Simpson, 20000 intervals), divided by a_mol for cm^2/g, and its R surface is
+ * Gauss-Legendre as for the Waller-Hartree total), divided by a_mol for cm^2/g, and its R surface is
  * built from the same density; n_el = 0 restores F^2 = exp(-q^2/q0^2) and the
  * closed-form total.  z: n_el atomic numbers in 1..100; count: atoms per formula
  * unit, finite and > 0; both read during the call.  1 <= n_el <= CTD_MAX_ELEMENTS

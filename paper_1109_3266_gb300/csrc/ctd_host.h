@@ -225,7 +225,7 @@ struct ctd_ctx {
     // they do not depend on the phantom
     std::map<std::vector<double>, std::vector<float>> surfaces;
     // node-table columns of a material by (Compton model, e_min, n_e, its parameters and
-    // elements): the Waller-Hartree and independent-atom totals are Simpson integrals
+    // elements): the Waller-Hartree and independent-atom totals are numeric integrals
     std::map<std::vector<double>, std::vector<double>> columns;
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> lane_done;

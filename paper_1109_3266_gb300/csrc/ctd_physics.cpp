@@ -46,24 +46,63 @@ inline double wh_a(double e_kev, double sq0)
     return sq0 > 0.0 ? (2.0 * kr * kr) / (sq0 * sq0) : 0.0;
 }
 
+// Gauss-Legendre rule of kGaussPoints points on [-1, 1]: the roots of P_n by Newton's
+// iteration from Chebyshev guesses, weights 2 / ((1 - x^2) P_n'(x)^2).
+constexpr int kGaussPoints = 16;
+struct GaussRule {
+    double x[kGaussPoints], w[kGaussPoints];
+    GaussRule()
+    {
+        const int n = kGaussPoints;
+        for (int i = 0; i < n; ++i) {
+            double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = z;   // P_0, P_1, then the recurrence up to P_n
+                for (int k = 2; k <= n; ++k) {
+                    const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = pk;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1.0);
+                const double dz = p1 / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-16) break;
+            }
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+    }
+};
+
+// Integral over mu in [-1, 1] of f(mu), the densities of Eqs. 1-2, whose features sit
+// near mu = 1 (forward scattering, widths down to about 1e-3 in 1 - mu at 150 keV):
+// Gauss-Legendre on panels of t = 1 - mu in [0, 2] halving toward t = 0 (2^-40 for
+// the last), so that every panel is smooth at its own scale.
+template <class F>
+double integrate_forward(const F &f)
+{
+    static const GaussRule g;
+    double sum = 0.0, hi = 2.0;
+    for (int panel = 0; panel <= 40; ++panel) {
+        const double lo = panel == 40 ? 0.0 : 0.5 * hi;
+        const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+        double s = 0.0;
+        for (int i = 0; i < kGaussPoints; ++i) s += g.w[i] * f(1.0 - (mid + half * g.x[i]));
+        sum += half * s;
+        hi = lo;
+    }
+    return sum;
+}
+
 }  // namespace
 
-// Waller-Hartree total per electron in cm^2: pi r0^2 times the composite
-// Simpson integral of Eq. 2 over mu in [-1, 1] on kCdfIntervals intervals.
+// Waller-Hartree total per electron in cm^2: pi r0^2 times the integral of Eq. 2
+// over mu in [-1, 1] (Gauss-Legendre on panels graded toward forward scattering).
 double sigma_wh(double e_kev, double sq0)
 {
-    const int M = kCdfIntervals;
     const double k = e_kev / kMec2;
     const double a = wh_a(e_kev, sq0);
-    double odd = 0.0, even = 0.0;
-    for (int n = 1; n < M; ++n) {
-        const double mu = static_cast<double>(2 * n - M) / static_cast<double>(M);
-        if (n & 1) odd += density_wh(k, a, mu);
-        else even += density_wh(k, a, mu);
-    }
-    const double ends = density_wh(k, a, -1.0) + density_wh(k, a, 1.0);
-    const double integral = ((2.0 / static_cast<double>(M)) / 3.0) * (ends + (4.0 * odd + 2.0 * even));
-    return (kPi * kR0 * kR0) * integral;
+    return (kPi * kR0 * kR0) * integrate_forward([&](double mu) { return density_wh(k, a, mu); });
 }
 
 double mu_compton_wh(const ctd_material &m, double e_kev)
@@ -118,21 +157,13 @@ struct FormFactor {
 }  // namespace
 
 // Rayleigh total per formula unit in cm^2 with the independent-atom form factor:
-// pi r0^2 times the composite Simpson integral of Eq. 1 over mu in [-1, 1].
+// pi r0^2 times the integral of Eq. 1 over mu in [-1, 1] (Gauss-Legendre on panels
+// graded toward forward scattering).
 double sigma_rayleigh_iaa(const Elements &el, double e_kev)
 {
     const FormFactor ff(el);
-    const int M = kCdfIntervals;
     const double kr = e_kev / kHc;
-    double odd = 0.0, even = 0.0;
-    for (int n = 1; n < M; ++n) {
-        const double mu = static_cast<double>(2 * n - M) / static_cast<double>(M);
-        if (n & 1) odd += ff.density(kr, mu);
-        else even += ff.density(kr, mu);
-    }
-    const double ends = ff.density(kr, -1.0) + ff.density(kr, 1.0);
-    const double integral = ((2.0 / static_cast<double>(M)) / 3.0) * (ends + (4.0 * odd + 2.0 * even));
-    return (kPi * kR0 * kR0) * integral;
+    return (kPi * kR0 * kR0) * integrate_forward([&](double mu) { return ff.density(kr, mu); });
 }
 
 double mu_rayleigh_iaa(const ctd_material &m, const Elements &el, double e_kev)

@@ -1,9 +1,9 @@
-"""The library's host physics and host logic equal the oracle's, bit for bit,
-without a GPU.
+"""The library's host physics and host logic against the oracle's, without a GPU.
 
-The two are written separately; they agree because both take the same closed
-forms and integrals in the same order of operations (binary64, the C
-library's functions).  Checked here through the host-only C calls
+The two are written separately.  The closed forms and the surfaces agree bit
+for bit (both take the same expressions and the same cumulative-trapezoid
+construction in binary64); the Waller-Hartree and IAA totals agree to 1e-8,
+the library integrating by Gauss-Legendre and the oracle by Simpson.  Checked here through the host-only C calls
 ctd_material_columns and ctd_angular_surface (node-table columns under both
 Compton models and both Rayleigh form factors; the C and R surfaces of every
 kind), ctd_allocate_histories (the largest-remainder spectrum allocation) and
@@ -38,7 +38,13 @@ def test_material_columns_equal_oracle(ctd, oracle, m, compton, iaa):
     e_min, e_max = 1, 150
     lib = ctd.ctd_material_columns(m, e_min, e_max, compton, m.elements if iaa else ())
     ref = oracle_columns(oracle, m, e_min, e_max, compton, iaa)
-    assert np.array_equal(lib.view(np.uint64), ref.view(np.uint64))
+    if compton == "kn" and not iaa:
+        # closed forms on both sides
+        assert np.array_equal(lib.view(np.uint64), ref.view(np.uint64))
+    else:
+        # the Waller-Hartree and IAA totals: Gauss-Legendre in the library, Simpson in the
+        # oracle (its error is about 5e-9)
+        np.testing.assert_allclose(lib, ref, rtol=1e-8, atol=0)
 
 
 @pytest.mark.parametrize("kind,m,iaa", [("kn", I.WATER, False), ("rayleigh", I.WATER, False),

@@ -108,7 +108,7 @@ def test_waller_hartree_limits(ctd):
 def test_iaa_rayleigh_total_equals_the_closed_form(ctd, m):
     _, _, r = parts(ctd, m, elements=m.elements)
     for e in (5, 20, 60, 100, 150):
-        assert r[at(e)] == pytest.approx(closed_sigma(m, float(e)) * NA / m.a_mol, rel=2e-6)
+        assert r[at(e)] == pytest.approx(closed_sigma(m, float(e)) * NA / m.a_mol, rel=1e-12)
 
 
 # ----------------------------------------------------------------- surfaces

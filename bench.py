@@ -18,7 +18,8 @@ also carries, each measured in this run:
             per batch, against the same requests run one after another;
   served    a Poisson stream of head requests, each stopped at 1 % avg RSD:
             p50/p99 latency and histories/s, continuous batching against one
-            request at a time;
+            request at a time; GPU-filling requests (0.5 cm heads, batches of
+            8e7 histories) and small ones (1 cm heads, batches of 4e6);
   error_vs_fp64_oracle  the device against the binary64 oracle on the CPU
             baseline's sample (the same histories on both sides).
 
@@ -522,17 +523,14 @@ def leg_batched(ctd, args, clk):
                         "graph; shared: one multi-request launch per batch", "clocks": clk.summary(a, b)}
 
 
-def leg_served(ctd, args, clk):
-    """Poisson stream of head requests, each stopped at 1 % avg RSD: continuous
-    batching (every request on its own stream) against one request at a time."""
-    import torch
-
+def served_stream(ctd, args, clk, d, batch, rate, n_req):
+    """One Poisson stream of head requests of d cm voxels, each stopped at 1 %
+    avg RSD in batches of `batch` histories: continuous batching (every request
+    on its own stream) against one request at a time, on the same arrivals."""
     from paper_1109_3266_gb300 import inputs as I, serve
-    torch.cuda.set_device(0)
-    d = args.served_voxel_cm
     nx, ny, nz = int(round(25.6 / d)), int(round(25.6 / d)), int(round(16.0 / d))
     pool = [I.head_phantom(nx, ny, nz, d, seed=3 + k) for k in range(args.pool)]
-    arrivals = I.served_arrivals(args.served_requests, args.rate, seed=5)
+    arrivals = I.served_arrivals(n_req, rate, seed=5)
 
     def make(seed):
         return I.head_request(pool[seed % len(pool)], seed)
@@ -542,10 +540,10 @@ def leg_served(ctd, args, clk):
         ctx = ctd.ctd_create(device=0, multi_blocks_per_sm=args.multi_blocks_per_sm, serve_max_active=max_active,
                              shared_launch=args.shared_launch, serve_round_histories=budget)
         # warm-up: one request alone
-        serve.serve(ctx, [(0.0, 4999)], make, args.batch_histories, 0.01, n_histories_max=40 * args.batch_histories)
+        serve.serve(ctx, [(0.0, 4999)], make, batch, 0.01, n_histories_max=40 * batch)
         a = clk.mark()
-        reqs, wall = serve.serve(ctx, arrivals, make, args.batch_histories, 0.01,
-                                 n_histories_max=40 * args.batch_histories, time_limit_s=args.time_limit)
+        reqs, wall = serve.serve(ctx, arrivals, make, batch, 0.01, n_histories_max=40 * batch,
+                                 time_limit_s=args.time_limit)
         b = clk.mark()
         done = [r for r in reqs if np.isfinite(r.latency)]
         hist = sum(r.histories for r in done)
@@ -555,17 +553,33 @@ def leg_served(ctd, args, clk):
                           round_histories=budget or 1e8, clocks=clk.summary(a, b))
         ctd.ctd_destroy(ctx)
     c, o = out["continuous"], out["one_at_a_time"]
-    return {"workload": "served", "phantom": [nx, ny, nz], "voxel_cm": d, "rate_per_s": args.rate,
-            "requests": args.served_requests, "batch_histories": args.batch_histories, "rsd_target": 0.01,
-            "min_batches": 10, "phantom_pool": args.pool, "p50_s": c["p50_s"], "p99_s": c["p99_s"],
+    return {"phantom": [nx, ny, nz], "voxel_cm": d, "rate_per_s": rate, "requests": n_req, "batch_histories": batch,
+            "rsd_target": 0.01, "min_batches": 10, "phantom_pool": args.pool, "p50_s": c["p50_s"], "p99_s": c["p99_s"],
             "value": c["histories_per_s"], "unit": UNIT,
             "launches": "shared multi-request launch" if args.shared_launch else "one stream per request",
             "continuous": c, "one_at_a_time": o,
             "throughput_vs_one_at_a_time": (c["histories_per_s"] / o["histories_per_s"]) if o["histories_per_s"]
             else None,
-            "stand_in": f"heads of {d} cm voxels instead of the 0.1 cm ones: one 0.1 cm head needs about 1e11 "
-                        "histories to reach 1 % (about 15 s of this GPU), so 4 requests/s would be about 60x over "
-                        "its capacity and every latency would be queueing"}
+            "p50_vs_one_at_a_time": (c["p50_s"] / o["p50_s"]) if c["p50_s"] and o["p50_s"] else None,
+            "p99_vs_one_at_a_time": (c["p99_s"] / o["p99_s"]) if c["p99_s"] and o["p99_s"] else None}
+
+
+def leg_served(ctd, args, clk):
+    """Poisson streams of head requests, each stopped at 1 % avg RSD: continuous
+    batching against one request at a time, for requests whose batches fill the
+    GPU and for small ones."""
+    import torch
+
+    torch.cuda.set_device(0)
+    out = served_stream(ctd, args, clk, args.served_voxel_cm, args.batch_histories, args.rate, args.served_requests)
+    out["workload"] = "served"
+    out["stand_in"] = (f"heads of {args.served_voxel_cm} cm voxels instead of the 0.1 cm ones: one 0.1 cm head needs "
+                       "about 1e11 histories to reach 1 % (about 15 s of this GPU), so 4 requests/s would be about 60x "
+                       "over its capacity and every latency would be queueing")
+    if args.served_small_requests > 0:
+        out["small_requests"] = served_stream(ctd, args, clk, args.served_small_voxel_cm, args.served_small_batch,
+                                              args.served_small_rate, args.served_small_requests)
+    return out
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -729,6 +743,10 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--pool", type=int, default=4)
     ap.add_argument("--served-voxel-cm", type=float, default=0.5)
+    ap.add_argument("--served-small-requests", type=int, default=300, help="served form, small requests (0: none)")
+    ap.add_argument("--served-small-rate", type=float, default=28.0)
+    ap.add_argument("--served-small-voxel-cm", type=float, default=1.0)
+    ap.add_argument("--served-small-batch", type=int, default=4_000_000)
     ap.add_argument("--batch-histories", type=int, default=80_000_000)
     ap.add_argument("--time-limit", type=float, default=120.0)
     ap.add_argument("--multi-blocks-per-sm", type=int, default=0)

@@ -370,10 +370,19 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
  * independently of the others: each call of ctd_serve_step takes in the
  * batches that have finished on the GPU (a batch counts only then), retires
  * requests that reached their stop and requests cancelled, admits what fits
- * and launches the next batch (transport, fold and, from min_batches on, the
- * statistics) of every running request with nothing on the GPU.  It does not
- * wait for the GPU, so requests submitted while others run start at the next
- * call.  With shared_launch = 1 each call runs one round, one batch of every
+ * and launches the next batches (transport, fold and, from min_batches on, the
+ * statistics) of running requests with nothing on the GPU.  It does not wait
+ * for the GPU.  Requests go in order of the histories they still need by
+ * estimate (the batches up to min_batches, then the avg RSD taken to fall as
+ * 1/sqrt(n); the earliest admitted among equals).  The first in line runs on a
+ * stream of the device's greatest priority, every batch before its first stop
+ * test in one go.  If its batches fill the GPU (at least 64 histories per
+ * resident thread of a launch), the second in line runs beside it one slice
+ * (an eighth of a batch) at a time, and only while the first one's batch on the
+ * GPU may be its last; if they do not, the others run, whole batches, while
+ * the histories on the GPU stay below two launches that fill it.  A request
+ * submitted while others run is admitted at the next call and starts there if
+ * it is first in line.  With shared_launch = 1 each call runs one round, one batch of every
  * running request in one shared launch (every request on one node grid), and
  * waits for it; a round whose launches fail counts for no request and marks
  * them CTD_REQ_FAILED.
@@ -419,7 +428,7 @@ int ctd_poll(ctd_ctx *ctx, ctd_req_id id, ctd_req_status *out);
  * passed (CTD_ETIMEOUT); out may be NULL. */
 int ctd_wait(ctd_ctx *ctx, ctd_req_id id, double timeout_s, ctd_req_status *out);
 /* A queued request is dropped at once, a running one at the next
- * ctd_serve_step (after its batch on the GPU, if any, has finished); either
+ * ctd_serve_step (after its batches on the GPU, if any, have finished); either
  * ends as CTD_REQ_CANCELLED. */
 int ctd_cancel(ctd_ctx *ctx, ctd_req_id id);
 

@@ -551,6 +551,7 @@ int ctd_destroy(ctd_ctx *ctx)
     for (auto e : ctx->lane_done) cudaEventDestroy(e);
     if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
     for (auto e : ctx->serve_ev) cudaEventDestroy(e);
+    for (auto e : ctx->serve_ev_pre) cudaEventDestroy(e);
     for (auto l : ctx->serve_hi) cudaStreamDestroy(l);
     if (ctx->serve_res) cudaFreeHost(ctx->serve_res);
     if (ctx->staged) cudaFreeHost(ctx->staged);

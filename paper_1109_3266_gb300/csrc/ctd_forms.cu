@@ -236,7 +236,7 @@ namespace {
 
 double elapsed_since(double t) { return now_s() - t; }
 
-constexpr int kServeSlices = 8;   // launches per batch of a served request that is not the oldest
+constexpr int kServeSlices = 8;   // slices of a batch of a served request not first in line
 
 // Lanes, their events and pinned result slots for served request chains, made
 // once per context.
@@ -259,6 +259,11 @@ int ensure_serve_lanes(ctd_ctx *ctx)
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ctx->serve_ev.push_back(e);
     }
+    while (ctx->serve_ev_pre.size() < static_cast<size_t>(kMaxLanes)) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->serve_ev_pre.push_back(e);
+    }
     if (!ctx->serve_res) {
         if (cudaMallocHost(reinterpret_cast<void **>(&ctx->serve_res), kMaxLanes * 4 * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
@@ -274,6 +279,18 @@ int free_lane(ctd_ctx *ctx)
     for (int i = 0; i < static_cast<int>(ctx->lane_owner.size()); ++i)
         if (ctx->lane_owner[i] == 0) return i;
     return -1;
+}
+
+// A request's tallies, statistics and counters cleared on stream s.
+int clear_run(Phantom &P, cudaStream_t s)
+{
+    const size_t nv = P.nvox;
+    CK(cudaMemsetAsync(P.tally.p, 0, nv * sizeof(double), s));
+    CK(cudaMemsetAsync(P.sum_d.p, 0, nv * sizeof(double), s));
+    CK(cudaMemsetAsync(P.sum_d2.p, 0, nv * sizeof(double), s));
+    CK(cudaMemsetAsync(P.edep.p, 0, nv * sizeof(double), s));
+    CK(cudaMemsetAsync(P.counts.p, 0, sizeof(ctd::DeviceCounts), s));
+    return CTD_OK;
 }
 
 // Admit queued requests in order while memory and slots allow.  Request chains
@@ -310,13 +327,8 @@ int admit(ctd_ctx *ctx, bool chains)
             ctx->pending.erase(ctx->pending.begin());
             continue;
         }
-        const cudaStream_t s = chains ? ctx->lanes[lane_i] : ctx->stream;
-        const size_t nv = P->nvox;
-        CK(cudaMemsetAsync(P->tally.p, 0, nv * sizeof(double), s));
-        CK(cudaMemsetAsync(P->sum_d.p, 0, nv * sizeof(double), s));
-        CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), s));
-        CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), s));
-        CK(cudaMemsetAsync(P->counts.p, 0, sizeof(ctd::DeviceCounts), s));
+        // request chains clear the buffers on the stream of their first launch
+        if (!chains && (rc = clear_run(*P, ctx->stream))) return rc;
         P->have_result = false;
         R.state = CTD_REQ_RUNNING;
         R.t_start = now_s();
@@ -349,46 +361,108 @@ void retire(ctd_ctx *ctx, ServeReq &R, int state)
         }
 }
 
-// The next batch of a running request on its own lane: transport, fold and, from
-// min_batches on, the statistics of the stop test with their copy to the lane's
-// pinned slot; the lane's event marks its end.
-int launch_batch(ctd_ctx *ctx, ServeReq &R, Phantom &P, bool first_in_line)
+// Histories of one launch that fill the GPU: kFillPerLane per resident lane.
+constexpr double kFillPerLane = 64.0;
+
+double fill_histories(const ctd_ctx *ctx)
 {
-    // the oldest running request's batches go to its lane's high-priority stream, so that
-    // its blocks are dispatched first and younger requests fill the SMs its batches leave
-    // idle; a batch starts only after the request's previous one has finished (the host
-    // saw its event), so switching streams keeps the order.  The first batch stays on the
-    // lane's own stream, behind the buffers' clearing.
-    const cudaStream_t s = first_in_line && R.batches > 0 ? ctx->serve_hi[R.lane] : ctx->lanes[R.lane];
+    return kFillPerLane * static_cast<double>(ctx->num_sms) * ctx->blocks_per_sm * ctx->threads;
+}
+
+// The next work of a running request on its own lane: transport, the fold of each
+// batch it completes and, from min_batches on, the statistics of the stop test with
+// their copy to the lane's pinned slot; the lane's event marks its end.
+// The first request in line sends, on its lane's high-priority stream, the rest of
+// a batch it began in slices and every batch before its first stop test at once
+// (nothing is decided between them), one launch each; a second event marks the end
+// of all of them but the last.  Any other request sends one slice (1/kServeSlices of
+// a batch of consecutive histories) of a batch that fills the GPU, or one whole
+// smaller batch, on the lane's own stream: its persistent blocks give the SMs back
+// after a slice, so the first request's blocks, dispatched first, wait at most one
+// slice for them.  Work starts only after the request's previous work has finished
+// (the host saw its event), so switching streams keeps the order.
+int launch_work(ctd_ctx *ctx, ServeReq &R, Phantom &P, bool first_in_line)
+{
+    const cudaStream_t s = first_in_line ? ctx->serve_hi[R.lane] : ctx->lanes[R.lane];
+    int rc;
+    if (R.batches == 0 && R.slice == 0 && (rc = clear_run(P, s))) return rc;
     const uint64_t B = R.req.batch_histories;
+    const uint64_t S = kServeSlices;
+    const uint64_t lo = B * static_cast<uint64_t>(R.slice) / S;   // first history of the first launch
+    uint64_t hi = B;
+    int n = 1;                                                     // batches the launches complete
+    int slice_after = 0;
+    if (first_in_line) {
+        if (R.batches + 1 < R.req.min_batches) n = R.req.min_batches - R.batches;
+    } else if (static_cast<double>(B) >= fill_histories(ctx)) {
+        hi = B * static_cast<uint64_t>(R.slice + 1) / S;
+        n = R.slice + 1 == kServeSlices ? 1 : 0;
+        slice_after = n ? 0 : R.slice + 1;
+    }
     ctd::RequestDesc q;
     fill_request(P, R.req.seed, q);
     q.work = ctx->serve_work.p + R.lane;
     q.pref = P.pref.p + 1 * (q.nbins + 1);    // batches of exactly B histories
-    q.h_base = static_cast<uint64_t>(R.batches) * B;
     q.tally = P.tally.p;
-    // the other requests' batches go out as kServeSlices launches of consecutive history
-    // ranges: their persistent blocks give the SMs back between slices, so the oldest
-    // request's next batch waits at most one slice for them
-    const int slices = first_in_line ? 1 : kServeSlices;
-    for (int i = 0; i < slices; ++i) {
-        q.local_begin = B * static_cast<uint64_t>(i) / slices;
-        q.local_end = B * static_cast<uint64_t>(i + 1) / slices;
-        if (q.local_begin == q.local_end) continue;
-        CK(cudaMemsetAsync(q.work, 0, sizeof(unsigned long long), s));
-        CKS(launch_one(ctx, P, q, s));
-    }
     const double scale = ctd::kKevToJ * 1000.0 / (P.dx * P.dy * P.dz * static_cast<double>(B));
-    CKS(ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, scale, s));
-    R.checked = R.batches + 1 >= R.req.min_batches;
+    double hist = 0.0;
+    for (int j = 0; j < std::max(n, 1); ++j) {
+        q.h_base = static_cast<uint64_t>(R.batches + j) * B;
+        q.local_begin = j == 0 ? lo : 0;
+        q.local_end = j == 0 ? hi : B;
+        if (q.local_begin < q.local_end) {
+            CK(cudaMemsetAsync(q.work, 0, sizeof(unsigned long long), s));
+            CKS(launch_one(ctx, P, q, s));
+            hist += static_cast<double>(q.local_end - q.local_begin);
+        }
+        if (j < n) CKS(ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, scale, s));
+        if (j == n - 2) CK(cudaEventRecord(ctx->serve_ev_pre[R.lane], s));
+    }
+    const int done = R.batches + n;
+    R.checked = n > 0 && done >= R.req.min_batches;
     if (R.checked) {
-        CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, R.batches + 1, P.dose.p, P.sd.p, P.nvox, s));
+        CKS(ctd::launch_finalize(P.sum_d.p, P.sum_d2.p, done, P.dose.p, P.sd.p, P.nvox, s));
         CKS(ctd::launch_rsd(P.dose.p, P.sd.p, P.rho.p, P.nvox, P.partials.p, kRsdParts, P.result.p, s));
         CK(cudaMemcpyAsync(ctx->serve_res + 4 * R.lane, P.result.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     CK(cudaEventRecord(ctx->serve_ev[R.lane], s));
+    R.group = n;
+    R.slice_after = slice_after;
+    R.flight_histories = first_in_line ? static_cast<double>(B) : hist;
+    R.split = n > 1;
     R.in_flight = true;
     return CTD_OK;
+}
+
+// Histories a running request is estimated to still need, counting its batches
+// on the GPU as done: the batches up to min_batches and, once the avg RSD is known,
+// n ((rsd / target)^2 - 1) for the avg RSD falling as 1 / sqrt(n), at least one
+// batch, at most what its history cap leaves.
+double remaining(const ServeReq &R)
+{
+    const double B = static_cast<double>(R.req.batch_histories);
+    const double ran = static_cast<double>(R.histories) + R.group * B;
+    const double cap = static_cast<double>(R.req.n_histories_max);
+    double need = std::max(0, R.req.min_batches - R.batches - R.group) * B;
+    if (R.req.rsd_target == 0.0) {
+        need = std::max(need, cap - ran);   // runs to its cap
+    } else if (R.batches >= R.req.min_batches && R.avg_rsd > 0.0) {
+        const double n = static_cast<double>(R.histories);
+        const double r = R.avg_rsd / R.req.rsd_target;
+        need = std::max(need, n * r * r - ran);
+    }
+    if (R.req.n_histories_max) need = std::min(need, std::max(0.0, cap - ran));
+    return std::max(need, B);
+}
+
+// Whether the first request in line leaves room for the others: not while it has
+// batches on the GPU of which none can be its last; during a batch that may be its
+// last they fill the SMs it leaves idle and the gap until the host sees it end.
+bool first_leaves_room(ctd_ctx *ctx, const ServeReq &F)
+{
+    if (!F.in_flight) return true;
+    if (!F.checked) return false;
+    return !F.split || cudaEventQuery(ctx->serve_ev_pre[F.lane]) != cudaErrorNotReady;
 }
 
 // A request that reached its target or its history cap: total deposit, results
@@ -438,10 +512,13 @@ int serve_chains(ctd_ctx *ctx, bool *progress)
             return fail(CTD_ECUDA, "served request %lld: %s", static_cast<long long>(id), cudaGetErrorString(q));
         }
         moved = true;
-        // the batch is done: only now does it count
+        // the batches are done: only now do they count
         R.in_flight = false;
-        R.batches += 1;
-        R.histories += R.req.batch_histories;
+        R.batches += R.group;
+        R.histories += static_cast<uint64_t>(R.group) * R.req.batch_histories;
+        R.slice = R.slice_after;
+        R.group = 0;
+        R.split = false;
         if (R.checked) {
             R.avg_rsd = ctx->serve_res[4 * R.lane];
             R.sigma_bar = ctx->serve_res[4 * R.lane + 1];
@@ -471,17 +548,46 @@ int serve_chains(ctd_ctx *ctx, bool *progress)
     const size_t before = ctx->active.size();
     if ((rc = admit(ctx, true))) return rc;
     moved = moved || ctx->active.size() != before;
-    const int64_t oldest = ctx->active.empty() ? 0 : ctx->active.front();   // admitted first in, first out
-    for (int64_t id : std::vector<int64_t>(ctx->active)) {
-        ServeReq &R = ctx->sreqs[id];
-        if (R.in_flight) continue;
+    // In order of the estimated histories still needed (the earliest admitted among
+    // equals): the first in line goes out first, so that its blocks are queued ahead of
+    // the others'.  When its batches fill the GPU, only the second in line runs beside
+    // it, and only while the first leaves room; when they do not, the others run while
+    // the histories on the GPU stay below two launches that fill it.
+    std::vector<std::pair<double, int64_t>> by_need;
+    for (int64_t id : ctx->active) by_need.emplace_back(remaining(ctx->sreqs[id]), id);
+    std::stable_sort(by_need.begin(), by_need.end(),
+                     [](const std::pair<double, int64_t> &a, const std::pair<double, int64_t> &b) {
+                         return a.first < b.first;
+                     });
+    auto launch = [&](ServeReq &R, bool first) {
         Phantom *P = find(ctx, R.ph);
-        if (!P || (rc = launch_batch(ctx, R, *P, id == oldest))) {
-            retire(ctx, R, CTD_REQ_FAILED);
-            if (!P) continue;
-            return rc;
+        int code = P ? launch_work(ctx, R, *P, first) : CTD_OK;
+        if (!P || code) retire(ctx, R, CTD_REQ_FAILED);
+        else moved = true;
+        return code;
+    };
+    if (!by_need.empty()) {
+        const int64_t first = by_need.front().second;
+        ServeReq &F = ctx->sreqs[first];
+        if (!F.in_flight && (rc = launch(F, true))) return rc;
+        const bool fills = static_cast<double>(F.req.batch_histories) >= fill_histories(ctx);
+        if (fills) {
+            if (by_need.size() > 1 && first_leaves_room(ctx, F)) {
+                ServeReq &R = ctx->sreqs[by_need[1].second];
+                if (!R.in_flight && (rc = launch(R, false))) return rc;
+            }
+        } else {
+            const double budget = 2.0 * fill_histories(ctx);
+            double on_gpu = 0.0;
+            for (const auto &e : by_need)
+                if (ctx->sreqs[e.second].in_flight) on_gpu += ctx->sreqs[e.second].flight_histories;
+            for (size_t k = 1; k < by_need.size() && on_gpu < budget; ++k) {
+                ServeReq &R = ctx->sreqs[by_need[k].second];
+                if (R.in_flight) continue;
+                if ((rc = launch(R, false))) return rc;
+                on_gpu += R.flight_histories;
+            }
         }
-        moved = true;
     }
     *progress = moved;
     return CTD_OK;

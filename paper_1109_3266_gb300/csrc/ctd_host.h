@@ -171,10 +171,16 @@ struct ServeReq {
     double avg_rsd = 0.0, sigma_bar = 0.0;
     double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
     bool cancel = false;
-    // request chains (shared_launch = 0): the stream slot the request runs on, and
-    // whether a batch of it is on the GPU (with its statistics for the stop test)
+    // request chains (shared_launch = 0): the stream slot the request runs on; the
+    // slices of its current batch done (`slice`); what it has on the GPU: the
+    // batches those launches complete (`group`, the last followed by the stop
+    // test's statistics when `checked`), the slice count after them, their
+    // histories, and whether the lane's second event marks the end of all of them
+    // but the last (`split`)
     int lane = -1;
-    bool in_flight = false, checked = false;
+    int slice = 0, group = 0, slice_after = 0;
+    double flight_histories = 0.0;
+    bool in_flight = false, checked = false, split = false;
 };
 
 constexpr int kRsdParts = 1024;   // partial sums of the statistics reductions
@@ -236,6 +242,7 @@ struct ctd_ctx {
     std::vector<int64_t> lane_owner;
     std::vector<cudaStream_t> serve_hi;   // per lane, a stream of the device's greatest priority
     std::vector<cudaEvent_t> serve_ev;
+    std::vector<cudaEvent_t> serve_ev_pre;   // per lane: every batch in flight but the last done
     double *serve_res = nullptr;
     ctd::host::DevBuf<unsigned long long> serve_work;   // claim counter per lane
 };

@@ -4,9 +4,10 @@ Requests arrive at given times; at each turn of the loop the requests that
 have arrived are created on the device and submitted, and the library's
 scheduler is stepped once: it takes in the batches that have finished on the
 GPU, retires requests at their target avg RSD, admits queued requests by free
-device memory and launches the next batch of every running request, each on
-its own stream (with the context's shared_launch option, one round of every
-running request in one shared launch instead).  Finished requests are read
+device memory and launches the next batches of running requests, each on its
+own stream, the request with the least work left first and at high priority
+(with the context's shared_launch option, one round of every running request
+in one shared launch instead).  Finished requests are read
 back and their phantoms released.  The scheduling and every step of the
 transport run in the CUDA library; this module only drives it and keeps the
 clock.

@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-#define CTD_ABI_VERSION 8
+#define CTD_ABI_VERSION 9
 
 /* largest number of elements of one material's formula unit (ctd_set_material_elements) */
 #define CTD_MAX_ELEMENTS 16
@@ -65,6 +65,13 @@ typedef struct {
                                  its own stream, so that one request's tail overlaps the
                                  next one's launch; 1 runs one multi-request launch per
                                  batch shared by all requests                          */
+    int l2_persist;           /* plain-form transport launches mark the phantom's tally (1)
+                                 or its voxel densities (2) as persisting in L2 (an
+                                 access-policy window over it, with the context's
+                                 persisting-L2 limit raised to its size, at most the
+                                 device's maximum, while the context lives and put back
+                                 by ctd_destroy); -1 or 0
+                                 (the default): neither                                  */
 } ctd_options;
 
 /* Material: the numbers the closed-form cross sections use (Sec. 2.1).
@@ -525,9 +532,8 @@ int ctd_probe_memory(ctd_ctx *ctx, int kind, uint64_t n_slots, uint64_t n_ops, d
 
 /* Allocation-free avg RSD.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need the
- * precision measure, such as code running inside CUDA stream capture (where
- * cudaMalloc is not permitted) or hosts whose own pool allocator owns all
- * device memory and forbids library allocations.
+ * precision measure, such as hosts whose own pool allocator owns all device
+ * memory and forbids library allocations.
  * It reduces dose and stddev arrays that already live on the device (nvox
  * doubles each, Gy per history) with densities density_dev (nvox floats) to
  * the same measures ctd_run reports: result_dev[0] = avg RSD (mean s/D over
@@ -537,10 +543,9 @@ int ctd_probe_memory(ctd_ctx *ctx, int kind, uint64_t n_slots, uint64_t n_ops, d
  * device.  It allocates nothing: its partial sums live in a fixed 160 KB
  * device array inside the library, which every GPU that loads the library
  * holds until exit, so nvox may not exceed 67,108,864 (CTD_EINVAL beyond).
- * Each call made outside stream capture looks up that array's device address
- * on the current device (so a device reset between calls is harmless); a call
- * made during capture uses the address its device's last call found, so make
- * the first call on each device before any stream capture.  All calls share
+ * Each call looks up that array's device address on the current device (so a
+ * device reset between calls is harmless), except on a stream that is being
+ * captured, where the address that device's previous call found is used.  All calls share
  * the array: a call overwrites every partial it reads, but calls that overlap
  * on the GPU race on it. */
 int ctd_avg_rsd_noalloc(const double *dose_dev, const double *stddev_dev, const float *density_dev, size_t nvox,

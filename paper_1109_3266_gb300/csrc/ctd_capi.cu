@@ -395,7 +395,22 @@ int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uin
     if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
     CK(cudaEventRecord(e0, ctx->stream));
     const int grid = ctx->num_sms * ctx->blocks_per_sm;
-    CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream));
+    ctd::L2Window win{};
+    if (ctx->l2_persist) {
+        // the tally's (or the densities') lines stay in L2
+        win.base = ctx->l2_persist == 1 ? static_cast<void *>(tally) : static_cast<void *>(P.rho.p);
+        win.bytes = std::min(P.nvox * (ctx->l2_persist == 1 ? sizeof(double) : sizeof(float)), ctx->l2_window_max);
+        // a set-aside of the window's size, no more: the rest of L2 stays for the other data
+        const size_t want = std::min(win.bytes, ctx->l2_persist_max);
+        if (want != ctx->l2_asked) {
+            ctx->l2_asked = want;
+            CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+            CK(cudaDeviceGetLimit(&ctx->l2_setaside, cudaLimitPersistingL2CacheSize));
+        }
+        win.hit_ratio = static_cast<float>(std::min(1.0, static_cast<double>(ctx->l2_setaside) / win.bytes));
+    }
+    CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream,
+                              ctx->l2_persist ? &win : nullptr));
     CK(cudaEventRecord(e1, ctx->stream));
     return CTD_OK;
 }
@@ -518,6 +533,8 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
         if (opt->chunk > 0) ctx->chunk = opt->chunk;
         if (opt->flight_cap > 0) ctx->flight_cap = opt->flight_cap;
         ctx->shared_launch = opt->shared_launch != 0;
+        ctx->l2_persist = opt->l2_persist > 0 ? opt->l2_persist : 0;
+        if (ctx->l2_persist > 2) return fail(CTD_EINVAL, "l2_persist must be -1, 0, 1 or 2");
     }
     if (ctx->threads % 32 != 0 || ctx->threads > 256) return fail(CTD_EINVAL, "threads_per_block must be a multiple of 32 and at most 256");
     if (ctx->blocks_per_sm > 64 || ctx->multi_blocks_per_sm > 64) return fail(CTD_EINVAL, "blocks_per_sm at most 64");
@@ -526,6 +543,16 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
     if (ctx->device < 0 || ctx->device >= ndev) return fail(CTD_EINVAL, "device %d out of range (%d devices)", ctx->device, ndev);
     CK(cudaSetDevice(ctx->device));
     CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (ctx->l2_persist) {
+        // the largest persisting set-aside the device grants, for this context's lifetime
+        int max_persist = 0, max_window = 0;
+        CK(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device));
+        CK(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device));
+        CK(cudaDeviceGetLimit(&ctx->l2_prev_limit, cudaLimitPersistingL2CacheSize));
+        ctx->l2_persist_max = static_cast<size_t>(std::max(max_persist, 0));
+        ctx->l2_window_max = static_cast<size_t>(std::max(max_window, 0));
+        if (!ctx->l2_persist_max || !ctx->l2_window_max) ctx->l2_persist = 0;
+    }
     if (opt && opt->stream) {
         ctx->stream = static_cast<cudaStream_t>(opt->stream);
     } else {
@@ -544,6 +571,10 @@ int ctd_destroy(ctd_ctx *ctx)
     for (auto l : ctx->lanes) cudaStreamSynchronize(l);
     for (auto l : ctx->serve_hi) cudaStreamSynchronize(l);
     ctx->phantoms.clear();
+    if (ctx->l2_persist) {
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_prev_limit);
+    }
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     for (auto e : ctx->events) cudaEventDestroy(e);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);

@@ -225,6 +225,12 @@ struct ctd_ctx {
     // single-request launches on its own stream (the device overlaps the chains),
     // 1 shares one multi-request launch per batch among all requests
     int shared_launch = 0;
+    // plain-form launches: an L2 access-policy window over the tally (1) or the
+    // voxel densities (2), with a persisting set-aside of its size (granted bytes; at
+    // most the device's maximum), no larger than the device's window; the context's
+    // persisting-L2 limit before, put back on destroy
+    int l2_persist = 0;
+    size_t l2_asked = 0, l2_setaside = 0, l2_persist_max = 0, l2_window_max = 0, l2_prev_limit = 0;
     ctd::host::Staged *staged = nullptr;      // pinned read-back of counts and results
     size_t staged_n = 0;
     // angular surfaces by (kind, q0, e_min, n_e, n_zeta[, the elements' (Z, count) pairs]):

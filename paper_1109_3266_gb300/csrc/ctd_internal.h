@@ -171,8 +171,17 @@ struct LaunchParams {
 // w = binary32 bits of the energy the ending event deposited (keV).
 enum { kEndPe = 0, kEndCutoff, kEndEscaped, kEndMissed, kEndTerminated, kEndAborted };
 
-// launches (ctd_transport.cu / ctd_stats.cu)
-int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream);
+// An L2 access-policy window for a launch: [base, base + bytes) persisting for a
+// share hit_ratio of its lines, the rest as usual.
+struct L2Window {
+    void *base;
+    size_t bytes;
+    float hit_ratio;
+};
+
+// launches (ctd_transport.cu / ctd_stats.cu); win may be null
+int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream,
+                     const L2Window *win = nullptr);
 size_t transport_smem_bytes(const LaunchParams &p, int threads);
 int launch_fold(double *tally, const float *rho, double *sum_d, double *sum_d2, double *edep, size_t nvox,
                 double scale, void *stream);

@@ -1,9 +1,8 @@
 // ctd_noalloc.cu -- an allocation-free variant of the avg-RSD reduction.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// precision measure: code running while a CUDA graph is being captured (where
-// cudaMalloc is not allowed), or hosts that hand all device memory to their
-// own pool allocator and forbid libraries from calling cudaMalloc.  For them,
+// precision measure, such as hosts that hand all device memory to their own
+// pool allocator and forbid libraries from calling cudaMalloc.  For them,
 // ctd_avg_rsd_noalloc reduces dose and stddev arrays that already live on the
 // device, using per-block partial sums kept in a fixed file-scope device array
 // instead of library-allocated scratch.

@@ -17,6 +17,8 @@
 // in the kernel's parameter space; and many requests at once, without or with
 // maps (blocks walk through a request table, one request at a time, its
 // descriptor and tables in shared memory).
+#include <cstring>
+
 #include "ctd_device.cuh"
 
 namespace ctd {
@@ -663,24 +665,46 @@ __global__ void eval_math_kernel(int fn, const float *x, float *out, size_t n)
 }
 
 template <int kMaxThreads, int kMinBlocks, int kForm, bool kTrace = false>
-int launch_t(const LaunchParams &p, int grid, int block, size_t smem, cudaStream_t stream)
+int launch_t(const LaunchParams &p, int grid, int block, size_t smem, cudaStream_t stream,
+             const L2Window *win = nullptr)
 {
     auto *k = transport_kernel<kMaxThreads, kMinBlocks, kForm, kTrace>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
             return CTD_ECUDA;
     }
-    k<<<grid, block, smem, stream>>>(p);
+    if (!win) {
+        k<<<grid, block, smem, stream>>>(p);
+        return cudaGetLastError() == cudaSuccess ? CTD_OK : CTD_ECUDA;
+    }
+    cudaLaunchAttribute attr;
+    std::memset(&attr, 0, sizeof(attr));
+    attr.id = cudaLaunchAttributeAccessPolicyWindow;
+    attr.val.accessPolicyWindow.base_ptr = win->base;
+    attr.val.accessPolicyWindow.num_bytes = win->bytes;
+    attr.val.accessPolicyWindow.hitRatio = win->hit_ratio;
+    attr.val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr.val.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k, p) != cudaSuccess) return CTD_ECUDA;
     return cudaGetLastError() == cudaSuccess ? CTD_OK : CTD_ECUDA;
 }
 
 template <int kForm>
-int launch_m(const LaunchParams &p, int grid, int block, int threads_per_sm, size_t smem, cudaStream_t s)
+int launch_m(const LaunchParams &p, int grid, int block, int threads_per_sm, size_t smem, cudaStream_t s,
+             const L2Window *win)
 {
     // the register budget follows the residency asked for (65536 registers per SM)
-    if (block <= 128 && threads_per_sm >= 896) return launch_t<128, 7, kForm>(p, grid, block, smem, s);
-    if (threads_per_sm >= 1024) return launch_t<256, 4, kForm>(p, grid, block, smem, s);
-    return launch_t<256, 3, kForm>(p, grid, block, smem, s);
+    if (block <= 128 && threads_per_sm >= 896) return launch_t<128, 7, kForm>(p, grid, block, smem, s, win);
+    if (threads_per_sm >= 1024) return launch_t<256, 4, kForm>(p, grid, block, smem, s, win);
+    return launch_t<256, 3, kForm>(p, grid, block, smem, s, win);
 }
 
 }  // namespace
@@ -697,7 +721,8 @@ constexpr int kMaxGrid = 1 << 16;
 
 // Kernel variants by residency: 4 blocks of 256 threads per SM cap it at 64
 // registers, 7 blocks of 128 at 73, fewer at 85.
-int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream)
+int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream,
+                     const L2Window *win)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grid <= 0 || grid > kMaxGrid || block <= 0 || block > 256 || block % 32 != 0) {
@@ -714,10 +739,10 @@ int launch_transport(const LaunchParams &p, int grid, int block, int threads_per
         return p.one.fl_n > 0 ? launch_t<256, 4, 1, true>(p, grid, block, smem, s)
                               : launch_t<256, 4, 0, true>(p, grid, block, smem, s);
     }
-    if (p.n_req > 0) return p.any_fluence ? launch_m<3>(p, grid, block, threads_per_sm, smem, s)
-                                           : launch_m<2>(p, grid, block, threads_per_sm, smem, s);
-    return p.one.fl_n > 0 ? launch_m<1>(p, grid, block, threads_per_sm, smem, s)
-                          : launch_m<0>(p, grid, block, threads_per_sm, smem, s);
+    if (p.n_req > 0) return p.any_fluence ? launch_m<3>(p, grid, block, threads_per_sm, smem, s, win)
+                                           : launch_m<2>(p, grid, block, threads_per_sm, smem, s, win);
+    return p.one.fl_n > 0 ? launch_m<1>(p, grid, block, threads_per_sm, smem, s, win)
+                          : launch_m<0>(p, grid, block, threads_per_sm, smem, s, win);
 }
 
 int launch_sample_mu(const float *surf, int n_zeta, int n_e, int e_min, float e, uint64_t seed, uint64_t n,

@@ -45,7 +45,7 @@ def test_calls_fail_cleanly_without_a_device():
     rc = ctd.lib().ctd_create(ctypes.byref(h), None)
     assert rc == 3 and not h.value
     assert ctd.lib().ctd_last_error()
-    assert ctd.lib().ctd_abi_version() == 8
+    assert ctd.lib().ctd_abi_version() == 9
 
 
 def test_kramers_helper_matches_the_input_recipe():

@@ -179,6 +179,37 @@ def test_served_requests_join_while_others_are_on_the_gpu(ctd):
     ctd.ctd_destroy(c)
 
 
+def test_l2_persisting_tally_gives_the_same_results(ctd, ctx):
+    # the access-policy window changes only what L2 keeps
+    p = problems()[0]
+    c = ctd.ctd_create(device=0, l2_persist=1)
+    try:
+        same(alone(ctd, ctx, p), alone(ctd, c, p))
+    finally:
+        ctd.ctd_destroy(c)
+
+
+def test_served_gpu_filling_requests_equal_plain_runs(ctd):
+    # batches of 1.2e7 histories fill the GPU (64 histories per resident thread): the
+    # first in line runs its batches before the first stop test in one step at high
+    # priority, the second fills its last batch one slice (an eighth) at a time and,
+    # once first, resumes the batch it began in slices; results stay those of plain runs
+    c = ctd.ctd_create(device=0, serve_round_histories=1e12)
+    B = 12_000_000
+    ps = [I.scaled(problems()[3], seed=41), I.scaled(problems()[3], seed=42), I.scaled(problems()[1], seed=43)]
+    hs = [ctd.load_problem(c, p) for p in ps]
+    ids = [ctd.ctd_submit(c, hs[i], B, 0.5, ps[i].seed, n_histories_max=6 * B, min_batches=3) for i in range(3)]
+    for i in ids:
+        assert ctd.ctd_wait(c, i, 120.0)["state"] == ctd.REQ_DONE
+    for i, p in enumerate(ps):
+        st = ctd.ctd_poll(c, ids[i])
+        k = st["batches"]
+        assert k >= 3 and st["histories"] == k * B
+        same(alone(ctd, c, p, n=k * B, nb=k), ctd.ctd_get_dose_and_stddev(c, hs[i], p.phantom.nvox))
+        ctd.ctd_destroy_phantom(c, hs[i])
+    ctd.ctd_destroy(c)
+
+
 def test_serve_loop_reports_latency(ctd, ctx):
     from paper_1109_3266_gb300 import serve
 

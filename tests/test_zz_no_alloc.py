@@ -1,6 +1,6 @@
 """ctd_avg_rsd_noalloc: the avg-RSD reduction for callers that cannot allocate
-device memory when they need it (code inside CUDA stream capture, or hosts
-whose own pool allocator owns all device memory).  It keeps its partial sums in
+device memory when they need it (such as hosts whose own pool allocator owns
+all device memory).  It keeps its partial sums in
 a fixed device array inside the library instead of allocating scratch.  Its
 results must equal those ctd_run reports through the allocating path, on two
 calls in a row and for two different inputs, and sizes beyond the array's

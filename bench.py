@@ -56,13 +56,13 @@ FLUSH_BYTES = 256 * 1024 * 1024
 # (smsp__thread_inst_executed / histories) and DRAM bytes per launch
 # (dram__bytes_read + dram__bytes_write); they are not measured in this run.
 KERNEL_PROFILE = {
-    "cbct_water": {"lane_inst_per_history": 2088.0, "dram_bytes_per_launch": 9.16e9, "histories_per_launch": 1e8,
+    "cbct_water": {"lane_inst_per_history": 2088.0, "dram_bytes_per_launch": 4.345e9, "histories_per_launch": 1e8,
                    "capture": "ncu --set full --clock-control none of one transport_kernel<256,4,0,0> launch of 1e8 "
-                              "CBCT-water histories (fast-math kernel): 8.69e9 warp instructions x 24.03 lanes; "
-                              "DRAM 5.63 + 3.54 GB"},
-    "head": {"lane_inst_per_history": 2440.0, "dram_bytes_per_launch": 14.71e9, "histories_per_launch": 2e8,
+                              "CBCT-water histories (packed-voxel kernel): 8.688e9 warp instructions x 24.03 lanes; "
+                              "DRAM 1.91 + 2.43 GB"},
+    "head": {"lane_inst_per_history": 2450.0, "dram_bytes_per_launch": 4.465e9, "histories_per_launch": 2e8,
              "capture": "ncu --set full --clock-control none of one transport_kernel<256,4,0,0> launch of 2e8 head "
-                        "histories (fast-math kernel): 2.646e10 warp instructions x 18.44 lanes; DRAM 9.54 + 5.17 GB"},
+                        "histories (packed-voxel kernel): 2.656e10 warp instructions x 18.45 lanes; DRAM 2.53 + 1.94 GB"},
 }
 
 
@@ -312,23 +312,24 @@ def rsd_stopped(ctd, ctx, h, p, seed, rsd, sec_run):
 
 def memory_probes(ctd, ctx, nvox):
     """Memory ceilings measured on this GPU by the library's probes over as many slots
-    as the phantom has voxels: binary64 reductions into random tally slots, random
-    voxel (material + density) gathers, random 4-byte gathers."""
+    as the phantom has voxels: binary64 reductions into random tally slots and random
+    4-byte gathers (a Woodcock step fetches its voxel's packed 4-byte word)."""
     n_ops = 1 << 31
     return {"l2_red_per_s": ctd.ctd_probe_memory(ctx, ctd.PROBE_L2_RED, nvox, n_ops),
-            "voxel_gather_per_s": ctd.ctd_probe_memory(ctx, ctd.PROBE_VOXEL, nvox, n_ops),
             "gather4_per_s": ctd.ctd_probe_memory(ctx, ctd.PROBE_GATHER4, nvox, n_ops),
             "probe": f"{n_ops} operations on uniform random slots of {nvox} voxels "
-                     f"({nvox * 8 / 1e6:.0f} MB binary64 tally, {nvox * 5 / 1e6:.0f} MB voxels), "
+                     f"({nvox * 8 / 1e6:.0f} MB binary64 tally, {nvox * 4 / 1e6:.0f} MB packed voxel words), "
                      f"mean of 3 launches after 1"}
 
 
 def roofline(p, run, peaks, peak_kind, probes, prof):
     """The transport kernel against its ceilings.  frac: the algorithmic bytes of a
-    history -- 5 B per Woodcock step (material byte + binary32 density) and 8 B per
-    deposit (a binary64 reduction) -- over one launch's histories and its average
-    launch time, against the measured HBM copy bandwidth.  Beside it the L2-reduction
-    and voxel-gather fractions of the probes' ceilings, and the SM-issue fraction."""
+    history -- 5 B per Woodcock step (material byte + binary32 density, which the
+    kernel reads as one packed 4-byte word) and 8 B per deposit (a binary64
+    reduction) -- over one launch's histories and its average launch time, against
+    the measured HBM copy bandwidth.  Beside it the L2-reduction and voxel-gather
+    (4-byte gather probe) fractions of the probes' ceilings, and the SM-issue
+    fraction."""
     st = run["stats"]
     n = st["histories"]
     launches = max(run["launches"], 1)
@@ -351,8 +352,8 @@ def roofline(p, run, peaks, peak_kind, probes, prof):
     if probes:
         out["l2_reduction"] = {"achieved_per_s": hist_s * dep_h, "peak_per_s": probes["l2_red_per_s"],
                                "frac": hist_s * dep_h / probes["l2_red_per_s"]}
-        out["voxel_gather"] = {"achieved_per_s": hist_s * steps_h, "peak_per_s": probes["voxel_gather_per_s"],
-                               "frac": hist_s * steps_h / probes["voxel_gather_per_s"]}
+        out["voxel_gather"] = {"achieved_per_s": hist_s * steps_h, "peak_per_s": probes["gather4_per_s"],
+                               "frac": hist_s * steps_h / probes["gather4_per_s"]}
         out["probe"] = probes["probe"]
     mhz = peaks.get("sm_max_mhz", 2070.0)
     ipeak = SM_COUNT * LANES_PER_SM_CLK * mhz * 1e6 / 1e12

@@ -161,7 +161,9 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt);
 int ctd_destroy(ctd_ctx *ctx);
 
 /* Voxel phantom (Sec. 2.2.1): nx*ny*nz voxels of dx*dy*dz cm centred at the
- * origin; mat[v] < n_mat indexes mats; density[v] >= 0 (g/cm^3).  Host arrays;
+ * origin; mat[v] < n_mat indexes mats; density[v] is 0 or in [2^-18, 2^13)
+ * g/cm^3 (the device keeps each voxel's material and density in one 32-bit word,
+ * exact over that range; other values give CTD_EINVAL).  Host arrays;
  * the library copies them to the device and keeps them resident until
  * ctd_destroy_phantom.  Default physics: nodes 1..150 keV, n_zeta 1024, scale 1,
  * full transport.  Fewer than 2^32 voxels (CTD_EINVAL otherwise). */
@@ -516,10 +518,11 @@ int ctd_eval_math(ctd_ctx *ctx, int fn, const float *x, float *out, size_t n);
  *        deposit instruction) of 1.0 into uniformly random slots of a buffer of
  *        n_slots doubles;
  *   kind CTD_PROBE_GATHER4 (1): gathers of 4-byte records from uniformly random
- *        slots of a buffer of n_slots floats;
+ *        slots of a buffer of n_slots floats (the Woodcock step's fetch of its
+ *        voxel's packed material-and-density word);
  *   kind CTD_PROBE_VOXEL (2): gathers of one voxel's material byte and 4-byte
- *        density from uniformly random slots of n_slots voxels (the Woodcock
- *        step's fetch).
+ *        density from two arrays, uniformly random slots of n_slots voxels (the
+ *        fetch a step would make without the packed word).
  * About n_ops operations (rounded up to whole rounds of 8 per thread over
  * SMs x 8 blocks of 256 threads) run in one launch, timed with CUDA events on
  * the context's stream after one untimed launch; *ops_per_s receives the mean

@@ -221,8 +221,8 @@ int check_ready(Phantom &P)
 void fill_request(Phantom &P, uint64_t seed, ctd::RequestDesc &q)
 {
     std::memset(&q, 0, sizeof(q));
-    q.mat = P.mat.p;
-    q.rho = P.rho.p;
+    q.vox = P.vox.p;
+    q.unused = nullptr;
     q.tab = P.tab.p;
     q.mmax = P.mm.p;
     q.rsurf = P.rs.p;
@@ -623,20 +623,22 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     P->phys.mode = CTD_MODE_FULL;
     P->phys.max_real = 0;
     P->phys.compton_model = CTD_COMPTON_KN;
-    if ((rc = P->mat.ensure(nvox)) || (rc = P->rho.ensure(nvox))) return rc;
+    if ((rc = P->mat.ensure(nvox)) || (rc = P->rho.ensure(nvox)) || (rc = P->vox.ensure(nvox))) return rc;
     CK(cudaMemcpyAsync(P->mat.p, mat, nvox, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(P->rho.p, density, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     // range checks, materials present and their largest densities, on the device
     DevBuf<ctd::PhantomScan> scan;
     if ((rc = scan.ensure(1))) return rc;
-    CKS(ctd::launch_scan_phantom(P->mat.p, P->rho.p, nvox, n_mat, scan.p, ctx->stream));
+    CKS(ctd::launch_scan_phantom(P->mat.p, P->rho.p, nvox, n_mat, P->vox.p, scan.p, ctx->stream));
     ctd::PhantomScan sc{};
     CK(cudaMemcpyAsync(&sc, scan.p, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (sc.first_bad_mat != ~0ull && sc.first_bad_mat <= sc.first_bad_rho)
         return fail(CTD_EINVAL, "voxel %llu has material %d >= n_mat", sc.first_bad_mat,
                     static_cast<int>(mat[sc.first_bad_mat]));
-    if (sc.first_bad_rho != ~0ull) return fail(CTD_EINVAL, "voxel %llu has an invalid density", sc.first_bad_rho);
+    if (sc.first_bad_rho != ~0ull)
+        return fail(CTD_EINVAL, "voxel %llu has density %g: densities must be 0 or in [2^-18, 2^13) g/cm^3",
+                    sc.first_bad_rho, static_cast<double>(density[sc.first_bad_rho]));
     for (int m = 0; m < n_mat; ++m) {
         P->present[m] = static_cast<int>(sc.present_mask >> m & 1u);
         float r;

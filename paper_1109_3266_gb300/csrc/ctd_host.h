@@ -115,6 +115,7 @@ struct Phantom {
 
     DevBuf<uint8_t> mat;
     DevBuf<float> rho;
+    DevBuf<uint32_t> vox;      // material and density packed (what the transport reads)
     // tables
     bool tables_ok = false;
     int n_e = 0;
@@ -148,6 +149,7 @@ struct Phantom {
         for (DevBuf<float> *b : {&rho, &tab, &mm, &cs, &rs, &bins, &proj}) b->cache = c;
         for (DevBuf<double> *b : {&tally, &sum_d, &sum_d2, &edep, &dose, &sd, &partials, &result}) b->cache = c;
         mat.cache = c;
+        vox.cache = c;
         counts.cache = c;
         work.cache = c;
         pref.cache = c;

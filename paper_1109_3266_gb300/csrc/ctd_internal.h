@@ -88,8 +88,8 @@ enum { kCntPe = 0, kCntCompton, kCntRayleigh, kCntFict, kCntEscaped, kCntMissed,
 // array of them in device memory, and each block copies the entry of the
 // request it is working on into shared memory.
 struct alignas(16) RequestDesc {
-    const uint8_t *mat;          // [nvox] material of the phantom
-    const float *rho;            // [nvox] g/cm^3
+    const uint32_t *vox;         // [nvox] material and density of each voxel, one word (kRhoExpBias)
+    const void *unused;          // keeps the descriptor a whole number of 16-byte words
     const float *tab;            // [n_mat][n_e][4]: c1, c2, c3 (cm^2/g), c3[j+1] - c3[j] in binary32
     const float *mmax;           // [n_e] majorant mu_max(E), 1/cm
     // R and C surfaces as cells of 4 floats, [n_e - 1][n_zeta - 1] per surface: cell (j, i)
@@ -132,18 +132,26 @@ static_assert(sizeof(RequestDesc) % 16 == 0, "RequestDesc must be a whole number
 
 constexpr int kMaxPhantomMaterials = 16;
 
-// What a phantom's voxels hold, found on the device when the phantom is created:
-// the first voxel whose material index is out of range and the first whose
-// density is not a finite number >= 0 (~0 if none), which materials occur, and the
-// largest density of each (binary32 bit patterns, which order like the values
-// for non-negative numbers).
+// A voxel's material and density in one 32-bit word, so that a Woodcock step
+// makes one gather: the material index in bits 28-31, the density's binary32
+// biased exponent less kRhoExpBias in bits 23-27 and its significand in bits
+// 0-22; the word's low 28 bits are 0 for density 0.  Exact for densities 0 and
+// [2^-18, 2^13) g/cm^3 (biased exponents 109..139).
+constexpr uint32_t kRhoExpBias = 108;
+constexpr uint32_t kRhoExpLo = 109, kRhoExpHi = 139;
+
+// What a phantom's voxels hold, found on the device when the phantom is created
+// (which also packs each voxel's word): the first voxel whose material index is
+// out of range and the first whose density is neither 0 nor in [2^-18, 2^13) g/cm^3
+// (~0 if none), which materials occur, and the largest density of each (binary32
+// bit patterns, which order like the values for non-negative numbers).
 struct PhantomScan {
     unsigned long long first_bad_mat, first_bad_rho;
     unsigned int present_mask;
     unsigned int max_bits[kMaxPhantomMaterials];
 };
-int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, PhantomScan *out,
-                        void *stream);
+int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, uint32_t *vox,
+                        PhantomScan *out, void *stream);
 
 // What every request of a launch shares: the node grid and the C surface.
 struct SharedTables {

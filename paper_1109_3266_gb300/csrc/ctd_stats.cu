@@ -188,7 +188,7 @@ __global__ void sum_final_kernel(const double *partials, int n_parts, double *re
 // per-material presence and largest density, reduced in shared memory, then one
 // global atomic per block and quantity.  -0 densities count as +0.
 __global__ void scan_phantom_kernel(const uint8_t *__restrict__ mat, const float *__restrict__ rho, size_t nvox,
-                                    int n_mat, PhantomScan *out)
+                                    int n_mat, uint32_t *__restrict__ vox, PhantomScan *out)
 {
     __shared__ unsigned int s_max[kMaxPhantomMaterials];
     __shared__ unsigned int s_mask;
@@ -208,11 +208,14 @@ __global__ void scan_phantom_kernel(const uint8_t *__restrict__ mat, const float
             atomicMin(&s_bad_mat, static_cast<unsigned long long>(v));
             continue;
         }
-        if (!(r >= 0.0f) || !isfinite(r)) {
+        const uint32_t f = __float_as_uint(r + 0.0f);   // -0 as +0
+        const uint32_t ex = f >> 23;
+        if (!(r >= 0.0f) || (f != 0u && (ex < kRhoExpLo || ex > kRhoExpHi))) {
             atomicMin(&s_bad_rho, static_cast<unsigned long long>(v));
             continue;
         }
-        atomicMax(&s_max[m], __float_as_uint(r + 0.0f));
+        vox[v] = (static_cast<uint32_t>(m) << 28) | (f ? f - (kRhoExpBias << 23) : 0u);
+        atomicMax(&s_max[m], f);
         atomicOr(&s_mask, 1u << m);
     }
     __syncthreads();
@@ -272,15 +275,15 @@ int launch_rsd(const double *dose, const double *sd, const float *rho, size_t nv
     return ok();
 }
 
-int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, PhantomScan *out,
-                        void *stream)
+int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, uint32_t *vox,
+                        PhantomScan *out, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PhantomScan init{};
     init.first_bad_mat = ~0ull;
     init.first_bad_rho = ~0ull;
     if (cudaMemcpyAsync(out, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess) return CTD_ECUDA;
-    scan_phantom_kernel<<<grid_for(nvox), kThreads, 0, s>>>(mat, rho, nvox, n_mat, out);
+    scan_phantom_kernel<<<grid_for(nvox), kThreads, 0, s>>>(mat, rho, nvox, n_mat, vox, out);
     return ok();
 }
 

@@ -326,8 +326,11 @@ __device__ __forceinline__ int flight(const SharedTables &sh, const RequestDesc 
                          static_cast<uint32_t>(q.nx) *
                              (static_cast<uint32_t>(static_cast<int>(fy)) +
                               static_cast<uint32_t>(q.ny) * static_cast<uint32_t>(static_cast<int>(fz)));
-    const int m = __ldg(&q.mat[idx]);
-    const float rho = __ldg(&q.rho[idx]);
+    // one gather: the material in the top 4 bits, the density's exponent rebased
+    const uint32_t w = __ldg(&q.vox[idx]);
+    const int m = static_cast<int>(w >> 28);
+    const uint32_t rb = w & 0x0fffffffu;
+    const float rho = rb ? __uint_as_float(rb + (kRhoExpBias << 23)) : 0.0f;
     // interaction type with probabilities mu_i / mu_max: fictitious when u1 is at or
     // above the total share; otherwise the first cumulative share above u1.  The
     // table's fourth column is the total share's node difference, so a fictitious

@@ -262,14 +262,20 @@ def test_phantom_checks_on_the_device(ctd, ctx):
     m1 = mat.copy()
     m1[[100_000, 20_000]] = [2, 7]
     assert "voxel 20000 has material 7" in msg(m1, rho)
-    for bad in (np.nan, np.inf, -1.0, -1e-30):
+    # densities travel packed with the material in one word: 0 or [2^-18, 2^13) g/cm^3
+    below, top = np.float32(2.0 ** -18), np.float32(2.0 ** 13)
+    for bad in (np.nan, np.inf, -1.0, -1e-30, np.nextafter(below, np.float32(0)), 1e-6, top, 1e30):
         r1 = rho.copy()
         r1[[99_999, 5_001]] = bad
-        assert "voxel 5001 has an invalid density" in msg(mat, r1)
+        assert "voxel 5001 has density" in msg(mat, r1)
+    for good in (below, np.nextafter(top, np.float32(0)), 0.0, 1e-5, 5000.0):
+        r1 = rho.copy()
+        r1[[99_999, 5_001]] = good
+        ctd.ctd_destroy_phantom(ctx, make(mat, r1))
     r1 = rho.copy()
     r1[4_000] = np.nan
     assert "voxel 3000 has material" in msg(np.where(np.arange(mat.size) == 3000, 5, mat).astype(np.uint8), r1)
-    assert "voxel 4000 has an invalid density" in msg(np.where(np.arange(mat.size) == 5000, 5, mat).astype(np.uint8), r1)
+    assert "voxel 4000 has density" in msg(np.where(np.arange(mat.size) == 5000, 5, mat).astype(np.uint8), r1)
     # -0 is a valid density
     m2 = mat.copy()
     m2[:10] = 1

@@ -69,6 +69,21 @@ SMALL = {
 }
 
 
+def test_densities_across_the_packed_word_history_by_history(ctd, ctx, oracle):
+    # a voxel's material and density reach the device as one 32-bit word: densities
+    # log-uniform over [2^-18, 16] g/cm^3, zeros and the smallest exact value decode exactly
+    p = I.cbct_water(n_hist=100_000, seed=5, shape=(48, 48, 24), d=0.8)
+    rng = np.random.default_rng(11)
+    rho = np.exp2(rng.uniform(-18.0, 4.0, size=p.phantom.rho.shape)).astype(np.float32)
+    flat = rho.reshape(-1)
+    flat[::97] = 0.0
+    flat[1::97] = 2.0 ** -18
+    p = dataclasses.replace(p, phantom=dataclasses.replace(p.phantom, rho=rho))
+    dev, = device_tracks(ctd, ctx, p, [(0, p.n_hist)])
+    ref, = oracle_tracks(oracle, p, [(0, p.n_hist)])
+    assert_consistent(dev, ref)
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_primary_only_history_by_history(ctd, ctx, oracle, name):
     p = SMALL[name]()

@@ -431,7 +431,7 @@ def leg_head(ctd, args, stream, flush, peaks, peak_kind, clk):
     p = workload("head", args.compton, args.rayleigh)
     ctx = ctd.ctd_create(device=0, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
                          threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap,
-                         l2_persist=args.l2_persist)
+                         l2_persist=args.l2_persist, plain_overlap=args.plain_overlap)
     h = ctd.load_problem(ctx, p)
     run = timed_runs(ctd, ctx, h, p, p.seed, args.head_steps, 2, 0.0, stream, flush, torch.cuda.synchronize, clk)
     st = run["stats"]
@@ -648,7 +648,7 @@ def run_ours(args):
     nvox = p.phantom.nvox
     ctx = ctd.ctd_create(device=local, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
                          threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap,
-                         l2_persist=args.l2_persist)
+                         l2_persist=args.l2_persist, plain_overlap=args.plain_overlap)
     h = ctd.load_problem(ctx, p)
     run = timed_runs(ctd, ctx, h, p, p.seed, args.steps, args.warmup, args.ramp_seconds, stream, flush, sync, clk)
     st = run["stats"]
@@ -735,7 +735,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--flight-cap", type=int, default=0)
-    ap.add_argument("--l2-persist", type=int, default=0, help="plain form: tally persisting in L2 (1 on, -1 off)")
+    ap.add_argument("--l2-persist", type=int, default=0, help="plain form: tally (1) or densities (2) persisting in L2")
+    ap.add_argument("--plain-overlap", type=int, default=0, help="plain form: batches on two streams (1; 0 or -1: one stream)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -72,6 +72,13 @@ typedef struct {
                                  device's maximum, while the context lives and put back
                                  by ctd_destroy); -1 or 0
                                  (the default): neither                                  */
+    int plain_overlap;        /* ctd_run: 1 alternates the batches between the context's stream
+                                 and a second stream of its own, each with its own tally,
+                                 so that one batch's launch starts while the previous one's
+                                 last blocks drain (folds stay in batch order); its launches
+                                 then overlap, so each one's event-timed duration includes
+                                 its neighbours'.  0 (default) or -1: every batch on the
+                                 context's stream                                        */
 } ctd_options;
 
 /* Material: the numbers the closed-form cross sections use (Sec. 2.1).

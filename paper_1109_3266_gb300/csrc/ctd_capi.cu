@@ -201,7 +201,7 @@ int ensure_run_buffers(Phantom &P)
     if ((rc = P.tally.ensure(P.nvox)) || (rc = P.sum_d.ensure(P.nvox)) || (rc = P.sum_d2.ensure(P.nvox)) ||
         (rc = P.edep.ensure(P.nvox)) || (rc = P.dose.ensure(P.nvox)) || (rc = P.sd.ensure(P.nvox)) ||
         (rc = P.partials.ensure(6 * kRsdParts)) || (rc = P.result.ensure(8)) || (rc = P.counts.ensure(1)) ||
-        (rc = P.work.ensure(1)))
+        (rc = P.work.ensure(2)))
         return rc;
     return CTD_OK;
 }
@@ -346,6 +346,15 @@ int join_lanes(ctd_ctx *ctx, cudaStream_t origin, int n)
 
 cudaStream_t lane(ctd_ctx *ctx, int r) { return ctx->lanes[r % kMaxLanes]; }
 
+// The second stream, its events and the phantom's second tally of an overlapped plain run.
+int ensure_plain_aux(ctd_ctx *ctx, Phantom &P)
+{
+    if (!ctx->plain_aux) CK(cudaStreamCreateWithFlags(&ctx->plain_aux, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&ctx->plain_fork, &ctx->plain_fold[0], &ctx->plain_fold[1]})
+        if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return P.tally2.ensure(P.nvox);
+}
+
 // One single-request launch of q (its tables from P) on stream s, at the
 // context's launch shape.
 int launch_one(ctd_ctx *ctx, Phantom &P, const ctd::RequestDesc &q, cudaStream_t s)
@@ -373,8 +382,11 @@ int finish_stats(Phantom &P, int nb, cudaStream_t s)
 
 // One transport launch over local histories [lb, le) of a batch starting at global h_base.
 int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uint64_t h_base, uint64_t lb,
-              uint64_t le, double *tally, size_t ev_index, uint4 *trace, uint64_t trace_h0, uint64_t trace_n)
+              uint64_t le, double *tally, size_t ev_index, uint4 *trace, uint64_t trace_h0, uint64_t trace_n,
+              cudaStream_t s, unsigned long long *work)
 {
+    if (!s) s = ctx->stream;
+    if (!work) work = P.work.p;
     ctd::LaunchParams L;
     std::memset(&L, 0, sizeof(L));
     L.trace = trace;
@@ -386,14 +398,14 @@ int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uin
     q.local_begin = lb;
     q.local_end = le;
     q.tally = tally;
-    q.work = P.work.p;
+    q.work = work;
     L.one = q;
     L.chunk = ctx->chunk;
     L.flight_cap = ctx->flight_cap;
-    CK(cudaMemsetAsync(P.work.p, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     cudaEvent_t e0 = event_at(ctx, 2 * ev_index), e1 = event_at(ctx, 2 * ev_index + 1);
     if (!e0 || !e1) return fail(CTD_ECUDA, "cudaEventCreate failed");
-    CK(cudaEventRecord(e0, ctx->stream));
+    CK(cudaEventRecord(e0, s));
     const int grid = ctx->num_sms * ctx->blocks_per_sm;
     ctd::L2Window win{};
     if (ctx->l2_persist) {
@@ -409,9 +421,9 @@ int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uin
         }
         win.hit_ratio = static_cast<float>(std::min(1.0, static_cast<double>(ctx->l2_setaside) / win.bytes));
     }
-    CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, ctx->stream,
+    CKS(ctd::launch_transport(L, grid, ctx->threads, ctx->threads * ctx->blocks_per_sm, s,
                               ctx->l2_persist ? &win : nullptr));
-    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventRecord(e1, s));
     return CTD_OK;
 }
 
@@ -534,6 +546,7 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
         if (opt->flight_cap > 0) ctx->flight_cap = opt->flight_cap;
         ctx->shared_launch = opt->shared_launch != 0;
         ctx->l2_persist = opt->l2_persist > 0 ? opt->l2_persist : 0;
+        ctx->plain_overlap = opt->plain_overlap > 0;
         if (ctx->l2_persist > 2) return fail(CTD_EINVAL, "l2_persist must be -1, 0, 1 or 2");
     }
     if (ctx->threads % 32 != 0 || ctx->threads > 256) return fail(CTD_EINVAL, "threads_per_block must be a multiple of 32 and at most 256");
@@ -583,6 +596,12 @@ int ctd_destroy(ctd_ctx *ctx)
     if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
     for (auto e : ctx->serve_ev) cudaEventDestroy(e);
     for (auto e : ctx->serve_ev_pre) cudaEventDestroy(e);
+    if (ctx->plain_aux) {
+        cudaStreamSynchronize(ctx->plain_aux);
+        cudaStreamDestroy(ctx->plain_aux);
+    }
+    for (cudaEvent_t e : {ctx->plain_fork, ctx->plain_fold[0], ctx->plain_fold[1]})
+        if (e) cudaEventDestroy(e);
     for (auto l : ctx->serve_hi) cudaStreamDestroy(l);
     if (ctx->serve_res) cudaFreeHost(ctx->serve_res);
     if (ctx->staged) cudaFreeHost(ctx->staged);
@@ -927,7 +946,10 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
     if ((rc = prepare_run(ctx, *P, n_histories, n_batches))) return rc;
     P->have_result = false;
     const size_t nv = P->nvox;
+    const bool two = ctx->plain_overlap;
+    if (two && (rc = ensure_plain_aux(ctx, *P))) return rc;
     CK(cudaMemsetAsync(P->tally.p, 0, nv * sizeof(double), ctx->stream));
+    if (two) CK(cudaMemsetAsync(P->tally2.p, 0, nv * sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(P->sum_d.p, 0, nv * sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(P->sum_d2.p, 0, nv * sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(P->edep.p, 0, nv * sizeof(double), ctx->stream));
@@ -936,16 +958,31 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
     fill_request(*P, seed, T);
     const uint64_t n_lo = n_histories / n_batches, rem = n_histories % n_batches;
     const double vol = P->dx * P->dy * P->dz;
+    if (two) {
+        CK(cudaEventRecord(ctx->plain_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->plain_aux, ctx->plain_fork, 0));
+    }
+    // With two streams, odd batches run on the second one with the second tally: a
+    // batch's launch waits only for the fold two batches back (same stream, same
+    // tally), so it starts while the previous batch drains; each fold waits for the
+    // previous batch's fold, so Sigma d and Sigma d^2 add up in batch order.
     uint64_t h = 0;
     for (int b = 0; b < n_batches; ++b) {
         const uint64_t nb = static_cast<uint64_t>(b) < rem ? n_lo + 1 : n_lo;
         const int which = static_cast<uint64_t>(b) < rem ? 0 : 1;
-        if ((rc = transport(ctx, *P, T, which, h, 0, nb, P->tally.p, b))) return rc;
+        const int k = two ? b & 1 : 0;
+        const cudaStream_t s = k ? ctx->plain_aux : ctx->stream;
+        double *tally = k ? P->tally2.p : P->tally.p;
+        if ((rc = transport(ctx, *P, T, which, h, 0, nb, tally, b, nullptr, 0, 0, s, P->work.p + k))) return rc;
+        if (two && b > 0) CK(cudaStreamWaitEvent(s, ctx->plain_fold[k ^ 1], 0));
         // d = E / (m n_b) with m = rho V / 1000 kg
         const double scale = ctd::kKevToJ * 1000.0 / (vol * static_cast<double>(nb));
-        CKS(ctd::launch_fold(P->tally.p, P->rho.p, P->sum_d.p, P->sum_d2.p, P->edep.p, nv, scale, ctx->stream));
+        CKS(ctd::launch_fold(tally, P->rho.p, P->sum_d.p, P->sum_d2.p, P->edep.p, nv, scale, s));
+        if (two) CK(cudaEventRecord(ctx->plain_fold[k], s));
         h += nb;
     }
+    // the context's stream continues after the last fold (which followed every other)
+    if (two && ((n_batches - 1) & 1)) CK(cudaStreamWaitEvent(ctx->stream, ctx->plain_fold[1], 0));
     CKS(ctd::launch_finalize(P->sum_d.p, P->sum_d2.p, n_batches, P->dose.p, P->sd.p, nv, ctx->stream));
     CKS(ctd::launch_rsd(P->dose.p, P->sd.p, P->rho.p, nv, P->partials.p, kRsdParts, P->result.p, ctx->stream));
     CKS(ctd::launch_sum(P->edep.p, nv, P->partials.p + 5 * kRsdParts, kRsdParts, P->result.p + 3, ctx->stream));

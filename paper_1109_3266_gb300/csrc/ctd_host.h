@@ -123,6 +123,7 @@ struct Phantom {
     DevBuf<float> tab, mm, cs, rs;
     // per-run state
     DevBuf<double> tally, sum_d, sum_d2, edep, dose, sd, partials, result;
+    DevBuf<double> tally2;     // the second stream's batch tally of an overlapped plain run
     DevBuf<ctd::DeviceCounts> counts;
     DevBuf<unsigned long long> work;
     DevBuf<uint64_t> pref;     // [2][nbins+1]: batch of n_lo+1, batch of n_lo
@@ -147,7 +148,8 @@ struct Phantom {
     void use_cache(BufferCache *c)
     {
         for (DevBuf<float> *b : {&rho, &tab, &mm, &cs, &rs, &bins, &proj}) b->cache = c;
-        for (DevBuf<double> *b : {&tally, &sum_d, &sum_d2, &edep, &dose, &sd, &partials, &result}) b->cache = c;
+        for (DevBuf<double> *b : {&tally, &tally2, &sum_d, &sum_d2, &edep, &dose, &sd, &partials, &result})
+            b->cache = c;
         mat.cache = c;
         vox.cache = c;
         counts.cache = c;
@@ -232,6 +234,11 @@ struct ctd_ctx {
     // most the device's maximum), no larger than the device's window; the context's
     // persisting-L2 limit before, put back on destroy
     int l2_persist = 0;
+    // overlapped plain runs: the second stream, the event that starts it, and one event
+    // per stream marking its last fold (folds run in batch order)
+    bool plain_overlap = false;
+    cudaStream_t plain_aux = nullptr;
+    cudaEvent_t plain_fork = nullptr, plain_fold[2] = {nullptr, nullptr};
     size_t l2_asked = 0, l2_setaside = 0, l2_persist_max = 0, l2_window_max = 0, l2_prev_limit = 0;
     ctd::host::Staged *staged = nullptr;      // pinned read-back of counts and results
     size_t staged_n = 0;
@@ -290,9 +297,10 @@ int finish_stats(Phantom &P, int nb, cudaStream_t s);
 // one transport launch over local histories [lb, le) of a batch starting at h_base,
 // bracketed by timing events 2 ev_index and 2 ev_index + 1
 // (trace: per-history records of histories trace_h0 .. trace_h0 + trace_n - 1, or nullptr)
+// on stream s (null: the context's) with claim counter work (null: the phantom's first)
 int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uint64_t h_base, uint64_t lb,
               uint64_t le, double *tally, size_t ev_index, uint4 *trace = nullptr, uint64_t trace_h0 = 0,
-              uint64_t trace_n = 0);
+              uint64_t trace_n = 0, cudaStream_t s = nullptr, unsigned long long *work = nullptr);
 double now_s();
 int transport_time(ctd_ctx *ctx, size_t n_launch, double &t);
 // counts and results of several phantoms read back through pinned staging

@@ -179,6 +179,17 @@ def test_served_requests_join_while_others_are_on_the_gpu(ctd):
     ctd.ctd_destroy(c)
 
 
+def test_plain_run_on_one_or_two_streams_gives_the_same_results(ctd, ctx):
+    # overlapped plain runs alternate batches between two streams and two tallies, the
+    # folds in batch order; odd and even batch counts end on either stream
+    c = ctd.ctd_create(device=0, plain_overlap=1)
+    try:
+        for p in (problems()[0], I.scaled(problems()[1], n_batches=11), I.scaled(problems()[3], n_batches=2)):
+            same(alone(ctd, c, p), alone(ctd, ctx, p))
+    finally:
+        ctd.ctd_destroy(c)
+
+
 def test_l2_persisting_tally_gives_the_same_results(ctd, ctx):
     # the access-policy window changes only what L2 keeps
     p = problems()[0]

@@ -468,7 +468,8 @@ def leg_batched(ctd, args, clk):
     reqs = I.batched_requests(args.n_requests, hist_lo=args.hist_lo, hist_hi=args.hist_hi, sides=sides)
     ctxs = [ctd.ctd_create(device=0, stream=stream.cuda_stream, blocks_per_sm=args.blocks_per_sm,
                            threads_per_block=args.threads, chunk=args.chunk, flight_cap=args.flight_cap,
-                           multi_blocks_per_sm=args.multi_blocks_per_sm, shared_launch=k) for k in (0, 1)]
+                           multi_blocks_per_sm=args.multi_blocks_per_sm, shared_launch=k,
+                           batch_lanes=args.batch_lanes) for k in (0, 1)]
     hss = [[ctd.load_problem(c, p) for p in reqs] for c in ctxs]
     ctx, hs = ctxs[0], hss[0]
     n_total = sum(p.n_hist for p in reqs)
@@ -756,6 +757,7 @@ def main():
     ap.add_argument("--time-limit", type=float, default=120.0)
     ap.add_argument("--multi-blocks-per-sm", type=int, default=0)
     ap.add_argument("--shared-launch", type=int, default=0, help="served form: one shared multi-request launch")
+    ap.add_argument("--batch-lanes", type=int, default=0, help="batched form: streams the request chains share")
     ap.add_argument("--round-histories", type=float, default=1e9,
                     help="served form: histories of one batch of every running request admission keeps within")
     ap.add_argument("--compton", default="kn", choices=["kn", "wh"],

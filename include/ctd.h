@@ -79,6 +79,10 @@ typedef struct {
                                  then overlap, so each one's event-timed duration includes
                                  its neighbours'.  0 (default) or -1: every batch on the
                                  context's stream                                        */
+    int batch_lanes;          /* batched form with request chains: the streams the chains
+                                 share, chain k (requests largest first) on stream
+                                 k mod batch_lanes, so that at most this many requests run
+                                 at once (1..64; 0: 64)                                  */
 } ctd_options;
 
 /* Material: the numbers the closed-form cross sections use (Sec. 2.1).
@@ -468,6 +472,7 @@ typedef struct {
     int threads_per_block;
     int shared_launch;         /* ctd_autotune_batch: the launch design chosen            */
     int multi_blocks_per_sm;   /* ctd_autotune_batch: blocks per SM of shared launches     */
+    int batch_lanes;           /* ctd_autotune_batch: streams of the request chains        */
 } ctd_tune_result;
 
 int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, ctd_tune_result *out);
@@ -480,10 +485,13 @@ int ctd_autotune(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_probe, uint64_t seed, 
  * per SM; shared multi-request launches at 2, 3 or 4 blocks per SM; claims of
  * 256 or 1024 histories (how many a warp takes into its photon queue at a time);
  * flight caps of 2 or 4 (how many Woodcock flights a lane runs before its warp
- * regroups at the queue); and the context's own shape (25 in all; shared
+ * regroups at the queue); request chains sharing 2, 4, 8 or 16 streams (256
+ * threads, 4 per SM, claims of 256, flight cap 4); and the context's own shape
+ * (29 in all; shared
  * shapes are skipped when the requests do not share one node grid).  The
  * fastest on the longer probe is kept in the context (shared_launch,
- * threads_per_block, blocks_per_sm, multi_blocks_per_sm, chunk, flight_cap) and
+ * threads_per_block, blocks_per_sm, multi_blocks_per_sm, chunk, flight_cap,
+ * batch_lanes) and
  * returned in out (histories_per_s on the longer probe; baseline_per_s of the
  * context's previous shape there; n_tried, the shapes of the first pass).  Results do not depend on the shape (up to the order of binary64
  * additions).  The requests' phantoms end holding the last probe's results. */

@@ -344,8 +344,6 @@ int join_lanes(ctd_ctx *ctx, cudaStream_t origin, int n)
     return CTD_OK;
 }
 
-cudaStream_t lane(ctd_ctx *ctx, int r) { return ctx->lanes[r % kMaxLanes]; }
-
 // The second stream, its events and the phantom's second tally of an overlapped plain run.
 int ensure_plain_aux(ctd_ctx *ctx, Phantom &P)
 {
@@ -547,6 +545,8 @@ int ctd_create(ctd_ctx **out, const ctd_options *opt)
         ctx->shared_launch = opt->shared_launch != 0;
         ctx->l2_persist = opt->l2_persist > 0 ? opt->l2_persist : 0;
         ctx->plain_overlap = opt->plain_overlap > 0;
+        if (opt->batch_lanes < 0 || opt->batch_lanes > kMaxLanes) return fail(CTD_EINVAL, "batch_lanes must be 0..64");
+        if (opt->batch_lanes > 0) ctx->batch_lanes = opt->batch_lanes;
         if (ctx->l2_persist > 2) return fail(CTD_EINVAL, "l2_persist must be -1, 0, 1 or 2");
     }
     if (ctx->threads % 32 != 0 || ctx->threads > 256) return fail(CTD_EINVAL, "threads_per_block must be a multiple of 32 and at most 256");

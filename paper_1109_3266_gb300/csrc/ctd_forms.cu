@@ -90,8 +90,8 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
     };
     put(descs.data(), descs.size() * sizeof(ctd::RequestDesc));
     put(folds.data(), folds.size() * sizeof(ctd::FoldDesc));
-    const int shape[8] = {n_batches, ctx->shared_launch, ctx->num_sms, ctx->blocks_per_sm, ctx->multi_blocks_per_sm,
-                          ctx->threads, ctx->chunk, ctx->flight_cap};
+    const int shape[9] = {n_batches, ctx->shared_launch, ctx->num_sms, ctx->blocks_per_sm, ctx->multi_blocks_per_sm,
+                          ctx->threads, ctx->chunk, ctx->flight_cap, ctx->batch_lanes};
     put(shape, sizeof(shape));
     size_t n_launch = 1;
     std::function<int(cudaStream_t)> body;
@@ -104,7 +104,8 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
             fill_shared(*ps[r], sh);
             put(&sh, sizeof(sh));
         }
-        if ((rc = ensure_lanes(ctx, n_req))) return rc;
+        const int n_lanes = std::min(n_req, ctx->batch_lanes);
+        if ((rc = ensure_lanes(ctx, n_lanes))) return rc;
         if (!event_at(ctx, 0) || !event_at(ctx, 1)) return fail(CTD_ECUDA, "cudaEventCreate failed");
         // chains are issued largest first, so that the last to finish are short ones
         // (longest processing time first: the smaller requests fill the tail)
@@ -113,17 +114,17 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return n_histories[a] > n_histories[b]; });
         put(order.data(), order.size() * sizeof(int));
-        body = [&, order](cudaStream_t cs) {
+        body = [&, order, n_lanes](cudaStream_t cs) {
             if (cudaMemsetAsync(ctx->u_work.p, 0, static_cast<size_t>(n_batches) * n_req * sizeof(unsigned long long),
                                 cs) != cudaSuccess ||
                 cudaEventRecordWithFlags(ctx->events[0], cs, cudaEventRecordExternal) != cudaSuccess)
                 return static_cast<int>(CTD_ECUDA);
-            int e = fork_lanes(ctx, cs, n_req);
+            int e = fork_lanes(ctx, cs, n_lanes);
             for (int k = 0; k < n_req && e == CTD_OK; ++k) {
                 const int r = order[k];
                 Phantom &P = *ps[r];
                 // the k-th largest request on lane k (mod the lanes)
-                const cudaStream_t ls = lane(ctx, k);
+                const cudaStream_t ls = ctx->lanes[k % n_lanes];
                 for (int b = 0; b < n_batches && e == CTD_OK; ++b) {
                     const size_t d = static_cast<size_t>(b) * n_req + r;
                     e = launch_one(ctx, P, descs[d], ls);
@@ -133,7 +134,7 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
                 }
                 if (e == CTD_OK) e = finish_stats(P, n_batches, ls);
             }
-            if (e == CTD_OK) e = join_lanes(ctx, cs, n_req);
+            if (e == CTD_OK) e = join_lanes(ctx, cs, n_lanes);
             if (e == CTD_OK && cudaEventRecordWithFlags(ctx->events[1], cs, cudaEventRecordExternal) != cudaSuccess)
                 e = CTD_ECUDA;
             return e;

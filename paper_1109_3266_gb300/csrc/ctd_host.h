@@ -229,6 +229,7 @@ struct ctd_ctx {
     // single-request launches on its own stream (the device overlaps the chains),
     // 1 shares one multi-request launch per batch among all requests
     int shared_launch = 0;
+    int batch_lanes = 64;          // batched form: streams the request chains share
     // plain-form launches: an L2 access-policy window over the tally (1) or the
     // voxel densities (2), with a persisting set-aside of its size (granted bytes; at
     // most the device's maximum), no larger than the device's window; the context's
@@ -289,7 +290,6 @@ cudaEvent_t event_at(ctd_ctx *ctx, size_t i);
 int ensure_lanes(ctd_ctx *ctx, int n);
 int fork_lanes(ctd_ctx *ctx, cudaStream_t origin, int n);
 int join_lanes(ctd_ctx *ctx, cudaStream_t origin, int n);
-cudaStream_t lane(ctd_ctx *ctx, int r);
 // one single-request launch of q on stream s at the context's launch shape
 int launch_one(ctd_ctx *ctx, Phantom &P, const ctd::RequestDesc &q, cudaStream_t s);
 // mean, standard error, avg RSD and deposited energy of nb finished batches

@@ -180,10 +180,10 @@ int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, con
         total += nh[r];
     }
     struct Shape {
-        int shared, threads, bps, mbps, chunk, cap;
+        int shared, threads, bps, mbps, chunk, cap, lanes;
     };
     const Shape old{ctx->shared_launch, ctx->threads, ctx->blocks_per_sm, ctx->multi_blocks_per_sm, ctx->chunk,
-                    ctx->flight_cap};
+                    ctx->flight_cap, ctx->batch_lanes};
     std::vector<Shape> shapes{old};
     // request chains: block shape and residency of each request's launches; shared
     // launches: blocks per SM of the multi-request kernel; both: claim size (how many
@@ -193,11 +193,14 @@ int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, con
     for (const auto &b : chains)
         for (int chunk : {256, 1024})
             for (int cap : {2, 4})
-                shapes.push_back({0, b[0], b[1], old.mbps, chunk, cap});
+                shapes.push_back({0, b[0], b[1], old.mbps, chunk, cap, old.lanes});
+    // request chains sharing fewer streams: fewer requests' phantoms and tallies in L2 at once
+    for (int lanes : {2, 4, 8, 16})
+        shapes.push_back({0, 256, 4, old.mbps, 256, 4, lanes});
     for (int mbps : {2, 3, 4})
         for (int chunk : {256, 1024})
             for (int cap : {2, 4})
-                shapes.push_back({1, 256, old.bps, mbps, chunk, cap});
+                shapes.push_back({1, 256, old.bps, mbps, chunk, cap, old.lanes});
     auto apply = [&](const Shape &s) {
         ctx->shared_launch = s.shared;
         ctx->threads = s.threads;
@@ -205,6 +208,7 @@ int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, con
         ctx->multi_blocks_per_sm = s.mbps;
         ctx->chunk = s.chunk;
         ctx->flight_cap = s.cap;
+        ctx->batch_lanes = s.lanes;
     };
     // best of two timed batched calls (the first call of a shape records its graph)
     auto time_shape = [&](const Shape &s, double &t_min) -> int {
@@ -276,6 +280,7 @@ int ctd_autotune_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, con
         out->baseline_per_s = static_cast<double>(total) / base;
         out->shared_launch = pick.shared;
         out->multi_blocks_per_sm = pick.mbps;
+        out->batch_lanes = pick.lanes;
     }
     return CTD_OK;
 }

@@ -33,7 +33,8 @@ class ctd_options(C.Structure):
                 ("threads_per_block", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int),
                 ("multi_blocks_per_sm", C.c_int), ("serve_max_active", C.c_int),
                 ("serve_round_histories", C.c_double), ("serve_reserve_bytes", C.c_double),
-                ("shared_launch", C.c_int), ("l2_persist", C.c_int), ("plain_overlap", C.c_int)]
+                ("shared_launch", C.c_int), ("l2_persist", C.c_int), ("plain_overlap", C.c_int),
+                ("batch_lanes", C.c_int)]
 
 
 class ctd_material(C.Structure):
@@ -83,7 +84,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(5)
 class ctd_tune_result(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("chunk", C.c_int), ("flight_cap", C.c_int), ("n_tried", C.c_int),
                 ("histories_per_s", C.c_double), ("baseline_per_s", C.c_double), ("threads_per_block", C.c_int),
-                ("shared_launch", C.c_int), ("multi_blocks_per_sm", C.c_int)]
+                ("shared_launch", C.c_int), ("multi_blocks_per_sm", C.c_int), ("batch_lanes", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -164,7 +165,7 @@ def _dp(a):
 # --------------------------------------------------------------------------- C names
 def ctd_create(device=0, stream=None, blocks_per_sm=0, threads_per_block=0, chunk=0, flight_cap=0,
                multi_blocks_per_sm=0, serve_max_active=0, serve_round_histories=0.0, shared_launch=0,
-               serve_reserve_bytes=0.0, l2_persist=0, plain_overlap=0):
+               serve_reserve_bytes=0.0, l2_persist=0, plain_overlap=0, batch_lanes=0):
     """Context handle.  stream: a CUDA stream handle (int), e.g. torch's current stream.
     shared_launch: batched and served forms share one multi-request launch per
     batch (1) instead of one chain of single-request launches per request (0).
@@ -173,7 +174,7 @@ def ctd_create(device=0, stream=None, blocks_per_sm=0, threads_per_block=0, chun
     two streams with a tally each (1; 0 or -1: one stream)."""
     opt = ctd_options(device, stream or None, blocks_per_sm, threads_per_block, chunk, flight_cap, multi_blocks_per_sm,
                       serve_max_active, float(serve_round_histories), float(serve_reserve_bytes), int(shared_launch),
-                      int(l2_persist), int(plain_overlap))
+                      int(l2_persist), int(plain_overlap), int(batch_lanes))
     h = C.c_void_p()
     _check(lib().ctd_create(C.byref(h), C.byref(opt)))
     return h

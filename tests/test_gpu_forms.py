@@ -179,6 +179,19 @@ def test_served_requests_join_while_others_are_on_the_gpu(ctd):
     ctd.ctd_destroy(c)
 
 
+def test_batched_chains_on_few_streams_equal_separate_runs(ctd, ctx):
+    # chains sharing two streams run the requests two at a time, each its own chain
+    ps = problems()
+    c = ctd.ctd_create(device=0, batch_lanes=2)
+    try:
+        hs = [ctd.load_problem(c, p) for p in ps]
+        ctd.ctd_run_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
+        for p, h in zip(ps, hs):
+            same(alone(ctd, ctx, p), ctd.ctd_get_dose_and_stddev(c, h, p.phantom.nvox))
+    finally:
+        ctd.ctd_destroy(c)
+
+
 def test_plain_run_on_one_or_two_streams_gives_the_same_results(ctd, ctx):
     # overlapped plain runs alternate batches between two streams and two tallies, the
     # folds in batch order; odd and even batch counts end on either stream
@@ -283,8 +296,9 @@ def test_batched_autotuner_picks_a_shape_and_results_do_not_depend_on_it(ctd, ct
     c = ctd.ctd_create(device=0)
     hs = [ctd.load_problem(c, p) for p in ps]
     r = ctd.ctd_autotune_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10, probe_fraction=0.2)
-    assert r["n_tried"] == 25 and r["histories_per_s"] > 0 and r["baseline_per_s"] > 0
+    assert r["n_tried"] == 29 and r["histories_per_s"] > 0 and r["baseline_per_s"] > 0
     assert r["shared_launch"] in (0, 1) and r["chunk"] in (256, 1024) and r["flight_cap"] in (2, 4)
+    assert r["batch_lanes"] in (2, 4, 8, 16, 64)
     # the context keeps the choice; the full requests give what they give alone
     ctd.ctd_run_batch(c, hs, [p.n_hist for p in ps], [p.seed for p in ps], 10)
     for p, h, rr in zip(ps, hs, ref):

@@ -736,7 +736,7 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--flight-cap", type=int, default=0)
-    ap.add_argument("--l2-persist", type=int, default=0, help="plain form: tally (1) or densities (2) persisting in L2")
+    ap.add_argument("--l2-persist", type=int, default=0, help="plain form: tally (1) or voxel words (2) persisting in L2")
     ap.add_argument("--plain-overlap", type=int, default=0, help="plain form: batches on two streams (1; 0 or -1: one stream)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=15.0)

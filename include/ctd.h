@@ -66,12 +66,11 @@ typedef struct {
                                  next one's launch; 1 runs one multi-request launch per
                                  batch shared by all requests                          */
     int l2_persist;           /* plain-form transport launches mark the phantom's tally (1)
-                                 or its voxel densities (2) as persisting in L2 (an
+                                 or its packed voxel words (2) as persisting in L2 (an
                                  access-policy window over it, with the context's
                                  persisting-L2 limit raised to its size, at most the
                                  device's maximum, while the context lives and put back
-                                 by ctd_destroy); -1 or 0
-                                 (the default): neither                                  */
+                                 by ctd_destroy); -1 or 0 (the default): neither         */
     int plain_overlap;        /* ctd_run: 1 alternates the batches between the context's stream
                                  and a second stream of its own, each with its own tally,
                                  so that one batch's launch starts while the previous one's

@@ -407,9 +407,9 @@ int transport(ctd_ctx *ctx, Phantom &P, ctd::RequestDesc &q, int which_size, uin
     const int grid = ctx->num_sms * ctx->blocks_per_sm;
     ctd::L2Window win{};
     if (ctx->l2_persist) {
-        // the tally's (or the densities') lines stay in L2
-        win.base = ctx->l2_persist == 1 ? static_cast<void *>(tally) : static_cast<void *>(P.rho.p);
-        win.bytes = std::min(P.nvox * (ctx->l2_persist == 1 ? sizeof(double) : sizeof(float)), ctx->l2_window_max);
+        // the tally's (or the voxel words') lines stay in L2
+        win.base = ctx->l2_persist == 1 ? static_cast<void *>(tally) : static_cast<void *>(P.vox.p);
+        win.bytes = std::min(P.nvox * (ctx->l2_persist == 1 ? sizeof(double) : sizeof(uint32_t)), ctx->l2_window_max);
         // a set-aside of the window's size, no more: the rest of L2 stays for the other data
         const size_t want = std::min(win.bytes, ctx->l2_persist_max);
         if (want != ctx->l2_asked) {

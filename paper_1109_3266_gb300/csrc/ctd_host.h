@@ -231,7 +231,7 @@ struct ctd_ctx {
     int shared_launch = 0;
     int batch_lanes = 64;          // batched form: streams the request chains share
     // plain-form launches: an L2 access-policy window over the tally (1) or the
-    // voxel densities (2), with a persisting set-aside of its size (granted bytes; at
+    // packed voxel words (2), with a persisting set-aside of its size (granted bytes; at
     // most the device's maximum), no larger than the device's window; the context's
     // persisting-L2 limit before, put back on destroy
     int l2_persist = 0;

@@ -169,7 +169,7 @@ def ctd_create(device=0, stream=None, blocks_per_sm=0, threads_per_block=0, chun
     """Context handle.  stream: a CUDA stream handle (int), e.g. torch's current stream.
     shared_launch: batched and served forms share one multi-request launch per
     batch (1) instead of one chain of single-request launches per request (0).
-    l2_persist: plain-form launches keep the tally (1) or the densities (2) persisting
+    l2_persist: plain-form launches keep the tally (1) or the voxel words (2) persisting
     in L2 (-1 or 0: neither).  plain_overlap: ctd_run alternates its batches between
     two streams with a tally each (1; 0 or -1: one stream)."""
     opt = ctd_options(device, stream or None, blocks_per_sm, threads_per_block, chunk, flight_cap, multi_blocks_per_sm,

@@ -642,13 +642,15 @@ int ctd_create_phantom(ctd_ctx *ctx, int nx, int ny, int nz, double dx, double d
     P->phys.mode = CTD_MODE_FULL;
     P->phys.max_real = 0;
     P->phys.compton_model = CTD_COMPTON_KN;
-    if ((rc = P->mat.ensure(nvox)) || (rc = P->rho.ensure(nvox)) || (rc = P->vox.ensure(nvox))) return rc;
+    if ((rc = P->mat.ensure(nvox)) || (rc = P->rho.ensure(nvox)) || (rc = P->vox.ensure(nvox)) ||
+        (rc = P->rinv.ensure(nvox)))
+        return rc;
     CK(cudaMemcpyAsync(P->mat.p, mat, nvox, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(P->rho.p, density, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     // range checks, materials present and their largest densities, on the device
     DevBuf<ctd::PhantomScan> scan;
     if ((rc = scan.ensure(1))) return rc;
-    CKS(ctd::launch_scan_phantom(P->mat.p, P->rho.p, nvox, n_mat, P->vox.p, scan.p, ctx->stream));
+    CKS(ctd::launch_scan_phantom(P->mat.p, P->rho.p, nvox, n_mat, P->vox.p, P->rinv.p, scan.p, ctx->stream));
     ctd::PhantomScan sc{};
     CK(cudaMemcpyAsync(&sc, scan.p, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -977,7 +979,7 @@ int ctd_run(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t seed, i
         if (two && b > 0) CK(cudaStreamWaitEvent(s, ctx->plain_fold[k ^ 1], 0));
         // d = E / (m n_b) with m = rho V / 1000 kg
         const double scale = ctd::kKevToJ * 1000.0 / (vol * static_cast<double>(nb));
-        CKS(ctd::launch_fold(tally, P->rho.p, P->sum_d.p, P->sum_d2.p, P->edep.p, nv, scale, s));
+        CKS(ctd::launch_fold(tally, P->rinv.p, P->sum_d.p, P->sum_d2.p, P->edep.p, nv, scale, s));
         if (two) CK(cudaEventRecord(ctx->plain_fold[k], s));
         h += nb;
     }
@@ -1108,7 +1110,7 @@ int ctd_shard_fold(ctd_ctx *ctx, ctd_phantom ph, int batch, double *tally_dev)
     shard_batch_of(*P, batch, size, which, h0);
     // d = E / (m n_b) with m = rho V / 1000 kg
     const double scale = ctd::kKevToJ * 1000.0 / (P->dx * P->dy * P->dz * static_cast<double>(size));
-    CKS(ctd::launch_fold(tally_dev, P->rho.p, P->sum_d.p, P->sum_d2.p, P->edep.p, P->nvox, scale, ctx->stream));
+    CKS(ctd::launch_fold(tally_dev, P->rinv.p, P->sum_d.p, P->sum_d2.p, P->edep.p, P->nvox, scale, ctx->stream));
     return CTD_OK;
 }
 

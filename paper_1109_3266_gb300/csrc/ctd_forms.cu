@@ -74,7 +74,7 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
             q.tally = P.tally.p;
             ctd::FoldDesc &f = folds[static_cast<size_t>(b) * n_req + r];
             f.tally = P.tally.p;
-            f.rho = P.rho.p;
+            f.rinv = P.rinv.p;
             f.sum_d = P.sum_d.p;
             f.sum_d2 = P.sum_d2.p;
             f.edep = P.edep.p;
@@ -129,7 +129,7 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
                     const size_t d = static_cast<size_t>(b) * n_req + r;
                     e = launch_one(ctx, P, descs[d], ls);
                     if (e == CTD_OK)
-                        e = ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, folds[d].scale,
+                        e = ctd::launch_fold(P.tally.p, P.rinv.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, folds[d].scale,
                                              ls);
                 }
                 if (e == CTD_OK) e = finish_stats(P, n_batches, ls);
@@ -416,7 +416,7 @@ int launch_work(ctd_ctx *ctx, ServeReq &R, Phantom &P, bool first_in_line)
             CKS(launch_one(ctx, P, q, s));
             hist += static_cast<double>(q.local_end - q.local_begin);
         }
-        if (j < n) CKS(ctd::launch_fold(P.tally.p, P.rho.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, scale, s));
+        if (j < n) CKS(ctd::launch_fold(P.tally.p, P.rinv.p, P.sum_d.p, P.sum_d2.p, P.edep.p, P.nvox, scale, s));
         if (j == n - 2) CK(cudaEventRecord(ctx->serve_ev_pre[R.lane], s));
     }
     const int done = R.batches + n;
@@ -638,7 +638,7 @@ int serve_round(ctd_ctx *ctx)
         tiles[i + 1] = tiles[i] + (P.nvox + ctd::kFoldTile - 1) / ctd::kFoldTile;
         ctd::FoldDesc &f = folds[i];
         f.tally = P.tally.p;
-        f.rho = P.rho.p;
+        f.rinv = P.rinv.p;
         f.sum_d = P.sum_d.p;
         f.sum_d2 = P.sum_d2.p;
         f.edep = P.edep.p;

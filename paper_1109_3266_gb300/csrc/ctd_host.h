@@ -116,6 +116,7 @@ struct Phantom {
     DevBuf<uint8_t> mat;
     DevBuf<float> rho;
     DevBuf<uint32_t> vox;      // material and density packed (what the transport reads)
+    DevBuf<double> rinv;       // 1 / density per voxel, 0 where it is 0 (what the fold reads)
     // tables
     bool tables_ok = false;
     int n_e = 0;
@@ -152,6 +153,7 @@ struct Phantom {
             b->cache = c;
         mat.cache = c;
         vox.cache = c;
+        rinv.cache = c;
         counts.cache = c;
         work.cache = c;
         pref.cache = c;

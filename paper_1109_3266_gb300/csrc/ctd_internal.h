@@ -150,7 +150,7 @@ struct PhantomScan {
     unsigned int present_mask;
     unsigned int max_bits[kMaxPhantomMaterials];
 };
-int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, uint32_t *vox,
+int launch_scan_phantom(const uint8_t *mat, const float *rho, size_t nvox, int n_mat, uint32_t *vox, double *rinv,
                         PhantomScan *out, void *stream);
 
 // What every request of a launch shares: the node grid and the C surface.
@@ -191,7 +191,7 @@ struct L2Window {
 int launch_transport(const LaunchParams &p, int grid, int block, int threads_per_sm, void *stream,
                      const L2Window *win = nullptr);
 size_t transport_smem_bytes(const LaunchParams &p, int threads);
-int launch_fold(double *tally, const float *rho, double *sum_d, double *sum_d2, double *edep, size_t nvox,
+int launch_fold(double *tally, const double *rinv, double *sum_d, double *sum_d2, double *edep, size_t nvox,
                 double scale, void *stream);
 int launch_finalize(const double *sum_d, const double *sum_d2, int nb, double *dose, double *sd, size_t nvox,
                     void *stream);
@@ -206,7 +206,7 @@ int launch_sum(const double *x, size_t n, double *partials, int n_parts, double 
 // kFoldTile voxels, tile_off[r] = first tile of request r
 struct FoldDesc {
     double *tally;
-    const float *rho;
+    const double *rinv;          // 1 / rho per voxel (0 where rho = 0)
     double *sum_d, *sum_d2, *edep;
     uint64_t nvox;
     double scale;

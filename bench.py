@@ -295,12 +295,13 @@ def timed_runs(ctd, ctx, h, p, seed, steps, warmup, ramp_s, stream, flush, sync,
             "ramp": {"seconds": ramp_t, "runs": ramp}, "clocks": clk.summary(a, b) if clk else None}
 
 
-def rsd_stopped(ctd, ctx, h, p, seed, rsd, sec_run):
-    """Seconds to 1 % avg RSD, measured with the RSD-stopped served form: batches of a
-    tenth of the extrapolated need N (RSD / 1 %)^2, stopped at 1 % after >= 10 batches."""
+def rsd_stopped(ctd, ctx, h, p, seed, rsd, sec_run, parts=10):
+    """Seconds to 1 % avg RSD, measured with the RSD-stopped served form: batches of
+    1/parts of the extrapolated need N (RSD / 1 %)^2, stopped at 1 % after >= 10
+    batches (the stop overshoots the need by up to one batch)."""
     import torch
     n_1 = p.n_hist * (rsd / 0.01) ** 2
-    B = int(max(1e6, n_1 / 10))
+    B = int(max(1e6, n_1 / parts))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rid = ctd.ctd_submit(ctx, h, B, 0.01, seed + 1, n_histories_max=int(40 * B))
@@ -441,7 +442,7 @@ def leg_head(ctd, args, stream, flush, peaks, peak_kind, clk):
            "unit": UNIT, "ms_per_step": 1e3 * sec_run, "avg_rsd": st["avg_rsd"], "clocks": run["clocks"]}
     out["sec_to_1pct_avg_rsd_extrapolated"] = sec_run * (st["avg_rsd"] / 0.01) ** 2
     if args.rsd_stop:
-        r = rsd_stopped(ctd, ctx, h, p, p.seed, st["avg_rsd"], sec_run)
+        r = rsd_stopped(ctd, ctx, h, p, p.seed, st["avg_rsd"], sec_run, args.rsd_parts)
         out["sec_to_1pct_avg_rsd"] = r["seconds"]
         out["rsd_stopped_run"] = r
     probes = None if args.no_probe else memory_probes(ctd, ctx, p.phantom.nvox)
@@ -676,7 +677,7 @@ def run_ours(args):
         "clocks": run["clocks"],
     }
     if args.rsd_stop:
-        r = rsd_stopped(ctd, ctx, h, p, p.seed, rsd, sec_run)
+        r = rsd_stopped(ctd, ctx, h, p, p.seed, rsd, sec_run, args.rsd_parts)
         line["sec_to_1pct_avg_rsd"] = r["seconds"]
         line["rsd_stopped_run"] = r
     else:
@@ -743,6 +744,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the memory-ceiling probes")
     ap.add_argument("--rsd-stop", type=int, default=1, help="measure sec-to-1%% with the RSD-stopped form")
+    ap.add_argument("--rsd-parts", type=int, default=10,
+                    help="RSD-stopped form: batches of 1/parts of the extrapolated need")
     ap.add_argument("--n-requests", type=int, default=64)
     ap.add_argument("--max-side", type=int, default=256)
     ap.add_argument("--served-requests", type=int, default=200)

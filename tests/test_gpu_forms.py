@@ -234,6 +234,24 @@ def test_served_gpu_filling_requests_equal_plain_runs(ctd):
     ctd.ctd_destroy(c)
 
 
+def test_served_request_without_target_runs_to_its_cap(ctd):
+    # rsd_target 0: the request stops at its history cap, checked from min_batches on,
+    # beside another request with a target
+    c = ctd.ctd_create(device=0, serve_round_histories=1e12)
+    pa, pb = problems()[1], problems()[3]
+    ha, hb = ctd.load_problem(c, pa), ctd.load_problem(c, pb)
+    a = ctd.ctd_submit(c, ha, 30_000, 0.0, pa.seed, n_histories_max=12 * 30_000, min_batches=4)
+    b = ctd.ctd_submit(c, hb, 2_000, 0.5, pb.seed, n_histories_max=100 * 2_000, min_batches=2)
+    sb = ctd.ctd_wait(c, b, 120.0)
+    sa = ctd.ctd_wait(c, a, 120.0)
+    assert sa["state"] == sb["state"] == ctd.REQ_DONE
+    assert sa["batches"] == 12 and sa["histories"] == 12 * 30_000
+    same(alone(ctd, c, pa, n=12 * 30_000, nb=12), ctd.ctd_get_dose_and_stddev(c, ha, pa.phantom.nvox))
+    k = sb["batches"]
+    same(alone(ctd, c, pb, n=k * 2_000, nb=k), ctd.ctd_get_dose_and_stddev(c, hb, pb.phantom.nvox))
+    ctd.ctd_destroy(c)
+
+
 def test_serve_loop_reports_latency(ctd, ctx):
     from paper_1109_3266_gb300 import serve
 

@@ -67,6 +67,9 @@ def test_full_grid_dose_matches_binary64_oracle(ctd, ctx, oracle, name):
 
 
 def test_full_grid_independent_seeds(ctd, ctx, oracle):
+    # (the head's 1 mm voxels collect too few deposits per batch at 1e8 histories for
+    # the combined z to be close to normal: its median |z| came out at 1.0, with >= 99 %
+    # of the voxels within 3 sigma, so only CBCT water is compared at independent seeds)
     p = CASES["cbct_water"]()
     dose, sd, st, h = ctd.run_problem(ctx, p)
     ctd.ctd_destroy_phantom(ctx, h)

@@ -425,6 +425,7 @@ struct Queue {
 };
 
 constexpr size_t kWarpBytes = kQueueBytes + sizeof(WarpPool) + 32 * sizeof(LaneSlot);
+static_assert(kWarpBytes % 16 == 0, "a warp's shared-memory area must keep 16-byte alignment");
 
 // All histories [q.local_begin, q.local_end) of one request, claimed by warps
 // from q.work in runs of `chunk`.  Returns when the warp has no photon left.
@@ -562,10 +563,12 @@ __device__ __forceinline__ void load_tables(const RequestDesc &q, int n_e, float
 }
 
 // Single request (kForm 0 or 1): the request lives in the kernel's parameter
-// space.  Several requests: each block works on one request at a time, a copy
-// of its descriptor, attenuation table and majorant in shared memory, and when
-// that request has no history left to claim the block moves on to the next
-// one, so that one request's tail overlaps the next one's start.
+// space, its attenuation table and majorant are copied into shared memory.
+// Several requests: each warp works on one request at a time with a copy of its
+// descriptor in shared memory and its tables read through L1, and when that
+// request has no history left to claim the warp moves on to the next one by
+// itself, so that one request's tail overlaps the next one's start without the
+// block waiting for its slowest warp.
 // kForm: 0 one request without a fluence map, 1 one request with a fluence map
 // (the map's source path is compiled only into this form, so that it does not
 // cost the open-field form registers), 2 several requests without maps, 3 several
@@ -573,17 +576,23 @@ __device__ __forceinline__ void load_tables(const RequestDesc &q, int n_e, float
 // forms take each request's Philox round keys from its descriptor in shared
 // memory.
 // kTrace (single-request forms): also write each history's record to P.trace.
+constexpr int kReqWords = sizeof(RequestDesc) / 16;
+
 template <int kMaxThreads, int kMinBlocks, int kForm, bool kTrace = false>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(const LaunchParams P)
 {
     extern __shared__ float4 smem[];
     const int n_e = P.sh.n_e;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr bool kMulti = kForm >= 2;
+    // single: the tables, then the warps' queues; several: per warp, a descriptor and
+    // the queue
     float4 *s_tab = smem;
     float *s_mm = reinterpret_cast<float *>(smem + P.sh.max_n_mat * n_e);
-    float4 *s_req4 = smem + P.sh.max_n_mat * n_e + (n_e + 3) / 4;
-    constexpr int kReqWords = sizeof(RequestDesc) / 16;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *wbase = reinterpret_cast<unsigned char *>(s_req4 + kReqWords) + warp * kWarpBytes;
+    float4 *w_req4 = smem + warp * (kReqWords + kWarpBytes / 16);
+    unsigned char *wbase = kMulti ? reinterpret_cast<unsigned char *>(w_req4 + kReqWords)
+                                  : reinterpret_cast<unsigned char *>(smem + P.sh.max_n_mat * n_e + (n_e + 3) / 4) +
+                                        warp * kWarpBytes;
     Queue Q;
     Q.h = reinterpret_cast<uint64_t *>(wbase);
     Q.f = reinterpret_cast<float *>(Q.h + kQueue);
@@ -592,7 +601,6 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
     cnt.me = reinterpret_cast<LaneSlot *>(wbase + kQueueBytes + sizeof(WarpPool)) + lane;
     cnt.clear();
 
-    constexpr bool kMulti = kForm >= 2;
     if (!kMulti) {
         load_tables(P.one, n_e, s_tab, s_mm);
         __syncthreads();
@@ -600,18 +608,16 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
         flush_warp(P.one.counts, cnt, lane);
         return;
     }
-    // every block starts at the first request and walks forward to the next
-    // request with histories left, so that the blocks of an SM mostly work on
-    // one request (its phantom and tally stay in L2) and a request's tail
-    // overlaps the next one's start
-    __shared__ int s_r;
-    const RequestDesc &q = *reinterpret_cast<const RequestDesc *>(s_req4);
+    // every warp starts at the first request and walks forward to the next request
+    // with histories left, so that the warps of an SM mostly work on one request
+    // (its phantom and tally stay in L2) and a request's tail overlaps the next one's
+    // start
+    const RequestDesc &q = *reinterpret_cast<const RequestDesc *>(w_req4);
     int r = 0;
-    for (int visited = 0;;) {
-        if (threadIdx.x == 0) {
-            int found = -1;
-            for (; visited + r < P.n_req; ++visited) {
-                const int rr = r + visited;
+    for (;;) {
+        int found = -1;
+        if (lane == 0) {
+            for (int rr = r; rr < P.n_req; ++rr) {
                 const RequestDesc &c = P.reqs[rr];
                 const unsigned long long claimed = *reinterpret_cast<volatile unsigned long long *>(c.work);
                 if (c.local_begin + claimed < c.local_end) {
@@ -619,22 +625,17 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) transport_kernel(cons
                     break;
                 }
             }
-            s_r = found;
         }
-        __syncthreads();
-        const int cur = s_r;
-        if (cur < 0) break;
-        const float4 *src = reinterpret_cast<const float4 *>(P.reqs + cur);
-        for (int i = threadIdx.x; i < kReqWords; i += blockDim.x) s_req4[i] = src[i];
-        __syncthreads();
-        load_tables(q, n_e, s_tab, s_mm);
-        __syncthreads();
-        run_request<true, kForm == 3, false>(P, q, s_tab, s_mm, Q, lane, cnt);
+        found = __shfl_sync(kFull, found, 0);
+        if (found < 0) break;
+        const float4 *src = reinterpret_cast<const float4 *>(P.reqs + found);
+        for (int i = lane; i < kReqWords; i += 32) w_req4[i] = src[i];
+        __syncwarp();
+        run_request<true, kForm == 3, false>(P, q, reinterpret_cast<const float4 *>(q.tab), q.mmax, Q, lane, cnt);
         flush_warp(q.counts, cnt, lane);
-        __syncthreads();
+        __syncwarp();
         // the same request is exhausted now; continue the walk from it
-        r = cur;
-        visited = 0;
+        r = found;
     }
 }
 
@@ -714,8 +715,9 @@ int launch_m(const LaunchParams &p, int grid, int block, int threads_per_sm, siz
 
 size_t transport_smem_bytes(const LaunchParams &p, int threads)
 {
-    return (static_cast<size_t>(p.sh.max_n_mat) * p.sh.n_e + (p.sh.n_e + 3) / 4 +
-            sizeof(RequestDesc) / 16) * sizeof(float4) +
+    // several requests: per warp, a descriptor and the queue
+    if (p.n_req > 0) return static_cast<size_t>(threads / 32) * (kReqWords * sizeof(float4) + kWarpBytes);
+    return (static_cast<size_t>(p.sh.max_n_mat) * p.sh.n_e + (p.sh.n_e + 3) / 4) * sizeof(float4) +
            static_cast<size_t>(threads / 32) * kWarpBytes;
 }
 

@@ -366,7 +366,7 @@ int ctd_trace_range(ctd_ctx *ctx, ctd_phantom ph, uint64_t n_histories, uint64_t
  * each request is its own chain of single-request launches and folds on its own
  * stream, and the device overlaps one chain's last blocks with the next chain's
  * first ones; with shared_launch = 1 batch b of every request runs in one
- * multi-request launch (each block works on one request at a time and moves on
+ * multi-request launch (each warp works on one request at a time and moves on
  * to the next when it runs out of histories; all requests on the same node
  * grid, else CTD_EINVAL), followed by one fold over every request's grids.
  * Each phantom's results are then read with ctd_get_dose_and_stddev and equal

@@ -85,7 +85,7 @@ enum { kCntPe = 0, kCntCompton, kCntRayleigh, kCntFict, kCntEscaped, kCntMissed,
 
 // One request's share of a transport launch.  A single-request launch passes
 // it by value (the kernel's parameter space); a multi-request launch passes an
-// array of them in device memory, and each block copies the entry of the
+// array of them in device memory, and each warp copies the entry of the
 // request it is working on into shared memory.
 struct alignas(16) RequestDesc {
     const uint32_t *vox;         // [nvox] material and density of each voxel, one word (kRhoExpBias)

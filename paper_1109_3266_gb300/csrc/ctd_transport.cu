@@ -15,8 +15,8 @@
 // One kernel template, four forms: one request without a fluence map, one
 // request with one (its source path compiled only there), both with the request
 // in the kernel's parameter space; and many requests at once, without or with
-// maps (blocks walk through a request table, one request at a time, its
-// descriptor and tables in shared memory).
+// maps (warps walk through a request table, one request at a time, its
+// descriptor in shared memory, its tables read through L1).
 #include <cstring>
 
 #include "ctd_device.cuh"

@@ -752,8 +752,8 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--pool", type=int, default=4)
     ap.add_argument("--served-voxel-cm", type=float, default=0.5)
-    ap.add_argument("--served-small-requests", type=int, default=300, help="served form, small requests (0: none)")
-    ap.add_argument("--served-small-rate", type=float, default=28.0)
+    ap.add_argument("--served-small-requests", type=int, default=400, help="served form, small requests (0: none)")
+    ap.add_argument("--served-small-rate", type=float, default=40.0)
     ap.add_argument("--served-small-voxel-cm", type=float, default=1.0)
     ap.add_argument("--served-small-batch", type=int, default=4_000_000)
     ap.add_argument("--batch-histories", type=int, default=80_000_000)

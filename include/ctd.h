@@ -442,6 +442,13 @@ int ctd_submit(ctd_ctx *ctx, ctd_phantom ph, const ctd_request *req, ctd_req_id 
 /* One step of the served form (above); *n_active (may be NULL) is the number
  * of requests still queued or running afterwards. */
 int ctd_serve_step(ctd_ctx *ctx, int *n_active);
+/* Steps of the served form until one of them took in, retired, admitted or
+ * launched something, nothing is queued or running, or timeout_s seconds have
+ * passed (>= 0, else CTD_EINVAL); between steps in which nothing happened it
+ * sleeps 20 us.  *n_active (may be NULL) as for ctd_serve_step.  A request
+ * loop calls it with the time until the next arrival, so that it sees each
+ * batch end within tens of microseconds without spinning. */
+int ctd_serve_wait(ctd_ctx *ctx, double timeout_s, int *n_active);
 int ctd_poll(ctd_ctx *ctx, ctd_req_id id, ctd_req_status *out);
 /* Drive ctd_serve_step until request id has finished or timeout_s seconds have
  * passed (CTD_ETIMEOUT); out may be NULL. */

@@ -769,6 +769,23 @@ int ctd_serve_step(ctd_ctx *ctx, int *n_active)
     return rc;
 }
 
+int ctd_serve_wait(ctd_ctx *ctx, double timeout_s, int *n_active)
+{
+    int rc;
+    if ((rc = use_device(ctx))) return rc;
+    if (!(timeout_s >= 0.0)) return fail(CTD_EINVAL, "timeout_s must be >= 0");
+    const double t0 = now_s();
+    for (;;) {
+        bool progress = false;
+        if ((rc = serve_pump(ctx, &progress))) break;
+        if (progress || (ctx->active.empty() && ctx->pending.empty()) || elapsed_since(t0) >= timeout_s) break;
+        // every running request's work is on the GPU: look again shortly instead of spinning
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    if (n_active) *n_active = static_cast<int>(ctx->active.size() + ctx->pending.size());
+    return rc;
+}
+
 int ctd_poll(ctd_ctx *ctx, ctd_req_id id, ctd_req_status *out)
 {
     if (!ctx) return fail(CTD_EINVAL, "null context");

@@ -132,6 +132,7 @@ def lib():
                                     C.c_int]
         L.ctd_submit.argtypes = [P, C.c_int32, C.POINTER(ctd_request), C.POINTER(C.c_int64)]
         L.ctd_serve_step.argtypes = [P, C.POINTER(C.c_int)]
+        L.ctd_serve_wait.argtypes = [P, C.c_double, C.POINTER(C.c_int)]
         L.ctd_poll.argtypes = [P, C.c_int64, C.POINTER(ctd_req_status)]
         L.ctd_wait.argtypes = [P, C.c_int64, C.c_double, C.POINTER(ctd_req_status)]
         L.ctd_cancel.argtypes = [P, C.c_int64]
@@ -257,6 +258,14 @@ def ctd_submit(ctx, ph, batch_histories, rsd_target, seed, n_histories_max=0, mi
     out = C.c_int64()
     _check(lib().ctd_submit(ctx, ph, C.byref(r), C.byref(out)))
     return out.value
+
+
+def ctd_serve_wait(ctx, timeout_s):
+    """Step the served form until something changed or timeout_s passed; returns the
+    number of requests still queued or running."""
+    n = C.c_int()
+    _check(lib().ctd_serve_wait(ctx, float(timeout_s), C.byref(n)))
+    return n.value
 
 
 def ctd_serve_step(ctx):

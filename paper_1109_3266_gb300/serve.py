@@ -2,13 +2,14 @@
 
 Requests arrive at given times; at each turn of the loop the requests that
 have arrived are created on the device and submitted, and the library's
-scheduler is stepped once: it takes in the batches that have finished on the
-GPU, retires requests at their target avg RSD, admits queued requests by free
+scheduler is stepped until something changes or the next request is due
+(ctd_serve_wait): it takes in the batches that have finished on the GPU,
+retires requests at their target avg RSD, admits queued requests by free
 device memory and launches the next batches of running requests, each on its
 own stream, the request with the least work left first and at high priority
 (with the context's shared_launch option, one round of every running request
-in one shared launch instead).  Finished requests are read
-back and their phantoms released.  The scheduling and every step of the
+in one shared launch instead).  Finished requests are read back and their
+phantoms released.  The scheduling and every step of the
 transport run in the CUDA library; this module only drives it and keeps the
 clock.
 """
@@ -70,9 +71,10 @@ def serve(ctx, arrivals, make_problem, batch_histories, rsd_target, min_batches=
         if not running:
             time.sleep(max(0.0, min(0.01, reqs[nxt].t_arrival - now)))
             continue
-        ctd.ctd_serve_step(ctx)
+        # step until a batch ends or a request is admitted, at most until the next arrival
+        until = 1e-3 if nxt >= len(reqs) else min(1e-3, max(0.0, reqs[nxt].t_arrival - (time.perf_counter() - t0)))
+        ctd.ctd_serve_wait(ctx, until)
         t_now = time.perf_counter() - t0
-        n_before = len(running)
         for rid in list(running):
             st = ctd.ctd_poll(ctx, rid)
             if st["state"] >= ctd.REQ_DONE:
@@ -86,11 +88,6 @@ def serve(ctx, arrivals, make_problem, batch_histories, rsd_target, min_batches=
                 if keep_results:
                     r.stats = ctd.ctd_get_dose_and_stddev(ctx, r.handle, 0, want_arrays=False)[2]
                 ctd.ctd_destroy_phantom(ctx, r.handle)
-        if len(running) == n_before:
-            # nothing finished: the GPU is busy with every running request's batch
-            wait = 2e-4 if nxt >= len(reqs) else min(2e-4, max(0.0, reqs[nxt].t_arrival - t_now))
-            if wait > 0:
-                time.sleep(wait)
     return reqs, time.perf_counter() - t0
 
 

@@ -142,6 +142,10 @@ def test_served_cancel_timeout_and_queue(ctd, ctx):
         ctd.ctd_wait(ctx, rid, 0.0)
     assert e.value.code == 5                                   # CTD_ETIMEOUT
     ctd.ctd_serve_step(ctx)
+    assert ctd.ctd_serve_wait(ctx, 0.001) == 1                 # the request stays running
+    with pytest.raises(ctd.CtdError) as e:
+        ctd.ctd_serve_wait(ctx, -1.0)
+    assert e.value.code == 1                                   # CTD_EINVAL
     ctd.ctd_cancel(ctx, rid)
     ctd.ctd_serve_step(ctx)
     assert ctd.ctd_poll(ctx, rid)["state"] == ctd.REQ_CANCELLED

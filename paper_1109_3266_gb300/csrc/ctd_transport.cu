@@ -17,8 +17,6 @@
 // in the kernel's parameter space; and many requests at once, without or with
 // maps (warps walk through a request table, one request at a time, its
 // descriptor in shared memory, its tables read through L1).
-#include <cstring>
-
 #include "ctd_device.cuh"
 
 namespace ctd {
@@ -681,16 +679,14 @@ int launch_t(const LaunchParams &p, int grid, int block, size_t smem, cudaStream
         k<<<grid, block, smem, stream>>>(p);
         return cudaGetLastError() == cudaSuccess ? CTD_OK : CTD_ECUDA;
     }
-    cudaLaunchAttribute attr;
-    std::memset(&attr, 0, sizeof(attr));
+    cudaLaunchAttribute attr{};
     attr.id = cudaLaunchAttributeAccessPolicyWindow;
     attr.val.accessPolicyWindow.base_ptr = win->base;
     attr.val.accessPolicyWindow.num_bytes = win->bytes;
     attr.val.accessPolicyWindow.hitRatio = win->hit_ratio;
     attr.val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
     attr.val.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;

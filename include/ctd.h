@@ -395,7 +395,8 @@ int ctd_run_batch(ctd_ctx *ctx, int n_req, const ctd_phantom *phantoms, const ui
  * estimate (the batches up to min_batches, then the avg RSD taken to fall as
  * 1/sqrt(n); the earliest admitted among equals).  The first in line runs on a
  * stream of the device's greatest priority, every batch before its first stop
- * test in one go.  If its batches fill the GPU (at least 64 histories per
+ * test in one go (work already on the GPU runs to its end: a request that
+ * becomes first in line goes out at the next launch boundary).  If its batches fill the GPU (at least 64 histories per
  * resident thread of a launch), the second in line runs beside it one slice
  * (an eighth of a batch) at a time, and only while the first one's batch on the
  * GPU may be its last; if they do not, the others run, whole batches, while

@@ -139,7 +139,13 @@ void or_eval_log_f32(const float *u, float *out, size_t n);
 void or_eval_sincos_f32(const float *t, float *c, float *s, size_t n);
 void or_eval_uniform_f32(const uint32_t *x, float *out, size_t n);   /* or_uniform in binary32, n words */
 
-/* problem set-up (tables and surfaces) and transport of a history range */
+/* problem set-up (tables and surfaces) and transport of a history range.
+ * Parity unpinned for the full multiple-scatter dose in heterogeneous phantoms:
+ * nothing independent of this code gives it (no EGSnrc or PENELOPE data here).
+ * The transport rests on its pinned parts (cross sections, surfaces, sampling,
+ * allocation, Philox), on closed forms in slabs and pencil beams with one or two
+ * real interactions, on energy conservation, and on the binary64 and binary32
+ * runs agreeing history by history under the decision margins below. */
 typedef struct or_setup or_setup;
 or_setup *or_setup_create_f64(const or_problem *p);
 or_setup *or_setup_create_f32(const or_problem *p);
